@@ -1,0 +1,131 @@
+"""Pins for the oracle's SQP loop (Sec. II-A Steps 1-3, Eq. 3 and Eq. 7).
+
+* LQR special case: a single joint about z (gravity along z exerts no torque)
+  has linear semi-implicit Euler dynamics, so with the quadratic joint cost one
+  SQP step with alpha = 1 must reproduce the discrete Riccati solution.
+* On the nonlinear arm, line-search invariants: every accepted step lowers the
+  L1 merit, the KKT residual goes to zero, full steps are taken near the end.
+"""
+import numpy as np
+import pytest
+
+from paper_2510_07625_gb300 import inputs as I
+
+
+def riccati_lqr(A, B, W, wr, WN, e0, N):
+    P = WN.copy()
+    Ks = []
+    R = wr * np.eye(B.shape[1])
+    for _ in range(N):
+        K = np.linalg.solve(R + B.T @ P @ B, B.T @ P @ A)
+        P = W + A.T @ P @ A - A.T @ P @ B @ K
+        Ks.append(K)
+    Ks = Ks[::-1]
+    e = e0.copy()
+    E, Us = [e], []
+    for k in range(N):
+        u = -Ks[k] @ e
+        e = A @ e + B @ u
+        Us.append(u)
+        E.append(e)
+    return np.array(E), np.array(Us)
+
+
+@pytest.mark.parametrize("N,h", [(5, 0.05), (20, 0.01)])
+def test_one_sqp_step_equals_riccati_on_linear_joint(oracle, N, h):
+    model = I.chain([2], [0.3], [1.0], name="1z")
+    Izz = model.inertia[2]
+    prob = I.joint_problem(3, model, N=N, dt=h)
+    A = np.array([[1.0, h], [0.0, 1.0]])
+    B = np.array([[h * h / Izz], [h / Izz]])
+    wq, wqd, wr, ts = prob.w[:4]
+    W = np.diag([wq, wqd])
+    xr = prob.x_ref[0]
+    E, Us = riccati_lqr(A, B, W, wr, ts * W, prob.x_s - xr, N)
+    res = oracle.solve(prob, max_iter=1, replay=[0], pcg_eps=1e-13, pcg_max=10000)
+    np.testing.assert_allclose(res["X"], E + xr, rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(res["U"], Us, rtol=1e-9, atol=1e-9 * max(1, np.abs(Us).max()))
+    # at the QP optimum of a linear-quadratic problem the KKT residual vanishes
+    assert oracle.kkt_residual(prob, res["X"], res["U"], res["lam"]) < 1e-9
+    # and the merit line search itself picks the full step
+    free = oracle.solve(prob, max_iter=1, pcg_eps=1e-13, pcg_max=10000)
+    assert free["alpha_idx"][0] == 0
+
+
+def test_nonlinear_arm_invariants(oracle):
+    prob = I.config_single()[0]
+    res = oracle.solve(prob, max_iter=25)
+    acc = res["alpha_idx"] >= 0
+    assert acc.all()
+    assert np.all(res["merit_after"] < res["merit_before"])
+    assert res["kkt_log"][-1] < 1e-9
+    # asymptotic regime, above the rounding floor: full steps are taken
+    mid = (res["kkt_log"] < 1e-3) & (res["kkt_log"] > 1e-8)
+    assert mid.sum() >= 5 and np.all(res["alpha_idx"][mid] == 0)
+    # constraint violation of the final iterate is ~0 (dynamics satisfied)
+    lin = oracle.linearize(prob, res["X"], res["U"])
+    assert np.abs(lin["c"]).max() < 1e-7
+
+
+def test_kkt_tolerance_stops_early(oracle):
+    prob = I.config_single()[0]
+    res = oracle.solve(prob, max_iter=40, kkt_tol=1e-5)
+    assert res["flags"] & oracle.FLAG_CONVERGED
+    assert res["kkt"] <= 1e-5
+    assert res["iters"] < 40
+    X, U = res["X"], res["U"]
+    assert oracle.kkt_residual(prob, X, U, res["lam"]) <= 1e-5
+
+
+def test_replay_reproduces_free_run(oracle):
+    prob = I.joint_problem(11)
+    free = oracle.solve(prob, max_iter=6)
+    rep = oracle.solve(prob, max_iter=6, replay=free["alpha_idx"])
+    np.testing.assert_array_equal(free["X"], rep["X"])
+    np.testing.assert_array_equal(free["U"], rep["U"])
+
+
+def test_cold_start_reading(oracle):
+    prob = I.joint_problem(0)
+    X, U, lam = oracle.cold_start(prob)
+    assert np.all(X == prob.x_s) and np.all(U == 0) and np.all(lam == 0)
+
+
+def test_merit_closed_form_at_cold_start(oracle):
+    """Eq. 3 at X_k = x_s, U = 0: J has a closed form and c = [0, f(x_s,0) - x_s, ...]."""
+    prob = I.joint_problem(4, I.arm7(), N=8, dt=0.01)
+    X, U, _ = oracle.cold_start(prob)
+    wq, wqd, wr, ts = prob.w[:4]
+    W = np.diag([wq] * 7 + [wqd] * 7)
+    d = prob.x_s - prob.x_ref[0]
+    J = 0.5 * (prob.N + ts) * d @ W @ d
+    e = oracle.step(prob.model, prob.x_s, np.zeros(7), prob.dt) - prob.x_s
+    mu = 10.0
+    want = J + mu * prob.N * np.abs(e).sum()
+    assert abs(oracle.merit(prob, X, U, mu) - want) < 1e-12 * want
+    pe = I.ee_problem(5, I.arm7(), N=6, dt=0.01)
+    X, U, _ = oracle.cold_start(pe)
+    wq, wqd, wr, ts, wee, rho = pe.w
+    p = oracle.fk(pe.model, pe.x_s[:7])
+    Jee = 0.5 * wee * (np.sum((p - pe.ee_ref[:-1]) ** 2) + ts * np.sum((p - pe.ee_ref[-1]) ** 2))
+    e = oracle.step(pe.model, pe.x_s, np.zeros(7), pe.dt) - pe.x_s
+    want = Jee + mu * pe.N * np.abs(e).sum()
+    assert abs(oracle.merit(pe, X, U, mu) - want) < 1e-12 * want
+
+
+def test_oracle_regression_fixture(oracle):
+    """Record written by tests/golden/make_golden.py (oracle only)."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "oracle_regression.json")
+    with open(path) as f:
+        gold = json.load(f)
+    cases = {"config_single": I.config_single()[0],
+             "arm6_seed1_N20": I.joint_problem(1, I.arm6(), N=20)}
+    for key, prob in cases.items():
+        g = gold[key]
+        r = oracle.solve(prob, max_iter=g["iters"])
+        assert r["alpha_idx"].tolist() == g["alpha_idx"]
+        np.testing.assert_allclose(r["X"], np.array(g["X"]), atol=1e-9)
+        np.testing.assert_allclose(r["U"], np.array(g["U"]), atol=1e-8)
+        np.testing.assert_allclose(r["kkt_log"], g["kkt_log"], rtol=1e-8)
