@@ -159,6 +159,26 @@ gato_status gato_get_results(gato_batch* b, gato_result* out, int32_t n);
 
 void gato_destroy_batch(gato_batch* b);
 
+/* Bytes copied host->device and device->host by the last solve call (host
+ * problems are staged through pinned memory; device problems copy only the
+ * descriptors and results).  Descriptor/result traffic is included. */
+gato_status gato_last_transfer_bytes(const gato_batch* b, int64_t* h2d, int64_t* d2h);
+
+/* ---- introspection for stage-level checks (not needed by solvers) ----
+ * Runs the plain form on problems[0] for its first SQP iteration, stopping
+ * after stage `stop_stage` (1 dynamics columns, 2 forward dynamics, 3 value
+ * pass + costs, 4 tangents, 5 dynamics Jacobians, 6 KKT residual, 7 Schur
+ * blocks, 8 preconditioner blocks, 9 PCG, 10 step recovery, 11 line search,
+ * 12 accept), then copies that solve's whole workspace (floats, layout given
+ * by gato_debug_layout) to ws_out[0..ws_floats).  Synchronous. */
+gato_status gato_debug_plain_stage(gato_batch* b, const gato_problem* problems, int32_t stop_stage,
+                                   float* ws_out, int64_t ws_floats);
+
+/* Fills offsets[0..21] (floats) of the workspace arrays in the order
+ * X U dX dU Fq Fv Minv qdd dTau Qinv Rinv q r c Jk Linv links D L P vec scal,
+ * and returns the workspace size in floats (or -1). */
+int64_t gato_debug_layout(const gato_batch* b, int64_t* offsets);
+
 const char* gato_status_string(gato_status s);
 const char* gato_last_error(const gato_batch* b);
 

@@ -1,0 +1,532 @@
+// C ABI of the batched SQP library (declared in include/gato.h).
+//
+// Host-side duties only: validation, model conversion, staging of host
+// problems through pinned memory, longest-horizon-first ordering, launching
+// the kernels in gato_kernels.cu and copying results back.  No arithmetic of
+// the method runs here.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/gato.h"
+#include "gato_internal.h"
+
+using namespace gato;
+
+namespace {
+
+struct HostCopyBack {
+  float* X;
+  float* U;
+  float* lam;
+  size_t nX, nU;              // element counts in user layout (lam has nX)
+  size_t offX, offU, offL;    // staging offsets (floats)
+  size_t end;                 // staging end of this problem
+};
+
+}  // namespace
+
+struct gato_batch {
+  int max_batch = 0, max_horizon = 0, n_models = 0;
+  DevModel models_h[8];
+  int model_dof[8];
+  gato_solver_params params;
+  cudaStream_t stream = nullptr;
+  DevModel* models_d = nullptr;
+  ProbDesc* probs_d = nullptr;
+  ProbDesc* probs_h = nullptr;
+  int* order_d = nullptr;
+  int* order_h = nullptr;
+  Result* res_d = nullptr;
+  Result* res_h = nullptr;
+  float* ws_d = nullptr;
+  size_t ws_stride = 0;
+  WsLayout layout;
+  float* plain_ws_d = nullptr;
+  WsLayout plain_layout;
+  float* stage_d = nullptr;
+  float* stage_h = nullptr;
+  size_t stage_stride = 0;
+  cudaEvent_t done = nullptr;
+  int last_n = 0;
+  bool pending = false;
+  std::vector<HostCopyBack> copy_back;
+  int64_t h2d_bytes = 0, d2h_bytes = 0;
+  std::string err;
+};
+
+namespace {
+
+gato_status fail(gato_batch* b, gato_status s, const std::string& msg) {
+  if (b) b->err = msg;
+  return s;
+}
+
+gato_status cuda_fail(gato_batch* b, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(b, GATO_E_CUDA, m);
+}
+
+bool finite_all(const float* a, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+size_t stage_floats(int nmax) {
+  const size_t K = nmax + 1;
+  return align32(16 + K * XM + K * 3 + K * XM + (size_t)nmax * QM + K * XM);
+}
+
+bool convert_model(const gato_model_desc& d, DevModel& m, std::string& why) {
+  if (d.dof < 1 || d.dof > QM) { why = "model dof must be 1..7"; return false; }
+  if (!(d.gravity >= 0.f) || !std::isfinite(d.gravity)) { why = "gravity must be finite and >= 0"; return false; }
+  std::memset(&m, 0, sizeof(m));
+  m.dof = d.dof;
+  m.g = d.gravity;
+  for (int i = 0; i < QM; ++i) {
+    if (i < d.dof) {
+      if (d.axis[i] < 0 || d.axis[i] > 2) { why = "joint axis must be 0, 1 or 2"; return false; }
+      if (!(d.link_len[i] >= 0.f) || !std::isfinite(d.link_len[i])) { why = "link lengths must be finite and >= 0"; return false; }
+      if (!(d.mass[i] > 0.f) || !std::isfinite(d.mass[i])) { why = "link masses must be finite and > 0"; return false; }
+      m.axis[i] = d.axis[i];
+      m.L[i] = d.link_len[i];
+      m.m[i] = d.mass[i];
+      for (int a = 0; a < 3; ++a) {
+        const float c = d.com[3 * i + a], I = d.inertia[3 * i + a];
+        if (!std::isfinite(c) || !(I >= 0.f) || !std::isfinite(I)) { why = "com / inertia must be finite, inertia >= 0"; return false; }
+        m.com[3 * i + a] = c;
+        m.Ic[3 * i + a] = I;
+      }
+    } else {
+      // massless padding joint at the end effector: exact zero rows downstream
+      m.axis[i] = 2;
+    }
+  }
+  return true;
+}
+
+gato_status validate_params(gato_batch* b, const gato_solver_params& p) {
+  if (!(p.mu >= 0.f) || !std::isfinite(p.mu)) return fail(b, GATO_E_INVALID, "mu must be finite and >= 0");
+  if (!(p.beta > 1.f) || !std::isfinite(p.beta)) return fail(b, GATO_E_INVALID, "beta must be > 1");
+  if (p.n_alpha < 1 || p.n_alpha > MAX_ALPHA) return fail(b, GATO_E_INVALID, "n_alpha must be 1..16");
+  if (!(p.pcg_eps > 0.f)) return fail(b, GATO_E_INVALID, "pcg_eps must be > 0");
+  if (p.pcg_max_iter < 1) return fail(b, GATO_E_INVALID, "pcg_max_iter must be >= 1");
+  if (p.precond != GATO_PRECOND_STAIR && p.precond != GATO_PRECOND_JACOBI)
+    return fail(b, GATO_E_INVALID, "unknown preconditioner");
+  if (!std::isfinite(p.kkt_tol)) return fail(b, GATO_E_INVALID, "kkt_tol must be finite");
+  return GATO_OK;
+}
+
+gato_status validate_problem(gato_batch* b, const gato_problem& p, int idx) {
+  char buf[160];
+  auto bad = [&](const char* why) {
+    std::snprintf(buf, sizeof(buf), "problem %d: %s", idx, why);
+    return fail(b, GATO_E_INVALID, buf);
+  };
+  if (p.model < 0 || p.model >= b->n_models) return bad("model index out of range");
+  if (p.N < 1 || p.N > b->max_horizon) return bad("N must be 1..max_horizon");
+  if (!(p.dt > 0.f) || !std::isfinite(p.dt)) return bad("dt must be finite and > 0");
+  if (p.mem != GATO_MEM_HOST && p.mem != GATO_MEM_DEVICE) return bad("mem must be HOST or DEVICE");
+  if (!p.x_s || !p.X || !p.U) return bad("x_s, X and U are required");
+  for (int i = 0; i < 6; ++i)
+    if (!std::isfinite(p.w[i]) || p.w[i] < 0.f) return bad("weights must be finite and >= 0");
+  const float wq = p.w[0], wqd = p.w[1], wr = p.w[2], ts = p.w[3], rho = p.w[5];
+  if (!(wr > 0.f)) return bad("control weight must be > 0");
+  if (!(ts > 0.f)) return bad("terminal scale must be > 0");
+  if (p.cost_kind == GATO_COST_JOINT) {
+    if (!p.x_ref) return bad("joint cost needs x_ref");
+    if (!(wq + rho > 0.f) || !(wqd + rho > 0.f)) return bad("joint cost Hessian must be positive definite");
+  } else if (p.cost_kind == GATO_COST_EE) {
+    if (!p.ee_ref) return bad("end-effector cost needs ee_ref");
+    if (!(rho > 0.f) || !(wqd + rho > 0.f)) return bad("end-effector cost needs rho > 0");
+  } else {
+    return bad("unknown cost kind");
+  }
+  if (p.mem == GATO_MEM_HOST) {
+    const int nx = 2 * b->model_dof[p.model], nu = b->model_dof[p.model];
+    if (!finite_all(p.x_s, nx)) return bad("x_s is not finite");
+    if (!finite_all(p.X, (size_t)(p.N + 1) * nx) || !finite_all(p.U, (size_t)p.N * nu))
+      return bad("initial X / U not finite");
+    if (p.cost_kind == GATO_COST_JOINT && !finite_all(p.x_ref, (size_t)(p.N + 1) * nx))
+      return bad("x_ref not finite");
+    if (p.cost_kind == GATO_COST_EE && !finite_all(p.ee_ref, (size_t)(p.N + 1) * 3))
+      return bad("ee_ref not finite");
+    if (p.lambda && !finite_all(p.lambda, (size_t)(p.N + 1) * nx)) return bad("lambda not finite");
+  }
+  return GATO_OK;
+}
+
+Params to_params(const gato_solver_params& p, int iters) {
+  Params o;
+  o.mu = p.mu;
+  o.beta = p.beta;
+  o.n_alpha = p.n_alpha;
+  o.pcg_eps = p.pcg_eps;
+  o.pcg_max = p.pcg_max_iter;
+  o.precond = p.precond;
+  o.kkt_tol = p.kkt_tol;
+  o.max_iter = iters;
+  return o;
+}
+
+// Builds the device descriptors (staging host problems), returns max N.
+gato_status prepare(gato_batch* b, const gato_problem* probs, int n, int* nmax_out) {
+  if (!probs || n < 1) return fail(b, GATO_E_INVALID, "need at least one problem");
+  if (n > b->max_batch) return fail(b, GATO_E_INVALID, "more problems than max_batch");
+  if (b->pending) {
+    gato_status s = gato_sync(b, -1);
+    if (s != GATO_OK) return s;
+  }
+  for (int i = 0; i < n; ++i) {
+    gato_status s = validate_problem(b, probs[i], i);
+    if (s != GATO_OK) return s;
+  }
+  b->copy_back.clear();
+  b->h2d_bytes = b->d2h_bytes = 0;
+  int nmax = 1;
+  size_t staged = 0;
+  for (int i = 0; i < n; ++i) {
+    const gato_problem& p = probs[i];
+    const int dof = b->model_dof[p.model], nx = 2 * dof, nu = dof, N = p.N;
+    ProbDesc& d = b->probs_h[i];
+    std::memset(&d, 0, sizeof(d));
+    d.model = p.model;
+    d.N = N;
+    d.cost_kind = p.cost_kind;
+    d.dof = dof;
+    d.dt = p.dt;
+    for (int k = 0; k < 6; ++k) d.w[k] = p.w[k];
+    nmax = std::max(nmax, N);
+    if (p.mem == GATO_MEM_DEVICE) {
+      d.x_s = p.x_s;
+      d.x_ref = p.cost_kind == GATO_COST_JOINT ? p.x_ref : nullptr;
+      d.ee_ref = p.cost_kind == GATO_COST_EE ? p.ee_ref : nullptr;
+      d.X = p.X;
+      d.U = p.U;
+      d.lam = p.lambda;
+    } else {
+      const size_t base = (size_t)i * b->stage_stride;
+      float* h = b->stage_h + base;
+      float* dv = b->stage_d + base;
+      const size_t K = N + 1;
+      size_t o = 0;
+      std::memcpy(h + o, p.x_s, nx * sizeof(float));
+      d.x_s = dv + o;
+      o += 16;
+      if (p.cost_kind == GATO_COST_JOINT) {
+        std::memcpy(h + o, p.x_ref, K * nx * sizeof(float));
+        d.x_ref = dv + o;
+      } else {
+        std::memcpy(h + o, p.ee_ref, K * 3 * sizeof(float));
+        d.ee_ref = dv + o;
+      }
+      o += K * XM;
+      const size_t oX = o;
+      std::memcpy(h + o, p.X, K * nx * sizeof(float));
+      d.X = dv + o;
+      o += K * XM;
+      std::memcpy(h + o, p.U, (size_t)N * nu * sizeof(float));
+      d.U = dv + o;
+      o += (size_t)N * QM;
+      if (p.lambda) {
+        std::memcpy(h + o, p.lambda, K * nx * sizeof(float));
+        d.lam = dv + o;
+      } else {
+        d.lam = nullptr;
+      }
+      o += K * XM;
+      HostCopyBack cb{p.X, p.U, p.lambda, K * nx, (size_t)N * nu, base + oX,
+                      base + oX + K * XM, base + oX + K * XM + (size_t)N * QM, base + o};
+      b->copy_back.push_back(cb);
+      staged = std::max(staged, base + o);
+      b->h2d_bytes += (int64_t)(nx + (p.cost_kind == GATO_COST_JOINT ? K * nx : K * 3) + K * nx +
+                                (size_t)N * nu + (p.lambda ? K * nx : 0)) * 4;
+      b->d2h_bytes += (int64_t)(K * nx + (size_t)N * nu + (p.lambda ? K * nx : 0)) * 4;
+    }
+  }
+  // longest horizon first: long solves start in the first wave
+  std::vector<int> idx(n);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return probs[a].N > probs[c].N; });
+  for (int i = 0; i < n; ++i) b->order_h[i] = idx[i];
+  cudaError_t e;
+  if (staged > 0) {
+    e = cudaMemcpyAsync(b->stage_d, b->stage_h, staged * sizeof(float), cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) return cuda_fail(b, e, "stage problems");
+  }
+  e = cudaMemcpyAsync(b->probs_d, b->probs_h, n * sizeof(ProbDesc), cudaMemcpyHostToDevice, b->stream);
+  if (e != cudaSuccess) return cuda_fail(b, e, "copy descriptors");
+  e = cudaMemcpyAsync(b->order_d, b->order_h, n * sizeof(int), cudaMemcpyHostToDevice, b->stream);
+  if (e != cudaSuccess) return cuda_fail(b, e, "copy order");
+  *nmax_out = nmax;
+  return GATO_OK;
+}
+
+gato_status finish_launch(gato_batch* b, int n, gato_result* results) {
+  cudaError_t e = cudaMemcpyAsync(b->res_h, b->res_d, n * sizeof(Result), cudaMemcpyDeviceToHost, b->stream);
+  if (e != cudaSuccess) return cuda_fail(b, e, "copy results");
+  if (!b->copy_back.empty()) {
+    size_t hi = 0;
+    for (auto& c : b->copy_back) hi = std::max(hi, c.end);
+    e = cudaMemcpyAsync(b->stage_h, b->stage_d, hi * sizeof(float), cudaMemcpyDeviceToHost, b->stream);
+    if (e != cudaSuccess) return cuda_fail(b, e, "copy solutions");
+  }
+  b->d2h_bytes += (int64_t)n * sizeof(Result);
+  e = cudaEventRecord(b->done, b->stream);
+  if (e != cudaSuccess) return cuda_fail(b, e, "record completion");
+  b->last_n = n;
+  b->pending = true;
+  if (results) {
+    gato_status s = gato_sync(b, -1);
+    if (s != GATO_OK) return s;
+    return gato_get_results(b, results, n);
+  }
+  return GATO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void gato_default_params(gato_solver_params* o) {
+  if (!o) return;
+  o->mu = 10.f;
+  o->beta = 2.f;
+  o->n_alpha = 8;
+  o->pcg_eps = 1e-6f;
+  o->pcg_max_iter = 1000;
+  o->precond = GATO_PRECOND_STAIR;
+  o->kkt_tol = 0.f;
+}
+
+const char* gato_status_string(gato_status s) {
+  switch (s) {
+    case GATO_OK: return "ok";
+    case GATO_E_INVALID: return "invalid argument";
+    case GATO_E_NOMEM: return "out of memory";
+    case GATO_E_CUDA: return "CUDA error";
+    case GATO_E_TIMEOUT: return "timeout";
+    case GATO_E_BUSY: return "busy";
+  }
+  return "unknown status";
+}
+
+const char* gato_last_error(const gato_batch* b) { return b ? b->err.c_str() : "no batch"; }
+
+gato_status gato_create_batch(const gato_batch_desc* desc, void* cuda_stream, gato_batch** out) {
+  if (!out) return GATO_E_INVALID;
+  *out = nullptr;
+  if (!desc || !desc->models) return GATO_E_INVALID;
+  if (desc->max_batch < 1 || desc->max_horizon < 1 || desc->max_horizon > NMAX_LIMIT ||
+      desc->n_models < 1 || desc->n_models > 8)
+    return GATO_E_INVALID;
+  gato_batch* b = new (std::nothrow) gato_batch();
+  if (!b) return GATO_E_NOMEM;
+  b->max_batch = desc->max_batch;
+  b->max_horizon = desc->max_horizon;
+  b->n_models = desc->n_models;
+  b->params = desc->params;
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  std::string why;
+  for (int i = 0; i < desc->n_models; ++i) {
+    if (!convert_model(desc->models[i], b->models_h[i], why)) {
+      delete b;
+      return GATO_E_INVALID;
+    }
+    b->model_dof[i] = desc->models[i].dof;
+  }
+  if (validate_params(b, desc->params) != GATO_OK) {
+    delete b;
+    return GATO_E_INVALID;
+  }
+  const int nmax = desc->max_horizon;
+  b->layout = ws_layout(nmax, nmax > SMEM_BLOCKS_NMAX, false);
+  b->ws_stride = b->layout.total;
+  b->plain_layout = ws_layout(nmax, true, true);
+  b->stage_stride = stage_floats(nmax);
+  const size_t nb = b->max_batch;
+  bool ok = true;
+  ok = ok && cudaMalloc(&b->models_d, 8 * sizeof(DevModel)) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->probs_d, nb * sizeof(ProbDesc)) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->order_d, nb * sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->res_d, nb * sizeof(Result)) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->ws_d, nb * b->ws_stride * sizeof(float)) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->plain_ws_d, b->plain_layout.total * sizeof(float)) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->stage_d, nb * b->stage_stride * sizeof(float)) == cudaSuccess;
+  ok = ok && cudaMallocHost(&b->probs_h, nb * sizeof(ProbDesc)) == cudaSuccess;
+  ok = ok && cudaMallocHost(&b->order_h, nb * sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMallocHost(&b->res_h, nb * sizeof(Result)) == cudaSuccess;
+  ok = ok && cudaMallocHost(&b->stage_h, nb * b->stage_stride * sizeof(float)) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    gato_destroy_batch(b);
+    return GATO_E_NOMEM;
+  }
+  if (cudaMemcpy(b->models_d, b->models_h, 8 * sizeof(DevModel), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(b->ws_d, 0, nb * b->ws_stride * sizeof(float)) != cudaSuccess ||
+      cudaMemset(b->plain_ws_d, 0, b->plain_layout.total * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    gato_destroy_batch(b);
+    return GATO_E_CUDA;
+  }
+  *out = b;
+  return GATO_OK;
+}
+
+void gato_destroy_batch(gato_batch* b) {
+  if (!b) return;
+  if (b->pending && b->done) cudaEventSynchronize(b->done);
+  cudaFree(b->models_d);
+  cudaFree(b->probs_d);
+  cudaFree(b->order_d);
+  cudaFree(b->res_d);
+  cudaFree(b->ws_d);
+  cudaFree(b->plain_ws_d);
+  cudaFree(b->stage_d);
+  cudaFreeHost(b->probs_h);
+  cudaFreeHost(b->order_h);
+  cudaFreeHost(b->res_h);
+  cudaFreeHost(b->stage_h);
+  if (b->done) cudaEventDestroy(b->done);
+  delete b;
+}
+
+gato_status gato_solve(gato_batch* b, const gato_problem* problems, int32_t n,
+                       int32_t max_sqp_iters, gato_result* results) {
+  if (!b) return GATO_E_INVALID;
+  if (max_sqp_iters < 1) return fail(b, GATO_E_INVALID, "max_sqp_iters must be >= 1");
+  int nmax = 0;
+  gato_status s = prepare(b, problems, n, &nmax);
+  if (s != GATO_OK) return s;
+  FusedLaunch a;
+  a.probs = b->probs_d;
+  a.models = b->models_d;
+  a.order = b->order_d;
+  a.results = b->res_d;
+  a.ws = b->ws_d;
+  a.ws_stride = b->ws_stride;
+  a.layout = b->layout;
+  a.n = n;
+  a.nmax = nmax;
+  a.iters = max_sqp_iters;
+  a.prm = to_params(b->params, max_sqp_iters);
+  a.threads = 0;
+  if (nmax > SMEM_BLOCKS_NMAX && b->layout.Dm == 0)
+    return fail(b, GATO_E_INVALID, "horizon too long for this batch");
+  cudaError_t e = launch_fused(a, b->stream);
+  if (e != cudaSuccess) return cuda_fail(b, e, "launch fused kernel");
+  return finish_launch(b, n, results);
+}
+
+gato_status gato_step(gato_batch* b, const gato_problem* problems, int32_t n, gato_result* results) {
+  return gato_solve(b, problems, n, 1, results);
+}
+
+gato_status gato_solve_plain(gato_batch* b, const gato_problem* problems, int32_t n,
+                             int32_t max_sqp_iters, gato_result* results) {
+  if (!b) return GATO_E_INVALID;
+  if (max_sqp_iters < 1) return fail(b, GATO_E_INVALID, "max_sqp_iters must be >= 1");
+  int nmax = 0;
+  gato_status s = prepare(b, problems, n, &nmax);
+  if (s != GATO_OK) return s;
+  const Params prm = to_params(b->params, max_sqp_iters);
+  for (int i = 0; i < n; ++i) {
+    cudaError_t e = launch_plain(b->probs_d, b->models_d, b->res_d, i, b->plain_ws_d, b->plain_layout,
+                                 b->max_horizon, max_sqp_iters, prm, -1, b->stream);
+    if (e != cudaSuccess) return cuda_fail(b, e, "launch plain stages");
+  }
+  return finish_launch(b, n, results);
+}
+
+gato_status gato_sync(gato_batch* b, int64_t timeout_us) {
+  if (!b) return GATO_E_INVALID;
+  if (!b->pending) return GATO_OK;
+  const auto t0 = std::chrono::steady_clock::now();
+  while (true) {
+    cudaError_t e = cudaEventQuery(b->done);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) {
+      b->pending = false;
+      return cuda_fail(b, e, "wait for batch");
+    }
+    if (timeout_us >= 0) {
+      const auto us = std::chrono::duration_cast<std::chrono::microseconds>(
+                          std::chrono::steady_clock::now() - t0).count();
+      if (us >= timeout_us) return fail(b, GATO_E_TIMEOUT, "sync deadline passed");
+    }
+    std::this_thread::yield();
+  }
+  b->pending = false;
+  // scatter host outputs: X, U, lambda from the staging copy
+  for (auto& c : b->copy_back) {
+    std::memcpy(c.X, b->stage_h + c.offX, c.nX * sizeof(float));
+    std::memcpy(c.U, b->stage_h + c.offU, c.nU * sizeof(float));
+    if (c.lam) std::memcpy(c.lam, b->stage_h + c.offL, c.nX * sizeof(float));
+  }
+  b->copy_back.clear();
+  return GATO_OK;
+}
+
+gato_status gato_get_results(gato_batch* b, gato_result* out, int32_t n) {
+  if (!b || !out) return GATO_E_INVALID;
+  if (b->pending) return fail(b, GATO_E_BUSY, "call gato_sync first");
+  if (n > b->last_n) return fail(b, GATO_E_INVALID, "more results requested than solves");
+  for (int i = 0; i < n; ++i) {
+    out[i].flags = b->res_h[i].flags;
+    out[i].sqp_iters = b->res_h[i].sqp_iters;
+    out[i].pcg_iters = b->res_h[i].pcg_iters;
+    out[i].kkt_residual = b->res_h[i].kkt;
+    out[i].merit = b->res_h[i].merit;
+  }
+  return GATO_OK;
+}
+
+gato_status gato_last_transfer_bytes(const gato_batch* b, int64_t* h2d, int64_t* d2h) {
+  if (!b) return GATO_E_INVALID;
+  if (h2d) *h2d = b->h2d_bytes;
+  if (d2h) *d2h = b->d2h_bytes;
+  return GATO_OK;
+}
+
+int64_t gato_debug_layout(const gato_batch* b, int64_t* o) {
+  if (!b || !o) return -1;
+  const WsLayout& L = b->plain_layout;
+  const size_t K = b->max_horizon + 1;
+  const size_t v[22] = {L.X,  L.U,  L.dX, L.dU, L.Fq, L.Fv, L.Mi, L.qdd, L.dT, L.Qi, L.Ri,
+                        L.qg, L.rg, L.cv, L.Jk, L.Li, L.LV, L.Dm, L.Lm,  L.Pm, L.vec,
+                        L.vec + 12 * K * VS};
+  for (int i = 0; i < 22; ++i) o[i] = (int64_t)v[i];
+  return (int64_t)L.total;
+}
+
+gato_status gato_debug_plain_stage(gato_batch* b, const gato_problem* problems, int32_t stop_stage,
+                                   float* ws_out, int64_t ws_floats) {
+  if (!b || !ws_out) return GATO_E_INVALID;
+  if (stop_stage < PS_MASS || stop_stage > PS_ACCEPT) return fail(b, GATO_E_INVALID, "bad stage");
+  if (ws_floats < (int64_t)b->plain_layout.total) return fail(b, GATO_E_INVALID, "ws_out too small");
+  int nmax = 0;
+  gato_status s = prepare(b, problems, 1, &nmax);
+  if (s != GATO_OK) return s;
+  const Params prm = to_params(b->params, 1);
+  cudaError_t e = launch_plain(b->probs_d, b->models_d, b->res_d, 0, b->plain_ws_d, b->plain_layout,
+                               b->max_horizon, 1, prm, stop_stage, b->stream);
+  if (e != cudaSuccess) return cuda_fail(b, e, "launch plain stages");
+  e = cudaMemcpyAsync(ws_out, b->plain_ws_d, b->plain_layout.total * sizeof(float),
+                      cudaMemcpyDeviceToHost, b->stream);
+  if (e != cudaSuccess) return cuda_fail(b, e, "copy workspace");
+  e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_fail(b, e, "stage run");
+  b->copy_back.clear();
+  return GATO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,413 @@
+// Device-side types, compensated arithmetic and rigid-body dynamics for the
+// batched SQP kernels (GATO, arXiv 2510.07625).
+//
+// Dynamics are written in 3-D Newton-Euler form in link coordinates: a value
+// pass of the recursive Newton-Euler algorithm (RNEA) and a tangent pass that
+// propagates one directional derivative d/dq_j or d/dqd_j through the same
+// recursion using the value pass's stored link quantities.  The paper uses an
+// external dynamics library for these (Sec. III-A); this is a from-scratch
+// replacement.  Every model is padded to 7 joints: joints past the model's dof
+// are massless, sit at the end effector, and get a unit diagonal in M, so the
+// padded rows of every matrix and vector stay exactly zero.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gato {
+
+constexpr int QM = 7;    // joints (padded)
+constexpr int XM = 14;   // state rows [q(7); qd(7)]
+constexpr int VS = 16;   // per-knot stride of state-sized vectors
+constexpr int US = 8;    // per-knot stride of control-sized vectors
+constexpr int BS = 199;  // per-knot stride of a 14x14 column-major block (196 + pad, 199 = 7 mod 32)
+constexpr int LVS = 24;  // floats per stored link record
+constexpr int MAX_ALPHA = 16;
+
+struct DevModel {
+  int dof;
+  int axis[QM];
+  float L[QM];
+  float m[QM];
+  float com[3 * QM];
+  float Ic[3 * QM];
+  float g;
+  float pad[3];
+};
+
+struct ProbDesc {
+  int model, N, cost_kind, dof;
+  float dt;
+  float w[6];
+  int pad0;
+  const float* x_s;
+  const float* x_ref;
+  const float* ee_ref;
+  float* X;
+  float* U;
+  float* lam;
+};
+
+struct Params {
+  float mu, beta;
+  int n_alpha;
+  float pcg_eps;
+  int pcg_max;
+  int precond;
+  float kkt_tol;
+  int max_iter;
+};
+
+struct Result {
+  int flags, sqp_iters, pcg_iters;
+  float kkt, merit;
+};
+
+enum : int {
+  F_CONVERGED = 1, F_MAXITER = 2, F_LSFAIL = 4, F_PCGMAX = 8, F_NONFINITE = 16
+};
+
+// ----------------------------------------------------------------- 3-vectors
+
+struct V3 {
+  float x, y, z;
+};
+__device__ __forceinline__ V3 v3(float x, float y, float z) { return V3{x, y, z}; }
+__device__ __forceinline__ V3 vzero() { return V3{0.f, 0.f, 0.f}; }
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return V3{a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return V3{a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V3 operator*(float s, V3 a) { return V3{s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ V3 cross(V3 a, V3 b) {
+  return V3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ float dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3 mulI(V3 I, V3 v) { return V3{I.x * v.x, I.y * v.y, I.z * v.z}; }
+
+// Coordinates of a parent-frame vector in the child frame rotated by q about axis a.
+__device__ __forceinline__ V3 rotT(int a, float s, float c, V3 v) {
+  if (a == 2) return V3{c * v.x + s * v.y, -s * v.x + c * v.y, v.z};
+  if (a == 1) return V3{c * v.x - s * v.z, v.y, s * v.x + c * v.z};
+  return V3{v.x, c * v.y + s * v.z, -s * v.y + c * v.z};
+}
+// Child-frame vector expressed in the parent frame.
+__device__ __forceinline__ V3 rot(int a, float s, float c, V3 v) {
+  if (a == 2) return V3{c * v.x - s * v.y, s * v.x + c * v.y, v.z};
+  if (a == 1) return V3{c * v.x + s * v.z, v.y, -s * v.x + c * v.z};
+  return V3{v.x, c * v.y - s * v.z, s * v.y + c * v.z};
+}
+// e_a x v
+__device__ __forceinline__ V3 ecross(int a, V3 v) {
+  if (a == 2) return V3{-v.y, v.x, 0.f};
+  if (a == 1) return V3{v.z, 0.f, -v.x};
+  return V3{0.f, -v.z, v.y};
+}
+__device__ __forceinline__ V3 unitv(int a) {
+  return a == 0 ? V3{1.f, 0.f, 0.f} : (a == 1 ? V3{0.f, 1.f, 0.f} : V3{0.f, 0.f, 1.f});
+}
+__device__ __forceinline__ float comp(int a, V3 v) { return a == 0 ? v.x : (a == 1 ? v.y : v.z); }
+
+// ------------------------------------------------------ compensated sums (Dot2)
+// Error-free transformations (Knuth TwoSum, FMA-based TwoProduct) keep a
+// running (hi, lo) pair, as in Ogita-Rump-Oishi's Dot2: the result is as
+// accurate as a sum carried in twice the working precision.
+
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF df_zero() { return DF{0.f, 0.f}; }
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ DF df_add(DF x, float y) {
+  float s, e;
+  two_sum(x.hi, y, s, e);
+  return DF{s, __fadd_rn(x.lo, e)};
+}
+__device__ __forceinline__ DF df_fma(DF x, float a, float b) {
+  float p = __fmul_rn(a, b);
+  float pe = __fmaf_rn(a, b, -p);
+  float s, e;
+  two_sum(x.hi, p, s, e);
+  return DF{s, __fadd_rn(x.lo, __fadd_rn(e, pe))};
+}
+__device__ __forceinline__ DF df_addd(DF x, DF y) {
+  float s, e;
+  two_sum(x.hi, y.hi, s, e);
+  return DF{s, __fadd_rn(__fadd_rn(x.lo, y.lo), e)};
+}
+__device__ __forceinline__ float df_val(DF x) { return __fadd_rn(x.hi, x.lo); }
+__device__ __forceinline__ DF df_norm(DF x) {
+  float s, e;
+  two_sum(x.hi, x.lo, s, e);
+  return DF{s, e};
+}
+__device__ __forceinline__ DF warp_df_sum(DF x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    DF y;
+    y.hi = __shfl_xor_sync(0xffffffffu, x.hi, o);
+    y.lo = __shfl_xor_sync(0xffffffffu, x.lo, o);
+    x = df_addd(x, y);
+  }
+  return x;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// ------------------------------------------------------------------ dynamics
+
+struct LinkRec {  // value-pass quantities of one link (link coordinates)
+  float s, c;
+  V3 wpT;   // parent angular velocity, in this frame
+  V3 wdpT;  // parent angular acceleration, in this frame
+  V3 w, wd; // this link's angular velocity / acceleration
+  V3 a;     // linear acceleration of this frame's origin (gravity included)
+  V3 f, n;  // total force / moment transmitted through this joint
+  float pad;
+};
+static_assert(sizeof(LinkRec) == LVS * sizeof(float), "link record size");
+
+__device__ __forceinline__ V3 mcom(const DevModel& M, int i) {
+  return V3{M.com[3 * i], M.com[3 * i + 1], M.com[3 * i + 2]};
+}
+__device__ __forceinline__ V3 minert(const DevModel& M, int i) {
+  return V3{M.Ic[3 * i], M.Ic[3 * i + 1], M.Ic[3 * i + 2]};
+}
+
+// Inverse dynamics tau = ID(q, qd, qdd) by RNEA.  sq/cq are sin/cos of q.
+// `grav` is the magnitude of gravity along -z (0 turns it off).  When rec is
+// non-null the link quantities are stored for a later tangent pass.
+__device__ __forceinline__ void rnea_value(const DevModel& M, const float* sq, const float* cq,
+                                           const float* qd, const float* qdd, float grav,
+                                           float* tau, LinkRec* rec) {
+  V3 F[QM], Nm[QM];
+  V3 wp = vzero(), wdp = vzero(), ap = v3(0.f, 0.f, grav);
+#pragma unroll
+  for (int i = 0; i < QM; ++i) {
+    const int a = M.axis[i];
+    const float s = sq[i], c = cq[i];
+    const V3 r = v3(0.f, 0.f, i > 0 ? M.L[i - 1] : 0.f);
+    const V3 ao = ap + cross(wdp, r) + cross(wp, cross(wp, r));
+    const V3 wpT = rotT(a, s, c, wp);
+    const V3 wdpT = rotT(a, s, c, wdp);
+    const V3 e = unitv(a);
+    const V3 w = wpT + qd[i] * e;
+    const V3 wd = wdpT + qd[i] * cross(wpT, e) + qdd[i] * e;
+    const V3 acc = rotT(a, s, c, ao);
+    const V3 cm = mcom(M, i), Ii = minert(M, i);
+    const V3 ac = acc + cross(wd, cm) + cross(w, cross(w, cm));
+    F[i] = M.m[i] * ac;
+    Nm[i] = mulI(Ii, wd) + cross(w, mulI(Ii, w));
+    if (rec) {
+      rec[i].s = s;
+      rec[i].c = c;
+      rec[i].wpT = wpT;
+      rec[i].wdpT = wdpT;
+      rec[i].w = w;
+      rec[i].wd = wd;
+      rec[i].a = acc;
+    }
+    wp = w;
+    wdp = wd;
+    ap = acc;
+  }
+  V3 fc = vzero(), nc = vzero();
+#pragma unroll
+  for (int i = QM - 1; i >= 0; --i) {
+    V3 f = F[i];
+    V3 n = Nm[i] + cross(mcom(M, i), F[i]);
+    if (i < QM - 1) {
+      const int a1 = M.axis[i + 1];
+      const V3 Rf = rot(a1, sq[i + 1], cq[i + 1], fc);
+      const V3 Rn = rot(a1, sq[i + 1], cq[i + 1], nc);
+      f = f + Rf;
+      n = n + Rn + cross(v3(0.f, 0.f, M.L[i]), Rf);
+    }
+    tau[i] = comp(M.axis[i], n);
+    if (rec) {
+      rec[i].f = f;
+      rec[i].n = n;
+    }
+    fc = f;
+    nc = n;
+  }
+}
+
+// Directional derivative of ID at the stored value pass, along q_j
+// (wrt_qd = false) or qd_j (wrt_qd = true); qdd is held fixed.
+__device__ __forceinline__ void rnea_tangent(const DevModel& M, const LinkRec* R, const float* qd,
+                                             bool wrt_qd, int j, float* dtau) {
+  V3 Ft[QM], Nt[QM];
+  V3 wpt = vzero(), wdpt = vzero(), apt = vzero();
+#pragma unroll
+  for (int i = 0; i < QM; ++i) {
+    const int a = M.axis[i];
+    const float s = R[i].s, c = R[i].c;
+    const float qt = (!wrt_qd && i == j) ? 1.f : 0.f;
+    const float qdt = (wrt_qd && i == j) ? 1.f : 0.f;
+    const V3 wp = i > 0 ? R[i - 1].w : vzero();
+    const V3 r = v3(0.f, 0.f, i > 0 ? M.L[i - 1] : 0.f);
+    const V3 aot = apt + cross(wdpt, r) + cross(wpt, cross(wp, r)) + cross(wp, cross(wpt, r));
+    const V3 e = unitv(a);
+    const V3 Rwt = rotT(a, s, c, wpt) - qt * ecross(a, R[i].wpT);
+    const V3 wt = Rwt + qdt * e;
+    const V3 Rwdt = rotT(a, s, c, wdpt) - qt * ecross(a, R[i].wdpT);
+    const V3 wdt = Rwdt + qd[i] * cross(Rwt, e) + qdt * cross(R[i].wpT, e);
+    const V3 at = rotT(a, s, c, aot) - qt * ecross(a, R[i].a);
+    const V3 cm = mcom(M, i), Ii = minert(M, i);
+    const V3 w = R[i].w;
+    const V3 act = at + cross(wdt, cm) + cross(wt, cross(w, cm)) + cross(w, cross(wt, cm));
+    Ft[i] = M.m[i] * act;
+    Nt[i] = mulI(Ii, wdt) + cross(wt, mulI(Ii, w)) + cross(w, mulI(Ii, wt));
+    wpt = wt;
+    wdpt = wdt;
+    apt = at;
+  }
+  V3 fct = vzero(), nct = vzero();
+#pragma unroll
+  for (int i = QM - 1; i >= 0; --i) {
+    V3 ft = Ft[i];
+    V3 nt = Nt[i] + cross(mcom(M, i), Ft[i]);
+    if (i < QM - 1) {
+      const int a1 = M.axis[i + 1];
+      const float s1 = R[i + 1].s, c1 = R[i + 1].c;
+      const float q1t = (!wrt_qd && i + 1 == j) ? 1.f : 0.f;
+      const V3 Rft = rot(a1, s1, c1, fct) + q1t * ecross(a1, rot(a1, s1, c1, R[i + 1].f));
+      const V3 Rnt = rot(a1, s1, c1, nct) + q1t * ecross(a1, rot(a1, s1, c1, R[i + 1].n));
+      ft = ft + Rft;
+      nt = nt + Rnt + cross(v3(0.f, 0.f, M.L[i]), Rft);
+    }
+    dtau[i] = comp(M.axis[i], nt);
+    fct = ft;
+    nct = nt;
+  }
+}
+
+// Lower-triangular mass matrix by unit-acceleration RNEA columns (gravity and
+// velocity off); padded joints get a unit diagonal.  Ml[i*(i+1)/2 + j], j <= i.
+__device__ __forceinline__ void mass_matrix_lower(const DevModel& M, const float* sq,
+                                                  const float* cq, float* Ml) {
+  float z[QM], e[QM], col[QM];
+#pragma unroll
+  for (int i = 0; i < QM; ++i) z[i] = 0.f;
+#pragma unroll
+  for (int j = 0; j < QM; ++j) {
+#pragma unroll
+    for (int i = 0; i < QM; ++i) e[i] = (i == j) ? 1.f : 0.f;
+    rnea_value(M, sq, cq, z, e, 0.f, col, nullptr);
+#pragma unroll
+    for (int i = j; i < QM; ++i) Ml[i * (i + 1) / 2 + j] = col[i];
+  }
+#pragma unroll
+  for (int j = 0; j < QM; ++j)
+    if (j >= M.dof) Ml[j * (j + 1) / 2 + j] = 1.f;
+}
+
+// In-place Cholesky of a packed lower-triangular 7x7; returns false if not PD.
+__device__ __forceinline__ bool chol7(float* Ml) {
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < QM; ++j) {
+    float s = Ml[j * (j + 1) / 2 + j];
+#pragma unroll
+    for (int l = 0; l < j; ++l) s -= Ml[j * (j + 1) / 2 + l] * Ml[j * (j + 1) / 2 + l];
+    ok = ok && (s > 0.f);
+    const float d = sqrtf(fmaxf(s, 1e-30f));
+    const float inv = 1.f / d;
+    Ml[j * (j + 1) / 2 + j] = d;
+#pragma unroll
+    for (int i = j + 1; i < QM; ++i) {
+      float t = Ml[i * (i + 1) / 2 + j];
+#pragma unroll
+      for (int l = 0; l < j; ++l) t -= Ml[i * (i + 1) / 2 + l] * Ml[j * (j + 1) / 2 + l];
+      Ml[i * (i + 1) / 2 + j] = t * inv;
+    }
+  }
+  return ok;
+}
+
+// Solves (L L^T) x = b in place with the packed factor.
+__device__ __forceinline__ void chol7_solve(const float* Lf, float* b) {
+#pragma unroll
+  for (int i = 0; i < QM; ++i) {
+    float t = b[i];
+#pragma unroll
+    for (int l = 0; l < i; ++l) t -= Lf[i * (i + 1) / 2 + l] * b[l];
+    b[i] = t / Lf[i * (i + 1) / 2 + i];
+  }
+#pragma unroll
+  for (int i = QM - 1; i >= 0; --i) {
+    float t = b[i];
+#pragma unroll
+    for (int l = i + 1; l < QM; ++l) t -= Lf[l * (l + 1) / 2 + i] * b[l];
+    b[i] = t / Lf[i * (i + 1) / 2 + i];
+  }
+}
+
+// Semi-implicit Euler step (the build's f(x, u, h)): returns qdd as well.
+__device__ __forceinline__ bool forward_dynamics(const DevModel& M, const float* q, const float* qd,
+                                                 const float* u, float* qdd) {
+  float sq[QM], cq[QM], Ml[QM * (QM + 1) / 2], z[QM], b[QM];
+#pragma unroll
+  for (int i = 0; i < QM; ++i) {
+    sincosf(q[i], &sq[i], &cq[i]);
+    z[i] = 0.f;
+  }
+  mass_matrix_lower(M, sq, cq, Ml);
+  rnea_value(M, sq, cq, qd, z, M.g, b, nullptr);
+#pragma unroll
+  for (int i = 0; i < QM; ++i) qdd[i] = u[i] - b[i];
+  const bool ok = chol7(Ml);
+  chol7_solve(Ml, qdd);
+  return ok;
+}
+
+// End-effector position and its 3x7 Jacobian (row-major) in base coordinates.
+__device__ __forceinline__ void fk_ee(const DevModel& M, const float* q, float* p, float* J) {
+  float R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};  // row-major, columns are the frame axes
+  V3 pos = vzero();
+  V3 pj[QM], ej[QM];
+#pragma unroll
+  for (int i = 0; i < QM; ++i) {
+    if (i > 0) pos = pos + M.L[i - 1] * v3(R[2], R[5], R[8]);
+    float s, c;
+    sincosf(q[i], &s, &c);
+    const int a = M.axis[i];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float c0 = R[3 * r], c1 = R[3 * r + 1], c2 = R[3 * r + 2];
+      if (a == 2) {
+        R[3 * r] = c * c0 + s * c1;
+        R[3 * r + 1] = -s * c0 + c * c1;
+      } else if (a == 1) {
+        R[3 * r] = c * c0 - s * c2;
+        R[3 * r + 2] = s * c0 + c * c2;
+      } else {
+        R[3 * r + 1] = c * c1 + s * c2;
+        R[3 * r + 2] = -s * c1 + c * c2;
+      }
+    }
+    pj[i] = pos;
+    ej[i] = v3(R[a], R[3 + a], R[6 + a]);
+  }
+  const V3 pe = pos + M.L[QM - 1] * v3(R[2], R[5], R[8]);
+  p[0] = pe.x;
+  p[1] = pe.y;
+  p[2] = pe.z;
+  if (J) {
+#pragma unroll
+    for (int i = 0; i < QM; ++i) {
+      const V3 col = cross(ej[i], pe - pj[i]);
+      J[i] = col.x;
+      J[QM + i] = col.y;
+      J[2 * QM + i] = col.z;
+    }
+  }
+}
+
+}  // namespace gato

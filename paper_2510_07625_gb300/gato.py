@@ -1,0 +1,378 @@
+"""ctypes binding of ``include/gato.h`` (libgato.so).
+
+The functions ``gato_*`` below carry the C names and only marshal arguments;
+every step of the solver runs in the library's CUDA kernels.  ``Batch`` and
+``DeviceProblems`` are conveniences that keep device buffers in torch tensors
+(torch is used for memory and streams only).
+
+Loading fails loudly when libgato.so is missing; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import inputs as _inputs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgato.so")
+
+GATO_OK, GATO_E_INVALID, GATO_E_NOMEM, GATO_E_CUDA, GATO_E_TIMEOUT, GATO_E_BUSY = 0, -1, -2, -3, -4, -5
+SOLVE_CONVERGED, SOLVE_MAXITER, SOLVE_LSFAIL, SOLVE_PCG_MAXIT, SOLVE_NONFINITE = 1, 2, 4, 8, 16
+COST_JOINT, COST_EE = 0, 1
+PRECOND_STAIR, PRECOND_JACOBI = 0, 1
+MEM_HOST, MEM_DEVICE = 0, 1
+
+EXPORTED = (
+    "gato_default_params", "gato_create_batch", "gato_solve", "gato_step", "gato_solve_plain",
+    "gato_sync", "gato_get_results", "gato_destroy_batch", "gato_status_string", "gato_last_error",
+    "gato_last_transfer_bytes", "gato_debug_plain_stage", "gato_debug_layout",
+)
+LAYOUT_NAMES = ("X", "U", "dX", "dU", "Fq", "Fv", "Minv", "qdd", "dTau", "Qinv", "Rinv", "q", "r",
+                "c", "Jk", "Linv", "links", "D", "L", "P", "vec", "scal")
+
+
+class ModelDesc(C.Structure):
+    _fields_ = [("dof", C.c_int32), ("axis", C.c_int32 * 7), ("link_len", C.c_float * 7),
+                ("mass", C.c_float * 7), ("com", C.c_float * 21), ("inertia", C.c_float * 21),
+                ("gravity", C.c_float)]
+
+
+class SolverParams(C.Structure):
+    _fields_ = [("mu", C.c_float), ("beta", C.c_float), ("n_alpha", C.c_int32),
+                ("pcg_eps", C.c_float), ("pcg_max_iter", C.c_int32), ("precond", C.c_int32),
+                ("kkt_tol", C.c_float)]
+
+
+class BatchDesc(C.Structure):
+    _fields_ = [("max_batch", C.c_int32), ("max_horizon", C.c_int32), ("n_models", C.c_int32),
+                ("models", C.POINTER(ModelDesc)), ("params", SolverParams)]
+
+
+class Problem(C.Structure):
+    _fields_ = [("model", C.c_int32), ("N", C.c_int32), ("dt", C.c_float),
+                ("cost_kind", C.c_int32), ("w", C.c_float * 6), ("mem", C.c_int32),
+                ("x_s", C.c_void_p), ("x_ref", C.c_void_p), ("ee_ref", C.c_void_p),
+                ("X", C.c_void_p), ("U", C.c_void_p), ("lam", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("flags", C.c_int32), ("sqp_iters", C.c_int32), ("pcg_iters", C.c_int32),
+                ("kkt_residual", C.c_float), ("merit", C.c_float)]
+
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Loads libgato.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_2510_07625_gb300.build` (needs nvcc)")
+    L = C.CDLL(LIB_PATH)
+    bp = C.c_void_p
+    L.gato_default_params.argtypes = [C.POINTER(SolverParams)]
+    L.gato_default_params.restype = None
+    L.gato_create_batch.argtypes = [C.POINTER(BatchDesc), C.c_void_p, C.POINTER(C.c_void_p)]
+    L.gato_create_batch.restype = C.c_int
+    for name in ("gato_solve", "gato_solve_plain"):
+        f = getattr(L, name)
+        f.argtypes = [bp, C.POINTER(Problem), C.c_int32, C.c_int32, C.POINTER(Result)]
+        f.restype = C.c_int
+    L.gato_step.argtypes = [bp, C.POINTER(Problem), C.c_int32, C.POINTER(Result)]
+    L.gato_step.restype = C.c_int
+    L.gato_sync.argtypes = [bp, C.c_int64]
+    L.gato_sync.restype = C.c_int
+    L.gato_get_results.argtypes = [bp, C.POINTER(Result), C.c_int32]
+    L.gato_get_results.restype = C.c_int
+    L.gato_destroy_batch.argtypes = [bp]
+    L.gato_destroy_batch.restype = None
+    L.gato_status_string.argtypes = [C.c_int]
+    L.gato_status_string.restype = C.c_char_p
+    L.gato_last_error.argtypes = [bp]
+    L.gato_last_error.restype = C.c_char_p
+    L.gato_last_transfer_bytes.argtypes = [bp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    L.gato_last_transfer_bytes.restype = C.c_int
+    L.gato_debug_plain_stage.argtypes = [bp, C.POINTER(Problem), C.c_int32, C.c_void_p, C.c_int64]
+    L.gato_debug_plain_stage.restype = C.c_int
+    L.gato_debug_layout.argtypes = [bp, C.POINTER(C.c_int64)]
+    L.gato_debug_layout.restype = C.c_int64
+    _lib = L
+    return L
+
+
+class GatoError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+# ----------------------------------------------------------- C-named wrappers
+
+def gato_default_params() -> SolverParams:
+    p = SolverParams()
+    load().gato_default_params(C.byref(p))
+    return p
+
+
+def gato_status_string(s: int) -> str:
+    return load().gato_status_string(s).decode()
+
+
+def gato_create_batch(desc: BatchDesc, stream: int | None = None) -> int:
+    h = C.c_void_p()
+    s = load().gato_create_batch(C.byref(desc), C.c_void_p(stream or 0), C.byref(h))
+    if s != GATO_OK:
+        raise GatoError(s, f"gato_create_batch: {gato_status_string(s)}")
+    return h.value
+
+
+def _check(handle, s, what):
+    if s != GATO_OK:
+        msg = load().gato_last_error(C.c_void_p(handle)).decode()
+        raise GatoError(s, f"{what}: {gato_status_string(s)}: {msg}")
+
+
+def gato_solve(handle, problems, n, iters, results=None):
+    r = results if results is not None else None
+    s = load().gato_solve(C.c_void_p(handle), problems, n, iters, r)
+    _check(handle, s, "gato_solve")
+
+
+def gato_step(handle, problems, n, results=None):
+    s = load().gato_step(C.c_void_p(handle), problems, n, results)
+    _check(handle, s, "gato_step")
+
+
+def gato_solve_plain(handle, problems, n, iters, results=None):
+    s = load().gato_solve_plain(C.c_void_p(handle), problems, n, iters, results)
+    _check(handle, s, "gato_solve_plain")
+
+
+def gato_sync(handle, timeout_us=-1) -> int:
+    s = load().gato_sync(C.c_void_p(handle), timeout_us)
+    if s not in (GATO_OK, GATO_E_TIMEOUT):
+        _check(handle, s, "gato_sync")
+    return s
+
+
+def gato_get_results(handle, n):
+    out = (Result * n)()
+    s = load().gato_get_results(C.c_void_p(handle), out, n)
+    _check(handle, s, "gato_get_results")
+    return out
+
+
+def gato_destroy_batch(handle):
+    load().gato_destroy_batch(C.c_void_p(handle))
+
+
+def gato_last_error(handle) -> str:
+    return load().gato_last_error(C.c_void_p(handle)).decode()
+
+
+def gato_last_transfer_bytes(handle):
+    a, b = C.c_int64(), C.c_int64()
+    load().gato_last_transfer_bytes(C.c_void_p(handle), C.byref(a), C.byref(b))
+    return a.value, b.value
+
+
+def gato_debug_layout(handle):
+    off = (C.c_int64 * 22)()
+    total = load().gato_debug_layout(C.c_void_p(handle), off)
+    return total, dict(zip(LAYOUT_NAMES, list(off)))
+
+
+def gato_debug_plain_stage(handle, problems, stop_stage):
+    total, off = gato_debug_layout(handle)
+    buf = np.zeros(total, np.float32)
+    s = load().gato_debug_plain_stage(C.c_void_p(handle), problems, stop_stage,
+                                      buf.ctypes.data_as(C.c_void_p), total)
+    _check(handle, s, "gato_debug_plain_stage")
+    return buf, off
+
+
+# ------------------------------------------------------------- conveniences
+
+def model_desc(m) -> ModelDesc:
+    d = ModelDesc()
+    d.dof = m.dof
+    for i in range(7):
+        d.axis[i] = m.axis[i] if i < m.dof else 2
+        d.link_len[i] = m.link_len[i] if i < m.dof else 0.0
+        d.mass[i] = m.mass[i] if i < m.dof else 0.0
+    for i in range(21):
+        d.com[i] = m.com[i] if i < 3 * m.dof else 0.0
+        d.inertia[i] = m.inertia[i] if i < 3 * m.dof else 0.0
+    d.gravity = m.gravity
+    return d
+
+
+def results_to_dicts(res, n):
+    return [dict(flags=res[i].flags, sqp_iters=res[i].sqp_iters, pcg_iters=res[i].pcg_iters,
+                 kkt=res[i].kkt_residual, merit=res[i].merit) for i in range(n)]
+
+
+class Batch:
+    """Owns a gato_batch handle for a fixed set of models."""
+
+    def __init__(self, models, max_batch, max_horizon, params: SolverParams | None = None,
+                 stream: int | None = None, **overrides):
+        self.models = list(models)
+        self._mdesc = (ModelDesc * len(self.models))(*[model_desc(m) for m in self.models])
+        p = params or gato_default_params()
+        for k, v in overrides.items():
+            setattr(p, k, v)
+        self.params = p
+        d = BatchDesc(max_batch, max_horizon, len(self.models),
+                      C.cast(self._mdesc, C.POINTER(ModelDesc)), p)
+        self.handle = gato_create_batch(d, stream)
+        self.max_batch = max_batch
+        self.max_horizon = max_horizon
+
+    def model_index(self, m):
+        for i, mm in enumerate(self.models):
+            if mm == m:
+                return i
+        raise KeyError(f"model {m.name} not in batch")
+
+    def solve(self, problems, n, iters, plain=False):
+        res = (Result * n)()
+        f = gato_solve_plain if plain else gato_solve
+        f(self.handle, problems, n, iters, res)
+        return res
+
+    def solve_async(self, problems, n, iters):
+        gato_solve(self.handle, problems, n, iters, None)
+
+    def sync(self, timeout_us=-1):
+        return gato_sync(self.handle, timeout_us)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            gato_destroy_batch(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cold_start_arrays(prob):
+    """Initial guess of reading c14: X_k = x_s, U = 0, lambda = 0 (float32)."""
+    nx, nu = 2 * prob.model.dof, prob.model.dof
+    X = np.tile(np.asarray(prob.x_s, np.float32), (prob.N + 1, 1))
+    U = np.zeros((prob.N, nu), np.float32)
+    lam = np.zeros((prob.N + 1, nx), np.float32)
+    return X, U, lam
+
+
+class HostProblems:
+    """gato_problem array over numpy (host) buffers; X/U/lambda updated in place."""
+
+    def __init__(self, batch: Batch, probs, X=None, U=None, lam=None):
+        self.probs = list(probs)
+        n = len(self.probs)
+        self.arr = (Problem * n)()
+        self.keep = []
+        self.X, self.U, self.lam = [], [], []
+        for i, p in enumerate(self.probs):
+            X0, U0, L0 = cold_start_arrays(p)
+            Xi = np.ascontiguousarray(X[i] if X is not None else X0, np.float32)
+            Ui = np.ascontiguousarray(U[i] if U is not None else U0, np.float32)
+            Li = np.ascontiguousarray(lam[i] if lam is not None else L0, np.float32)
+            xs = np.ascontiguousarray(p.x_s, np.float32)
+            ref = np.ascontiguousarray(p.x_ref if p.cost_kind == COST_JOINT else p.ee_ref, np.float32)
+            self.keep += [xs, ref]
+            self.X.append(Xi)
+            self.U.append(Ui)
+            self.lam.append(Li)
+            a = self.arr[i]
+            a.model = batch.model_index(p.model)
+            a.N = p.N
+            a.dt = p.dt
+            a.cost_kind = p.cost_kind
+            for k in range(6):
+                a.w[k] = p.w[k]
+            a.mem = MEM_HOST
+            a.x_s = xs.ctypes.data
+            a.x_ref = ref.ctypes.data if p.cost_kind == COST_JOINT else None
+            a.ee_ref = ref.ctypes.data if p.cost_kind == COST_EE else None
+            a.X = Xi.ctypes.data
+            a.U = Ui.ctypes.data
+            a.lam = Li.ctypes.data
+        self.n = n
+
+
+class DeviceProblems:
+    """gato_problem array over torch CUDA tensors (padded [B, Nmax+1, nx] slabs)."""
+
+    def __init__(self, batch: Batch, probs, device="cuda"):
+        import torch
+
+        self.torch = torch
+        self.probs = list(probs)
+        n = len(self.probs)
+        Nmax = max(p.N for p in self.probs)
+        self.Nmax = Nmax
+        f32 = torch.float32
+        self.x_s = torch.zeros(n, 14, dtype=f32, device=device)
+        self.ref = torch.zeros(n, (Nmax + 1) * 14, dtype=f32, device=device)
+        self.X = torch.zeros(n, (Nmax + 1) * 14, dtype=f32, device=device)
+        self.U = torch.zeros(n, Nmax * 7, dtype=f32, device=device)
+        self.lam = torch.zeros(n, (Nmax + 1) * 14, dtype=f32, device=device)
+        self.arr = (Problem * n)()
+        hx = np.zeros((n, 14), np.float32)
+        href = np.zeros((n, (Nmax + 1) * 14), np.float32)
+        hX = np.zeros((n, (Nmax + 1) * 14), np.float32)
+        for i, p in enumerate(self.probs):
+            nx = 2 * p.model.dof
+            hx[i, :nx] = p.x_s
+            r = p.x_ref if p.cost_kind == COST_JOINT else p.ee_ref
+            r = np.asarray(r, np.float32).ravel()
+            href[i, :r.size] = r
+            X0, _, _ = cold_start_arrays(p)
+            hX[i, :X0.size] = X0.ravel()
+        self.x_s.copy_(torch.from_numpy(hx))
+        self.ref.copy_(torch.from_numpy(href))
+        self.X.copy_(torch.from_numpy(hX))
+        es = 4
+        for i, p in enumerate(self.probs):
+            a = self.arr[i]
+            a.model = batch.model_index(p.model)
+            a.N = p.N
+            a.dt = p.dt
+            a.cost_kind = p.cost_kind
+            for k in range(6):
+                a.w[k] = p.w[k]
+            a.mem = MEM_DEVICE
+            a.x_s = self.x_s.data_ptr() + i * 14 * es
+            rp = self.ref.data_ptr() + i * (Nmax + 1) * 14 * es
+            a.x_ref = rp if p.cost_kind == COST_JOINT else None
+            a.ee_ref = rp if p.cost_kind == COST_EE else None
+            a.X = self.X.data_ptr() + i * (Nmax + 1) * 14 * es
+            a.U = self.U.data_ptr() + i * Nmax * 7 * es
+            a.lam = self.lam.data_ptr() + i * (Nmax + 1) * 14 * es
+        self.n = n
+        self._X0 = self.X.clone()
+
+    def reset(self):
+        """Back to the cold start (X = x_s, U = 0, lambda = 0)."""
+        self.X.copy_(self._X0)
+        self.U.zero_()
+        self.lam.zero_()
+
+    def solution(self, i):
+        p = self.probs[i]
+        nx, nu = 2 * p.model.dof, p.model.dof
+        X = self.X[i, : (p.N + 1) * nx].reshape(p.N + 1, nx).double().cpu().numpy()
+        U = self.U[i, : p.N * nu].reshape(p.N, nu).double().cpu().numpy()
+        L = self.lam[i, : (p.N + 1) * nx].reshape(p.N + 1, nx).double().cpu().numpy()
+        return X, U, L

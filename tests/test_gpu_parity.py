@@ -1,0 +1,191 @@
+"""End-to-end parity of the fused CUDA SQP against the FP64 oracle, via the C ABI.
+
+Tolerances (the derivation is written out in DESIGN.md, "Parity"):
+
+* Converged solves: X, U within 1e-4 relative (||.||_inf / max(1, ||.||_inf))
+  and the KKT residuals of both final iterates, evaluated by the oracle in FP64,
+  within 1e-5 of each other.  A converged iterate is a fixed point of the SQP
+  map, so it does not depend on the rounding of the path that reached it.
+* Single SQP steps from the same iterate: the step computed in FP32 differs
+  from the FP64 one by the QP's sensitivity to FP32 rounding of its own data.
+  The oracle measures that sensitivity at the same iterate (its QP solved with
+  S and rhs rounded to FP32) and the test allows a fixed multiple of it.
+* The fused kernel and the plain form run the same stage code in the same
+  order: bitwise equal.  A solve's result does not depend on its batch.
+"""
+import numpy as np
+import pytest
+
+from paper_2510_07625_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_07625_gb300 import build, gato
+
+    build.build_library()
+    gato.load()
+    return gato
+
+
+def rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / max(1.0, np.abs(b).max())
+
+
+def gpu_solve(G, probs, iters, plain=False, X=None, U=None, lam=None, **prm):
+    models = []
+    for p in probs:
+        if p.model not in models:
+            models.append(p.model)
+    B = G.Batch(models, len(probs), max(p.N for p in probs), **prm)
+    hp = G.HostProblems(B, probs, X=X, U=U, lam=lam)
+    res = B.solve(hp.arr, hp.n, iters, plain=plain)
+    out = G.results_to_dicts(res, hp.n)
+    B.close()
+    return [dict(X=hp.X[i].astype(np.float64), U=hp.U[i].astype(np.float64),
+                 lam=hp.lam[i].astype(np.float64), **out[i]) for i in range(hp.n)]
+
+
+def qp_sensitivity(oracle, prob, X, U, lam):
+    """Relative change of the QP step when S and rhs are rounded to FP32."""
+    from tests.test_oracle_kkt import blocks_to_dense
+    S = oracle.schur(prob, X, U)
+    lin = oracle.linearize(prob, X, U)
+
+    def step(Sd, Ss, rhs):
+        nu = oracle.blocktri_solve(Sd, Ss, rhs)
+        t = lin["q"] + nu
+        t[:-1] -= np.einsum("kji,kj->ki", lin["A"], nu[1:])
+        dX = -np.einsum("kij,kj->ki", np.linalg.inv(lin["Q"]), t)
+        s = lin["r"] - np.einsum("kji,kj->ki", lin["B"], nu[1:])
+        dU = -np.einsum("kij,kj->ki", np.linalg.inv(lin["R"]), s)
+        return np.concatenate([dX.ravel(), dU.ravel()])
+    f = lambda a: a.astype(np.float32).astype(np.float64)
+    d0 = step(S["Sd"], S["Ss"], S["rhs"])
+    d1 = step(f(S["Sd"]), f(S["Ss"]), f(S["rhs"]))
+    return np.abs(d1 - d0).max() / np.abs(d0).max(), np.abs(d0).max()
+
+
+def test_fused_equals_plain_bitwise(G):
+    probs = [I.joint_problem(0, I.arm7(), N=16), I.ee_problem(1, I.arm7(), N=12),
+             I.joint_problem(2, I.arm6(), N=9)]
+    for p in probs:
+        a = gpu_solve(G, [p], 3)[0]
+        b = gpu_solve(G, [p], 3, plain=True)[0]
+        np.testing.assert_array_equal(a["X"], b["X"])
+        np.testing.assert_array_equal(a["U"], b["U"])
+        np.testing.assert_array_equal(a["lam"], b["lam"])
+        assert (a["flags"], a["sqp_iters"], a["pcg_iters"]) == (b["flags"], b["sqp_iters"], b["pcg_iters"])
+
+
+def test_batch_invariance_bitwise(G):
+    probs = I.config_fixed_batch(B=8, N=20)
+    together = gpu_solve(G, probs, 3)
+    for i in (0, 5):
+        alone = gpu_solve(G, [probs[i]], 3)[0]
+        np.testing.assert_array_equal(alone["X"], together[i]["X"])
+        np.testing.assert_array_equal(alone["U"], together[i]["U"])
+
+
+def _per_step_parity(G, oracle, prob, iters, factor=30.0):
+    """Each GPU SQP step against the oracle step from the same iterate."""
+    X, U, lam = oracle.cold_start(prob)
+    worst = 0.0
+    for it in range(iters):
+        g = gpu_solve(G, [prob], 1, X=[X], U=[U], lam=[lam])[0]
+        o = oracle.solve(prob, max_iter=1, X=X, U=U, lam=lam)
+        sens, dmax = qp_sensitivity(oracle, prob, X, U, lam)
+        if g["sqp_iters"] == 1 and len(o["alpha_idx"]) == 1 and o["alpha_idx"][0] >= 0:
+            a = 0.5 ** o["alpha_idx"][0]
+            tol = 1e-4 * max(1.0, np.abs(o["X"]).max()) + factor * a * sens * dmax
+            errX = np.abs(g["X"] - o["X"]).max()
+            errU = np.abs(g["U"] - o["U"]).max()
+            if np.abs(g["X"] - X).max() > 0:  # GPU accepted a step
+                gap = o["merit_gap"][0]
+                if gap > 1e-5:  # not a near-tie: same alpha expected
+                    assert errX <= tol and errU <= tol * max(1.0, np.abs(o["U"]).max()), \
+                        (it, errX, errU, tol, sens)
+                worst = max(worst, errX / tol)
+        X, U, lam = g["X"], g["U"], g["lam"]
+    return worst
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_single_solve_per_step_parity(G, oracle, seed):
+    """The single-solve workload (7-DoF, N=32, dt=0.01), 5 SQP iterations."""
+    _per_step_parity(G, oracle, I.joint_problem(seed, I.arm7(), 32, 0.01), 5)
+
+
+def test_ee_per_step_parity(G, oracle):
+    _per_step_parity(G, oracle, I.ee_problem(3, I.arm7(), 24, 0.01), 4)
+
+
+def test_arm6_per_step_parity(G, oracle):
+    _per_step_parity(G, oracle, I.joint_problem(5, I.arm6(), 20, 0.01), 4)
+
+
+def _converged_parity(G, oracle, probs, iters, tol=1e-4):
+    gs = gpu_solve(G, probs, iters, kkt_tol=1e-5)
+    for p, g in zip(probs, gs):
+        o = oracle.solve(p, max_iter=iters + 20, kkt_tol=1e-9)
+        assert o["flags"] & oracle.FLAG_CONVERGED, "oracle did not converge"
+        assert g["flags"] & 1, (p.seed, g)
+        eX, eU = rel(g["X"], o["X"]), rel(g["U"], o["U"])
+        assert eX <= tol and eU <= tol, (p.seed, p.N, eX, eU)
+        k_g = oracle.kkt_residual(p, g["X"], g["U"], g["lam"])
+        k_o = oracle.kkt_residual(p, o["X"], o["U"], o["lam"])
+        assert abs(k_g - k_o) <= 1e-5, (k_g, k_o)
+
+
+def test_converged_parity_single_solve(G, oracle):
+    _converged_parity(G, oracle, [I.joint_problem(0, I.arm7(), 32, 0.01)], 40)
+
+
+def test_converged_parity_fixed_batch(G, oracle):
+    probs = [I.joint_problem(s, I.arm7(), 32, 0.01) for s in range(8)]
+    _converged_parity(G, oracle, probs, 40)
+
+
+def test_converged_parity_uneven_mix(G, oracle):
+    probs = I.config_uneven(B=6)
+    _converged_parity(G, oracle, probs, 60)
+
+
+def test_host_and_device_paths_agree(G):
+    import torch
+
+    probs = [I.joint_problem(s, I.arm7(), 20, 0.01) for s in range(3)] + [I.ee_problem(4, I.arm7(), 20)]
+    host = gpu_solve(G, probs, 2)
+    B = G.Batch([I.arm7()], len(probs), 20)
+    dp = G.DeviceProblems(B, probs)
+    B.solve(dp.arr, dp.n, 2)
+    torch.cuda.synchronize()
+    for i in range(len(probs)):
+        X, U, L = dp.solution(i)
+        np.testing.assert_array_equal(X, host[i]["X"])
+        np.testing.assert_array_equal(U, host[i]["U"])
+    B.close()
+
+
+def test_edge_cases(G):
+    # N = 1, Jacobi preconditioner
+    p = I.joint_problem(1, I.arm7(), 1, 0.01)
+    r = gpu_solve(G, [p], 3, precond=1)[0]
+    assert r["sqp_iters"] == 3 and not (r["flags"] & 16)
+    # non-finite initial state is rejected on the host (nothing launched)
+    q = I.joint_problem(2, I.arm7(), 8, 0.01)
+    q.x_s = q.x_s.copy()
+    q.x_s[3] = np.nan
+    with pytest.raises(G.GatoError) as e:
+        gpu_solve(G, [q], 1)
+    assert e.value.status == G.GATO_E_INVALID
+    # the largest horizon the batch allows, blocks outside shared memory
+    big = I.joint_problem(3, I.arm7(), 128, 0.01)
+    r = gpu_solve(G, [big], 2)[0]
+    assert r["sqp_iters"] == 2 and not (r["flags"] & 16)

@@ -1,0 +1,202 @@
+"""Stage-by-stage parity of the CUDA path against the FP64 oracle (Alg. 1 stages).
+
+Each test runs the plain form of one solve through the C ABI up to a stage,
+reads that solve's workspace back, and compares the stage's output with the
+oracle's same quantity on the same inputs.  Tolerances are FP32 ones: the
+dynamics Jacobians go through M^-1 (condition ~1e3), so they get 1e-4
+relative to the block's largest entry; pure recombinations (recovery, merit)
+of GPU-produced data are checked against the oracle's formula applied to
+that data, in FP64, at 1e-5.
+"""
+import numpy as np
+import pytest
+
+from paper_2510_07625_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+VS, US, BS, XM = 16, 8, 199, 14
+
+
+def pad_idx(dof):
+    return list(range(dof)) + [7 + i for i in range(dof)]
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_07625_gb300 import build, gato
+
+    build.build_library()
+    gato.load()
+    return gato
+
+
+def stage(G, prob, st, X=None, U=None, lam=None, **prm):
+    B = G.Batch([prob.model], 1, prob.N, **prm)
+    hp = G.HostProblems(B, [prob],
+                        X=None if X is None else [X.astype(np.float32)],
+                        U=None if U is None else [U.astype(np.float32)],
+                        lam=None if lam is None else [lam.astype(np.float32)])
+    buf, off = G.gato_debug_plain_stage(B.handle, hp.arr, st)
+    total, _ = G.gato_debug_layout(B.handle)
+    B.close()
+    return buf.astype(np.float64), off, prob.N
+
+
+def knots(buf, off, name, K, stride, n):
+    return buf[off[name]:off[name] + K * stride].reshape(K, stride)[:, :n]
+
+
+def block(buf, off, name, K):
+    a = buf[off[name]:off[name] + K * BS].reshape(K, BS)[:, :196].reshape(K, XM, XM)
+    return np.transpose(a, (0, 2, 1))  # stored column-major
+
+
+def vec(buf, off, k_max, idx):
+    VV = (k_max + 1) * VS
+    base = off["vec"] + idx * VV
+    return buf[base:base + VV].reshape(k_max + 1, VS)[:, :XM]
+
+
+PROBS = [
+    ("arm7_joint", lambda: I.joint_problem(0, I.arm7(), N=8, dt=0.01)),
+    ("arm6_joint", lambda: I.joint_problem(3, I.arm6(), N=6, dt=0.02)),
+    ("arm7_ee", lambda: I.ee_problem(2, I.arm7(), N=7, dt=0.01)),
+]
+
+
+def midpoint(oracle, prob):
+    r = oracle.solve(prob, max_iter=2)
+    return r["X"], r["U"], r["lam"]
+
+
+@pytest.mark.parametrize("name,mk", PROBS, ids=[p[0] for p in PROBS])
+def test_linearisation_stage(G, oracle, name, mk):
+    prob = mk()
+    X, U, lam = midpoint(oracle, prob)
+    buf, off, N = stage(G, prob, 6, X, U, lam)
+    K = N + 1
+    dof = prob.model.dof
+    pi = pad_idx(dof)
+    lin = oracle.linearize(prob, X, U)
+    h = prob.dt
+    Fq = buf[off["Fq"]:off["Fq"] + N * 49].reshape(N, 7, 7)
+    Fv = buf[off["Fv"]:off["Fv"] + N * 49].reshape(N, 7, 7)
+    Mi = buf[off["Minv"]:off["Minv"] + N * 49].reshape(N, 7, 7)
+    I7 = np.eye(7)
+    for k in range(N):
+        A = np.block([[I7 + h * h * Fq[k], h * I7 + h * h * Fv[k]], [h * Fq[k], I7 + h * Fv[k]]])
+        Bm = np.vstack([h * h * Mi[k], h * Mi[k]])
+        A = A[np.ix_(pi, pi)]
+        Bm = Bm[np.ix_(pi, list(range(dof)))]
+        sA = np.abs(lin["A"][k]).max()
+        sB = np.abs(lin["B"][k]).max()
+        np.testing.assert_allclose(A, lin["A"][k], atol=1e-4 * sA, rtol=0)
+        np.testing.assert_allclose(Bm, lin["B"][k], atol=1e-4 * sB, rtol=0)
+    c = knots(buf, off, "c", K, VS, XM)[:, pi]
+    np.testing.assert_allclose(c, lin["c"], atol=2e-5 * max(1, np.abs(X).max()), rtol=0)
+    q = knots(buf, off, "q", K, VS, XM)[:, pi]
+    np.testing.assert_allclose(q, lin["q"], atol=1e-4 * max(1, np.abs(lin["q"]).max()), rtol=0)
+    r = knots(buf, off, "r", N, US, dof)
+    np.testing.assert_allclose(r, lin["r"], atol=1e-5 * max(1, np.abs(lin["r"]).max()), rtol=0)
+    Qi = buf[off["Qinv"]:off["Qinv"] + K * 56].reshape(K, 56)
+    for k in range(K):
+        Qfull = np.zeros((14, 14))
+        Qfull[:7, :7] = Qi[k, :49].reshape(7, 7)
+        Qfull[7:, 7:] = np.diag(Qi[k, 49:56])
+        want = np.linalg.inv(lin["Q"][k])
+        np.testing.assert_allclose(Qfull[np.ix_(pi, pi)], want, atol=2e-4 * np.abs(want).max(), rtol=0)
+    # KKT residual and merit of the current iterate, against the oracle (FP64)
+    scal = buf[off["scal"]:off["scal"] + 64]
+    kkt_ora = oracle.kkt_residual(prob, X, U, lam)
+    assert abs(scal[0] - kkt_ora) <= 1e-4 * max(1.0, kkt_ora)
+    m_ora = oracle.merit(prob, X, U)
+    assert abs(scal[1] - m_ora) <= 1e-5 * m_ora
+
+
+@pytest.mark.parametrize("name,mk", PROBS, ids=[p[0] for p in PROBS])
+def test_schur_and_preconditioner_stage(G, oracle, name, mk):
+    prob = mk()
+    X, U, lam = midpoint(oracle, prob)
+    buf, off, N = stage(G, prob, 8, X, U, lam)
+    K = N + 1
+    pi = pad_idx(prob.model.dof)
+    S = oracle.schur(prob, X, U)
+    D = block(buf, off, "D", K)
+    L = block(buf, off, "L", K)
+    P = block(buf, off, "P", K)
+    rhs = vec(buf, off, prob.N, 8)
+    for k in range(K):
+        Dk = D[k][np.ix_(pi, pi)]
+        np.testing.assert_allclose(Dk, S["Sd"][k], atol=1e-4 * np.abs(S["Sd"][k]).max(), rtol=0)
+        # the GPU's D^-1 inverts the GPU's own D to FP32 working accuracy
+        Dg, Pg = D[k][np.ix_(pi, pi)], P[k][np.ix_(pi, pi)]
+        kappa = np.linalg.cond(Dg)
+        assert np.abs(Pg @ Dg - np.eye(len(pi))).max() < 50 * kappa * 6e-8
+        if k > 0:
+            Lk = L[k][np.ix_(pi, pi)]
+            np.testing.assert_allclose(Lk, S["Ss"][k - 1], atol=1e-4 * np.abs(S["Ss"][k - 1]).max(), rtol=0)
+    np.testing.assert_allclose(rhs[:, pi], S["rhs"], atol=1e-4 * np.abs(S["rhs"]).max(), rtol=0)
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+@pytest.mark.parametrize("name,mk", PROBS, ids=[p[0] for p in PROBS])
+def test_pcg_recovery_and_line_search_stages(G, oracle, name, mk, precond):
+    prob = mk()
+    X, U, lam = midpoint(oracle, prob)
+    N, K = prob.N, prob.N + 1
+    dof = prob.model.dof
+    pi = pad_idx(dof)
+    S = oracle.schur(prob, X, U, precond=precond)
+    buf, off, _ = stage(G, prob, 11, X, U, lam, precond=precond)
+    nu = vec(buf, off, N, 0)[:, pi]
+    # PCG: the GPU multiplier meets the stopping rule on the oracle's FP64 system
+    from tests.test_oracle_kkt import blocks_to_dense
+    Sd = blocks_to_dense(S["Sd"], S["Ss"])
+    Pm = blocks_to_dense(S["Pd"], S["Ps"])
+    r0 = S["rhs"].ravel() - Sd @ lam.ravel()
+    r = S["rhs"].ravel() - Sd @ nu.ravel()
+    rel = np.sqrt(abs(r @ Pm @ r) / (r0 @ Pm @ r0))
+    exact = np.linalg.solve(Sd, S["rhs"].ravel())
+    err_nu = np.abs(nu.ravel() - exact).max() / np.abs(exact).max()
+    assert rel < 5e-3, rel
+    assert err_nu < 5e-3, err_nu
+    # recovery: dZ = -G^-1 (g + C^T nu) on the GPU's own linearisation and nu, in FP64
+    h = prob.dt
+    Fq = buf[off["Fq"]:off["Fq"] + N * 49].reshape(N, 7, 7)
+    Fv = buf[off["Fv"]:off["Fv"] + N * 49].reshape(N, 7, 7)
+    Mi = buf[off["Minv"]:off["Minv"] + N * 49].reshape(N, 7, 7)
+    Qi = buf[off["Qinv"]:off["Qinv"] + K * 56].reshape(K, 56)
+    Ri = knots(buf, off, "Rinv", N, US, 7)
+    qg = knots(buf, off, "q", K, VS, XM)
+    rg = knots(buf, off, "r", N, US, 7)
+    nup = vec(buf, off, N, 0)
+    I7 = np.eye(7)
+    dX_want = np.zeros((K, XM))
+    dU_want = np.zeros((N, 7))
+    for k in range(K):
+        t = qg[k] + nup[k]
+        if k < N:
+            A = np.block([[I7 + h * h * Fq[k], h * I7 + h * h * Fv[k]], [h * Fq[k], I7 + h * Fv[k]]])
+            Bm = np.vstack([h * h * Mi[k], h * Mi[k]])
+            t = t - A.T @ nup[k + 1]
+            dU_want[k] = -Ri[k] * (rg[k] - Bm.T @ nup[k + 1])
+        Qf = np.zeros((14, 14))
+        Qf[:7, :7] = Qi[k, :49].reshape(7, 7)
+        Qf[7:, 7:] = np.diag(Qi[k, 49:])
+        dX_want[k] = -Qf @ t
+    dX = knots(buf, off, "dX", K, VS, XM)
+    dU = knots(buf, off, "dU", N, US, 7)
+    np.testing.assert_allclose(dX, dX_want, atol=1e-5 * np.abs(dX_want).max(), rtol=0)
+    np.testing.assert_allclose(dU, dU_want, atol=1e-5 * np.abs(dU_want).max(), rtol=0)
+    dX, dU = dX[:, pi], dU[:, :dof]
+    # line search: trial merits of the GPU step, against the oracle merit in FP64
+    scal = buf[off["scal"]:off["scal"] + 64]
+    for a in range(8):
+        al = 0.5 ** a
+        m_ora = oracle.merit(prob, X + al * dX, U + al * dU)
+        assert abs(scal[16 + a] - m_ora) <= 2e-5 * m_ora, (a, scal[16 + a], m_ora)
