@@ -1,0 +1,366 @@
+"""Benchmark of the batched SQP solver on GB300 (one JSON line on stdout).
+
+Workload (the figure-eight sweep at N=64, 7-DoF, per the headline metric):
+B=256 end-effector tracking solves, N=64 knots, dt=0.01 s, 10 SQP iterations
+per solve call, FP32 with compensated PCG dots and merit sums.  A "step" is one
+gato_solve call over the whole batch from the cold start.  Extra keys report
+the p50/p99 latency of the B=32 call (10 and 3 SQP iterations) and the plain
+one-solve-per-launch GPU form at B=32.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle (the method written from the paper,
+plain C++) on the host cores on a bounded sample of the same workload.
+Multi-GPU runs are independent replicas (each rank its own batch; no
+collective on the data path); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SQP solves/s and p50/p99 latency at B=32-256 (7-DoF, N=64) vs plain GPU form"
+B_MAIN, N_MAIN, ITERS = 256, 64, 10
+B_LAT = 32
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# --------------------------------------------------------------- FLOP model
+
+def flops_per_solve(N, sqp_iters, pcg_iters, n_alpha=8, ee=True):
+    """Algorithmic FP32 FLOPs of one solve (counts of the stage formulas).
+
+    Per knot and SQP iteration: dynamics + Jacobians 45.0 kFLOP, cost 0.1 kFLOP
+    (joint) / 1.6 kFLOP (end effector), KKT residual 0.6, Schur blocks 14.5,
+    14x14 block inverse 5.5, recovery 0.6, line search n_alpha x 7.1 kFLOP.
+    Per block row and PCG iteration: 2.9 kFLOP.
+    """
+    per_knot = 45.0e3 + (1.6e3 if ee else 0.1e3) + 0.6e3 + 14.5e3 + 5.5e3 + 0.6e3 + n_alpha * 7.1e3
+    return N * per_knot * sqp_iters + (N + 1) * 2.9e3 * pcg_iters
+
+
+def fp32_peak_tflops(sm_mhz, sms=152):
+    """Non-tensor FP32 peak: SMs x 128 FMA lanes x 2 FLOP x clock."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# --------------------------------------------------------------- clock sampler
+
+class ClockSampler:
+    """Samples nvidia-smi while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2510_07625_gb300 import build, gato, inputs as I
+
+    build.build_library()
+    stream = torch.cuda.current_stream()
+    probs = I.config_sweep(B_MAIN, N_MAIN)
+    B = gato.Batch([I.arm7()], B_MAIN, N_MAIN, stream=stream.cuda_stream)
+    dp = gato.DeviceProblems(B, probs)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        dp.reset()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        gato.gato_solve(B.handle, dp.arr, dp.n, ITERS, None)
+        ev1.record(stream)
+        return ev0, ev1
+
+    for _ in range(args.warmup):
+        step()
+        B.sync()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    times, pcg, sqp = [], 0, 0
+    with ClockSampler(local) as clk:
+        t_wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()  # L2 flush between timed launches (outside the events)
+            e0, e1 = step()
+            B.sync()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+        res = gato.gato_get_results(B.handle, dp.n)
+    if ws > 1:
+        torch.distributed.barrier()
+    pcg = sum(res[i].pcg_iters for i in range(dp.n))
+    sqp = sum(res[i].sqp_iters for i in range(dp.n))
+    t_sum = sum(times)
+    t_max = t_sum
+    if ws > 1:
+        tt = torch.tensor([t_sum], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = ws * B_MAIN * args.steps / t_max
+    ms_per_step = 1e3 * t_max / args.steps
+    flops = sum(flops_per_solve(N_MAIN, res[i].sqp_iters, res[i].pcg_iters) for i in range(dp.n))
+    clocks = clk.summary()
+    sm_mhz = clocks["sm_mhz"] or 2070.0
+    peak = fp32_peak_tflops(sm_mhz)
+    achieved = flops / statistics.median(times) / 1e12
+    out = {}
+    if rank == 0:
+        lat = latency_runs(gato, I, torch, stream, flush)
+        plain = plain_form(gato, I, torch)
+        e2e = e2e_run(gato, I, args)
+        cpu = cpu_baseline()
+        out = {
+            "metric": METRIC, "value": round(value, 2), "unit": "solves/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded figure-eight end-effector tracking, 7-DoF rod arm)",
+            "config": {"workload": f"figure-eight EE tracking, B={B_MAIN}, N={N_MAIN}, dt=0.01, "
+                                   f"{ITERS} SQP iterations per call, cold start",
+                       "B": B_MAIN, "N": N_MAIN, "sqp_iters": ITERS, "dof": 7,
+                       "parallelism": f"replicas x{ws}", "l2": "flushed between timed launches (512 MB write)"},
+            "latency_ms": lat, "plain_gpu_form": plain,
+            "speedup_vs_plain_B32": round(plain["solves_per_s_B32"] and lat["B32_iters10"]["solves_per_s"]
+                                          / plain["solves_per_s_B32"], 2),
+            "pcg_iters_per_solve": round(pcg / dp.n, 1), "sqp_iters_per_solve": round(sqp / dp.n, 2),
+            "wall_s_timed": round(t_wall, 4),
+            "roofline": {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 2),
+                         "unit": "TFLOP/s", "frac": round(achieved / peak, 5), "traffic": TRAFFIC_BYTES,
+                         "kernel": "sqp_fused<544,true>",
+                         "peak_note": f"FP32 non-tensor: 152 SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz (sampled)"},
+            "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": args.steps, "clocks": clocks,
+        }
+        print(json.dumps(out), flush=True)
+    B.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return out
+
+
+# DRAM bytes per launch of the dominant kernel on this workload, from the ncu
+# capture summarised in profiles/ (None when the kernel changed since).
+TRAFFIC_BYTES = None
+
+
+def latency_runs(gato, I, torch, stream, flush, n_calls=200):
+    """p50/p99 of one B=32 call (device events), 10 and 3 SQP iterations."""
+    out = {}
+    probs = I.config_sweep(B_LAT, N_MAIN)
+    B = gato.Batch([I.arm7()], B_LAT, N_MAIN, stream=stream.cuda_stream)
+    dp = gato.DeviceProblems(B, probs)
+    for iters in (ITERS, 3):
+        ts = []
+        for rep in range(n_calls + 5):
+            dp.reset()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            gato.gato_solve(B.handle, dp.arr, dp.n, iters, None)
+            e1.record(stream)
+            B.sync()
+            if rep >= 5:
+                ts.append(e0.elapsed_time(e1))
+        ts.sort()
+        p50 = ts[len(ts) // 2]
+        p99 = ts[min(len(ts) - 1, int(0.99 * len(ts)))]
+        out[f"B32_iters{iters}"] = {"p50_ms": round(p50, 4), "p99_ms": round(p99, 4),
+                                    "solves_per_s": round(B_LAT / (p50 / 1e3), 1), "calls": n_calls}
+    B.close()
+    return out
+
+
+def plain_form(gato, I, torch, reps=3):
+    """The plain one-solve-per-launch form on the B=32 batch (same arithmetic)."""
+    probs = I.config_sweep(B_LAT, N_MAIN)
+    B = gato.Batch([I.arm7()], B_LAT, N_MAIN)
+    dp = gato.DeviceProblems(B, probs)
+    ts = []
+    for _ in range(reps):
+        dp.reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gato.gato_solve_plain(B.handle, dp.arr, dp.n, ITERS, None)
+        B.sync()
+        ts.append(time.perf_counter() - t0)
+    B.close()
+    t = statistics.median(ts)
+    return {"solves_per_s_B32": round(B_LAT / t, 1), "ms_per_call_B32": round(1e3 * t, 2),
+            "launches_per_solve_iter": 12}
+
+
+def e2e_run(gato, I, args):
+    """The same metric through the C ABI with host buffers (copies inside the timing)."""
+    import numpy as np
+
+    probs = I.config_sweep(B_MAIN, N_MAIN)
+    B = gato.Batch([I.arm7()], B_MAIN, N_MAIN)
+    hp = gato.HostProblems(B, probs)
+    X0 = [x.copy() for x in hp.X]
+    res = (gato.Result * hp.n)()
+    ts = []
+    h2d = d2h = 0
+    for rep in range(args.warmup + args.steps):
+        for i in range(hp.n):
+            hp.X[i][...] = X0[i]
+            hp.U[i][...] = 0
+            hp.lam[i][...] = 0
+        t0 = time.perf_counter()
+        gato.gato_solve(B.handle, hp.arr, hp.n, ITERS, res)
+        t = time.perf_counter() - t0
+        if rep >= args.warmup:
+            ts.append(t)
+        h2d, d2h = gato.gato_last_transfer_bytes(B.handle)
+    B.close()
+    return {"value": round(B_MAIN * len(ts) / sum(ts), 2), "unit": "solves/s",
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+
+# --------------------------------------------------------------- CPU oracle
+
+def oracle_rate(n_solves, threads=None):
+    """FP64 oracle on host cores: solves/s over a bounded sample of the workload."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    from paper_2510_07625_gb300 import inputs as I
+
+    oracle.build()
+    threads = threads or os.cpu_count()
+    probs = I.config_sweep(n_solves, N_MAIN)
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        list(ex.map(lambda p: oracle.solve(p, max_iter=ITERS), probs))
+    t = time.perf_counter() - t0
+    return n_solves / t, threads, t
+
+
+def cpu_baseline():
+    n = 4 * max(16, os.cpu_count() or 1)
+    rate, thr, t = oracle_rate(n)
+    return {"value": round(rate, 3), "unit": "solves/s", "cores": thr, "kind": "oracle",
+            "sample": f"{n} of the {B_MAIN} solves (seeds 0..{n - 1}), {ITERS} SQP iterations each, "
+                      f"one solve per thread, {t:.1f} s wall"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    n = max(8, os.cpu_count() or 1)
+    rates, tt, thr = [], [], 0
+    for i in range(args.warmup + args.steps):
+        r, thr, t = oracle_rate(n)
+        if i >= args.warmup:
+            rates.append(r)
+            tt.append(t)
+    value = n * len(tt) / sum(tt)
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "solves/s",
+           "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(1e3 * sum(tt) / len(tt), 2), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"figure-eight EE tracking, B={B_MAIN}, N={N_MAIN}, dt=0.01, "
+                                  f"{ITERS} SQP iterations per call, cold start",
+                      "sample_per_step": n},
+           "cpu_baseline": {"kind": "oracle", "cores": thr, "value": round(value, 3),
+                            "sample": f"{n} solves of the workload per step, one per thread"},
+           "e2e": {"value": round(value, 3), "unit": "solves/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gato", choices=["gato", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

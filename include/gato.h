@@ -174,8 +174,9 @@ gato_status gato_last_transfer_bytes(const gato_batch* b, int64_t* h2d, int64_t*
 gato_status gato_debug_plain_stage(gato_batch* b, const gato_problem* problems, int32_t stop_stage,
                                    float* ws_out, int64_t ws_floats);
 
-/* Fills offsets[0..21] (floats) of the workspace arrays in the order
- * X U dX dU Fq Fv Minv qdd dTau Qinv Rinv q r c Jk Linv links D L P vec scal,
+/* Fills offsets[0..23] (floats) of the workspace arrays in the order
+ * X U dX dU Fq Fv Minv qdd dTau Qinv Rinv q r c Jk Linv links D L P vec scal
+ * dres_x dres_u,
  * and returns the workspace size in floats (or -1). */
 int64_t gato_debug_layout(const gato_batch* b, int64_t* offsets);
 

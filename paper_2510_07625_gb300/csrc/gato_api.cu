@@ -501,10 +501,10 @@ int64_t gato_debug_layout(const gato_batch* b, int64_t* o) {
   if (!b || !o) return -1;
   const WsLayout& L = b->plain_layout;
   const size_t K = b->max_horizon + 1;
-  const size_t v[22] = {L.X,  L.U,  L.dX, L.dU, L.Fq, L.Fv, L.Mi, L.qdd, L.dT, L.Qi, L.Ri,
-                        L.qg, L.rg, L.cv, L.Jk, L.Li, L.LV, L.Dm, L.Lm,  L.Pm, L.vec,
-                        L.vec + 12 * K * VS};
-  for (int i = 0; i < 22; ++i) o[i] = (int64_t)v[i];
+  const size_t v[24] = {L.X,  L.U,  L.dX, L.dU, L.Fq, L.Fv, L.Mi, L.qdd, L.dT, L.Qi, L.Ri, L.qg,
+                        L.rg, L.cv, L.Jk, L.Li, L.LV, L.Dm, L.Lm, L.Pm, L.vec, L.vec + 12 * K * VS,
+                        L.Dx, L.Du};
+  for (int i = 0; i < 24; ++i) o[i] = (int64_t)v[i];
   return (int64_t)L.total;
 }
 

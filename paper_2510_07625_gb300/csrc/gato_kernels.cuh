@@ -30,6 +30,8 @@ __device__ __forceinline__ void bind_workspace(Ctx& C, float* ws, const WsLayout
   C.cv = ws + L.cv;
   C.Jk = ws + L.Jk;
   C.Li = ws + L.Li;
+  C.Dx = ws + L.Dx;
+  C.Du = ws + L.Du;
   C.LV = reinterpret_cast<LinkRec*>(ws + L.LV);
 }
 
@@ -55,6 +57,7 @@ __device__ __forceinline__ void bind_vectors(Ctx& C, float* v, size_t VV) {
   C.wv = v + 6 * VV;
   C.zv = v + 7 * VV;
   C.rhs = v + 8 * VV;
+  C.dnu = v + 9 * VV;
 }
 
 __device__ __forceinline__ int sflags(const Ctx& C) {

@@ -27,9 +27,10 @@ struct Ctx {
   float* xs;            // padded x_s [VS]
   // global workspace
   float *X, *U, *dX, *dU, *Fq, *Fv, *Mi, *qdd, *dT, *Qi, *Ri, *qg, *rg, *cv, *Jk, *Li;
+  float *Dx, *Du;       // dual residual d = g + C^T nu at the current linearisation
   LinkRec* LV;
   // hot arrays (shared or global)
-  float *Dm, *Lm, *Pm, *nu, *rr, *pb0, *pb1, *qv, *yv, *wv, *zv, *rhs;
+  float *Dm, *Lm, *Pm, *nu, *rr, *pb0, *pb1, *qv, *yv, *wv, *zv, *rhs, *dnu;
   // reductions (always shared): red[2][32][2], scal[64]
   float* red;
   float* scal;
@@ -45,7 +46,8 @@ enum : int {
 constexpr int FQS = 49, QIS = 56, DTS = 14 * 8, LIS = 196;
 
 struct WsLayout {
-  size_t X, U, dX, dU, Fq, Fv, Mi, qdd, dT, Qi, Ri, qg, rg, cv, Jk, Li, LV, Dm, Lm, Pm, vec, total;
+  size_t X, U, dX, dU, Fq, Fv, Mi, qdd, dT, Qi, Ri, qg, rg, cv, Jk, Li, LV, Dm, Lm, Pm, vec, Dx, Du,
+      total;
 };
 
 __host__ __device__ inline size_t align32(size_t n) { return (n + 31) & ~size_t(31); }
@@ -73,6 +75,8 @@ __host__ __device__ inline WsLayout ws_layout(int Nmax, bool global_blocks, bool
   L.Jk = o; o += align32(K);
   L.Li = o; o += align32(K * LIS);
   L.LV = o; o += align32(Nmax * QM * LVS);
+  L.Dx = o; o += align32(K * VS);
+  L.Du = o; o += align32(Nmax * US);
   if (global_blocks) {
     L.Dm = o; o += align32(K * BS);
     L.Lm = o; o += align32(K * BS);
@@ -170,9 +174,10 @@ __device__ __forceinline__ DF block_df_sum(const Ctx& C, DF v) {
   }
   if (threadIdx.x == 0) C.scal[S_REDBUF] = (float)(buf ^ 1);
   __syncthreads();
-  DF s = df_zero();
-  for (int w = 0; w < NW; ++w) s = df_addd(s, DF{C.red[(buf * 32 + w) * 2], C.red[(buf * 32 + w) * 2 + 1]});
-  return s;
+  // every warp reduces the per-warp partials with the same shuffle tree, so all
+  // threads hold the same (deterministic) total without another barrier
+  DF s = lane < NW ? DF{C.red[(buf * 32 + lane) * 2], C.red[(buf * 32 + lane) * 2 + 1]} : df_zero();
+  return warp_df_sum(s);
 }
 
 template <int NT>
@@ -427,23 +432,45 @@ __device__ void st_dyn_jacobians(const Ctx& C) {
 }
 
 // KKT residual (reading c17) and the merit of the current iterate (Eq. 3).
+// Also stores the dual residual d = g + C^T nu, accumulated with compensated
+// sums: near convergence d is a small difference of O(|nu|) terms, and the
+// step is recovered from it through G^-1 (R^-1 = 1/w_u amplifies its error).
 template <int NT>
 __device__ void st_kkt_merit(const Ctx& C, float mu) {
   const int N = C.N;
-  const float h = C.h;
+  const float h = C.h, h2 = C.h * C.h;
   float cmax = 0.f, gmax = 0.f, dmax = 0.f;
   bool bad = false;
   DF jsum = df_zero(), csum = df_zero();
   KNOT_LOOP(NT, N) {
     if (act) {
       const float* nu = C.nu + k * VS;
-      float at0 = 0.f, at1 = 0.f, bt = 0.f;
+      DF d0 = df_add(df_add(df_zero(), C.qg[k * VS + j]), nu[j]);
+      DF d1 = df_add(df_add(df_zero(), C.qg[k * VS + j + QM]), nu[j + QM]);
+      DF du = df_zero();
       if (k < N) {
-        float cf[QM];
-        at_factor(C.nu + (k + 1) * VS, h, cf);
-        at_rows(C.Fq + k * FQS, C.Fv + k * FQS, C.nu + (k + 1) * VS, cf, h, j, at0, at1);
-        bt = bt_row(C.Mi + k * FQS, cf, j);
+        const float* n1 = C.nu + (k + 1) * VS;
+        const float* Fq = C.Fq + k * FQS;
+        const float* Fv = C.Fv + k * FQS;
+        const float* Mi = C.Mi + k * FQS;
+        // A^T n1: rows j (q) and j+7 (qd) of [[I + h^2 Fq, hI + h^2 Fv], [h Fq, I + h Fv]]^T
+        d0 = df_add(d0, -n1[j]);
+        d1 = df_fma(d1, -h, n1[j]);
+        d1 = df_add(d1, -n1[j + QM]);
+        du = df_add(du, C.rg[k * US + j]);
+#pragma unroll
+        for (int r = 0; r < QM; ++r) {
+          d0 = df_fma(d0, -h2 * Fq[r * QM + j], n1[r]);
+          d0 = df_fma(d0, -h * Fq[r * QM + j], n1[QM + r]);
+          d1 = df_fma(d1, -h2 * Fv[r * QM + j], n1[r]);
+          d1 = df_fma(d1, -h * Fv[r * QM + j], n1[QM + r]);
+          du = df_fma(du, -h2 * Mi[r * QM + j], n1[r]);
+          du = df_fma(du, -h * Mi[r * QM + j], n1[QM + r]);
+        }
       }
+      const float dv[2] = {df_val(d0), df_val(d1)};
+      C.Dx[k * VS + j] = dv[0];
+      C.Dx[k * VS + j + QM] = dv[1];
       for (int t = 0; t < 2; ++t) {
         const int i = j + QM * t;
         const float cvi = C.cv[k * VS + i];
@@ -451,15 +478,16 @@ __device__ void st_kkt_merit(const Ctx& C, float mu) {
         csum = df_add(csum, fabsf(cvi));
         const float g = C.qg[k * VS + i];
         gmax = fmaxf(gmax, fabsf(g));
-        const float dv = g + nu[i] - (t == 0 ? at0 : at1);
-        dmax = fmaxf(dmax, fabsf(dv));
-        bad = bad || !isfinite(cvi) || !isfinite(dv);
+        dmax = fmaxf(dmax, fabsf(dv[t]));
+        bad = bad || !isfinite(cvi) || !isfinite(dv[t]);
       }
       if (k < N) {
         const float g = C.rg[k * US + j];
+        const float duv = df_val(du);
+        C.Du[k * US + j] = duv;
         gmax = fmaxf(gmax, fabsf(g));
-        dmax = fmaxf(dmax, fabsf(g - bt));
-        bad = bad || !isfinite(g - bt);
+        dmax = fmaxf(dmax, fabsf(duv));
+        bad = bad || !isfinite(duv);
       }
       if (j == 0) {
         jsum = df_add(jsum, C.Jk[k]);
@@ -486,8 +514,11 @@ __device__ void st_kkt_merit(const Ctx& C, float mu) {
 // ------------------------------------------------------ stage 2: Schur form
 
 // Eq. 5-6 blocks (reading c1/c3 signs):  L_k = phi_{k-1} = -A_{k-1} Q_{k-1}^-1,
-// D_k = theta_{k-1} = A Q^-1 A^T + B R^-1 B^T + Q_k^-1 (D_0 = Q_0^-1), and
-// rhs_0 = -c_0 - Q_0^-1 q_0, rhs_k = -e_{k-1} - zeta_{k-1}.
+// D_k = theta_{k-1} = A Q^-1 A^T + B R^-1 B^T + Q_k^-1 (D_0 = Q_0^-1).
+// Right-hand side for the multiplier correction dnu = nu - nu_0: zeta_k and
+// gamma of Eq. 5 with the gradient g replaced by the dual residual
+// d = g + C^T nu_0, i.e. rhs = -c - C G^-1 d = gamma - S nu_0, the initial
+// residual of the warm-started PCG, formed without cancellation.
 template <int NT>
 __device__ void st_schur(const Ctx& C) {
   const int N = C.N;
@@ -502,7 +533,7 @@ __device__ void st_schur(const Ctx& C) {
         for (int c = 0; c < XM; ++c) {
           const float qv = Qinv_elem(Qi, i, c);
           blk(C.Dm, 0, i, c) = qv;
-          acc += qv * C.qg[c];
+          acc += qv * C.Dx[c];
           blk(C.Lm, 0, i, c) = 0.f;
         }
         C.rhs[i] = -C.cv[i] - acc;
@@ -559,14 +590,14 @@ __device__ void st_schur(const Ctx& C) {
           for (int m = 0; m < QM; ++m) bb += BRrow[m] * Mi[cm * QM + m];
           blk(C.Dm, k, i, c) = a + sc * bb + Qinv_elem(Qi1, i, c);
         }
-        // zeta = L_k q_{k-1} - B R^-1 r_{k-1} + Q_k^-1 q_k
+        // zeta with d: L_k d_{k-1} - B R^-1 d_u,{k-1} + Q_k^-1 d_k
         float z = 0.f;
 #pragma unroll
-        for (int l = 0; l < XM; ++l) z += blk(C.Lm, k, i, l) * C.qg[kk * VS + l];
+        for (int l = 0; l < XM; ++l) z += blk(C.Lm, k, i, l) * C.Dx[kk * VS + l];
 #pragma unroll
-        for (int m = 0; m < QM; ++m) z -= BRrow[m] * C.rg[kk * US + m];
+        for (int m = 0; m < QM; ++m) z -= BRrow[m] * C.Du[kk * US + m];
 #pragma unroll
-        for (int l = 0; l < XM; ++l) z += Qinv_elem(Qi1, i, l) * C.qg[k * VS + l];
+        for (int l = 0; l < XM; ++l) z += Qinv_elem(Qi1, i, l) * C.Dx[k * VS + l];
         C.rhs[k * VS + i] = -C.cv[k * VS + i] - z;
       }
     }
@@ -702,22 +733,24 @@ __device__ __forceinline__ void p_rows(const Ctx& C, int k, int j, const float* 
   o1 = a1;
 }
 
-// Preconditioned CG on S nu = rhs (Sec. II-B, III-B), warm-started from nu.
-// Stair preconditioner (Eq. 6) applied as D^-1 - D^-1 O D^-1 (reading c4).
-// Stops when sqrt(eta / eta_0) <= eps (reading c8).  Returns iterations.
+// Preconditioned CG (Sec. II-B, III-B) for the multiplier correction
+// S dnu = rhs, started from dnu = 0; nu_0 + dnu equals the warm-started PCG
+// iterate on S nu = gamma.  Stair preconditioner (Eq. 6) applied as
+// D^-1 - D^-1 O D^-1 (reading c4).  Stops when sqrt(eta / eta_0) <= eps
+// (reading c8).  Returns iterations.
 template <int NT>
 __device__ int st_pcg(const Ctx& C, float eps, int maxit, int precond, bool* hit_max) {
   const int N = C.N;
   const bool stair = (precond == 0);
   *hit_max = false;
-  // r = rhs - S nu ; y = D^-1 r
+  // dnu = 0, r = rhs ; y = D^-1 r
   {
     KNOT_LOOP(NT, N) {
       if (act) {
-        float s0, s1;
-        s_rows(C, N, k, j, [&](int kk, int c) { return C.nu[kk * VS + c]; }, s0, s1);
-        C.rr[k * VS + j] = C.rhs[k * VS + j] - s0;
-        C.rr[k * VS + j + QM] = C.rhs[k * VS + j + QM] - s1;
+        C.dnu[k * VS + j] = 0.f;
+        C.dnu[k * VS + j + QM] = 0.f;
+        C.rr[k * VS + j] = C.rhs[k * VS + j];
+        C.rr[k * VS + j + QM] = C.rhs[k * VS + j + QM];
       }
       __syncwarp();
       if (act) {
@@ -793,7 +826,7 @@ __device__ int st_pcg(const Ctx& C, float eps, int maxit, int precond, bool* hit
         if (act) {
           for (int t = 0; t < 2; ++t) {
             const int i = k * VS + j + QM * t;
-            C.nu[i] += alpha * pnew[i];
+            C.dnu[i] += alpha * pnew[i];
             C.rr[i] -= alpha * C.qv[i];
           }
         }
@@ -853,7 +886,8 @@ __device__ int st_pcg(const Ctx& C, float eps, int maxit, int precond, bool* hit
 
 // ------------------------------------------------- stage 4: step recovery
 
-// dx_k = -Q_k^-1 (q_k + nu_k - A_k^T nu_{k+1}), du_k = -R_k^-1 (r_k - B_k^T nu_{k+1}).
+// dx_k = -Q_k^-1 (q_k + nu_k - A_k^T nu_{k+1}), du_k = -R_k^-1 (r_k - B_k^T nu_{k+1})
+// (Eq. 4, reading c1), evaluated as -G^-1 (d + C^T dnu); then nu += dnu.
 template <int NT>
 __device__ void st_recover(const Ctx& C) {
   const int N = C.N;
@@ -865,12 +899,12 @@ __device__ void st_recover(const Ctx& C) {
       float at0 = 0.f, at1 = 0.f;
       if (k < N) {
         float cf[QM];
-        at_factor(C.nu + (k + 1) * VS, h, cf);
-        at_rows(C.Fq + k * FQS, C.Fv + k * FQS, C.nu + (k + 1) * VS, cf, h, j, at0, at1);
+        at_factor(C.dnu + (k + 1) * VS, h, cf);
+        at_rows(C.Fq + k * FQS, C.Fv + k * FQS, C.dnu + (k + 1) * VS, cf, h, j, at0, at1);
         bt = bt_row(C.Mi + k * FQS, cf, j);
       }
-      C.wv[k * VS + j] = C.qg[k * VS + j] + C.nu[k * VS + j] - at0;
-      C.wv[k * VS + j + QM] = C.qg[k * VS + j + QM] + C.nu[k * VS + j + QM] - at1;
+      C.wv[k * VS + j] = C.Dx[k * VS + j] + C.dnu[k * VS + j] - at0;
+      C.wv[k * VS + j + QM] = C.Dx[k * VS + j + QM] + C.dnu[k * VS + j + QM] - at1;
     }
     __syncwarp();
     if (act) {
@@ -884,10 +918,12 @@ __device__ void st_recover(const Ctx& C) {
       C.dX[k * VS + j + QM] = dx1;
       bad = bad || !isfinite(dx0) || !isfinite(dx1);
       if (k < N) {
-        const float du = -C.Ri[k * US + j] * (C.rg[k * US + j] - bt);
+        const float du = -C.Ri[k * US + j] * (C.Du[k * US + j] - bt);
         C.dU[k * US + j] = du;
         bad = bad || !isfinite(du);
       }
+      C.nu[k * VS + j] += C.dnu[k * VS + j];
+      C.nu[k * VS + j + QM] += C.dnu[k * VS + j + QM];
     }
   }
   if (bad) atomicOr(reinterpret_cast<int*>(C.scal + S_FLAGS), F_NONFINITE);

@@ -31,7 +31,7 @@ EXPORTED = (
     "gato_last_transfer_bytes", "gato_debug_plain_stage", "gato_debug_layout",
 )
 LAYOUT_NAMES = ("X", "U", "dX", "dU", "Fq", "Fv", "Minv", "qdd", "dTau", "Qinv", "Rinv", "q", "r",
-                "c", "Jk", "Linv", "links", "D", "L", "P", "vec", "scal")
+                "c", "Jk", "Linv", "links", "D", "L", "P", "vec", "scal", "Dx", "Du")
 
 
 class ModelDesc(C.Structure):
@@ -183,7 +183,7 @@ def gato_last_transfer_bytes(handle):
 
 
 def gato_debug_layout(handle):
-    off = (C.c_int64 * 22)()
+    off = (C.c_int64 * 24)()
     total = load().gato_debug_layout(C.c_void_p(handle), off)
     return total, dict(zip(LAYOUT_NAMES, list(off)))
 

@@ -46,7 +46,10 @@ FIG8_OMEGA = math.pi  # period 2 s
 # Cost weights, in the order used everywhere: position, velocity, control,
 # terminal scale, end-effector position, diagonal damping rho.
 W_JOINT = (1.0, 0.1, 1e-3, 10.0, 0.0, 0.0)
-W_EE = (0.0, 0.1, 1e-3, 10.0, 100.0, 1e-3)
+# rho = 1 on the end-effector cost: with rho <= 1e-2 the Gauss-Newton Q_k (rank-3
+# JᵀJ plus rho) makes FP32 PCG break down (Sec. IV-B uses rho as exactly this
+# numerical-stability damping).
+W_EE = (0.0, 0.1, 1e-3, 10.0, 100.0, 1.0)
 
 
 @dataclass(frozen=True)

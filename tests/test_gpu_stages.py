@@ -69,6 +69,12 @@ PROBS = [
 ]
 
 
+def lam_padded(lam, pi, K):
+    out = np.zeros((K, XM))
+    out[:, pi] = lam
+    return out
+
+
 def midpoint(oracle, prob):
     r = oracle.solve(prob, max_iter=2)
     return r["X"], r["U"], r["lam"]
@@ -110,6 +116,15 @@ def test_linearisation_stage(G, oracle, name, mk):
         Qfull[7:, 7:] = np.diag(Qi[k, 49:56])
         want = np.linalg.inv(lin["Q"][k])
         np.testing.assert_allclose(Qfull[np.ix_(pi, pi)], want, atol=2e-4 * np.abs(want).max(), rtol=0)
+    # dual residual d = g + C^T nu (compensated on the GPU) against the oracle in FP64
+    t = lin["q"] + lam
+    t[:-1] -= np.einsum("kji,kj->ki", lin["A"], lam[1:])
+    du_want = lin["r"] - np.einsum("kji,kj->ki", lin["B"], lam[1:])
+    Dx = knots(buf, off, "Dx", K, VS, XM)[:, pi]
+    Du = knots(buf, off, "Du", N, US, dof)
+    scale = max(1.0, np.abs(lin["q"]).max(), np.abs(lam).max())
+    np.testing.assert_allclose(Dx, t, atol=1e-4 * scale, rtol=0)
+    np.testing.assert_allclose(Du, du_want, atol=1e-4 * scale, rtol=0)
     # KKT residual and merit of the current iterate, against the oracle (FP64)
     scal = buf[off["scal"]:off["scal"] + 64]
     kkt_ora = oracle.kkt_residual(prob, X, U, lam)
@@ -124,23 +139,58 @@ def test_schur_and_preconditioner_stage(G, oracle, name, mk):
     X, U, lam = midpoint(oracle, prob)
     buf, off, N = stage(G, prob, 8, X, U, lam)
     K = N + 1
+    h = prob.dt
     pi = pad_idx(prob.model.dof)
     S = oracle.schur(prob, X, U)
     D = block(buf, off, "D", K)
     L = block(buf, off, "L", K)
     P = block(buf, off, "P", K)
     rhs = vec(buf, off, prob.N, 8)
+    # (1) the stage's own arithmetic: Eq. 5 blocks and the correction rhs
+    #     recomputed in FP64 from the GPU's inputs to this stage
+    Fq = buf[off["Fq"]:off["Fq"] + N * 49].reshape(N, 7, 7)
+    Fv = buf[off["Fv"]:off["Fv"] + N * 49].reshape(N, 7, 7)
+    Mi = buf[off["Minv"]:off["Minv"] + N * 49].reshape(N, 7, 7)
+    Qi = buf[off["Qinv"]:off["Qinv"] + K * 56].reshape(K, 56)
+    Ri = knots(buf, off, "Rinv", N, US, 7)
+    Dx = knots(buf, off, "Dx", K, VS, XM)
+    Du = knots(buf, off, "Du", N, US, 7)
+    cv = knots(buf, off, "c", K, VS, XM)
+    I7 = np.eye(7)
+    Qf = np.zeros((K, 14, 14))
+    for k in range(K):
+        Qf[k, :7, :7] = Qi[k, :49].reshape(7, 7)
+        Qf[k, 7:, 7:] = np.diag(Qi[k, 49:])
+    D_want = [Qf[0]]
+    L_want = [np.zeros((14, 14))]
+    rhs_want = [-cv[0] - Qf[0] @ Dx[0]]
+    for k in range(N):
+        A = np.block([[I7 + h * h * Fq[k], h * I7 + h * h * Fv[k]], [h * Fq[k], I7 + h * Fv[k]]])
+        Bm = np.vstack([h * h * Mi[k], h * Mi[k]])
+        BRB = Bm @ np.diag(Ri[k]) @ Bm.T
+        Lk = -A @ Qf[k]
+        D_want.append(A @ Qf[k] @ A.T + BRB + Qf[k + 1])
+        L_want.append(Lk)
+        zeta = Lk @ Dx[k] - Bm @ np.diag(Ri[k]) @ Du[k] + Qf[k + 1] @ Dx[k + 1]
+        rhs_want.append(-cv[k + 1] - zeta)
+    for k in range(K):
+        sc = np.abs(D_want[k]).max()
+        np.testing.assert_allclose(D[k], D_want[k], atol=2e-6 * sc, rtol=0)
+        if k > 0:
+            np.testing.assert_allclose(L[k], L_want[k], atol=2e-6 * np.abs(L_want[k]).max(), rtol=0)
+    rw = np.array(rhs_want)
+    np.testing.assert_allclose(rhs, rw, atol=1e-5 * max(1e-6, np.abs(rw).max()), rtol=0)
+    # (2) the blocks against the oracle's Schur complement (FP32 Jacobians)
     for k in range(K):
         Dk = D[k][np.ix_(pi, pi)]
         np.testing.assert_allclose(Dk, S["Sd"][k], atol=1e-4 * np.abs(S["Sd"][k]).max(), rtol=0)
         # the GPU's D^-1 inverts the GPU's own D to FP32 working accuracy
-        Dg, Pg = D[k][np.ix_(pi, pi)], P[k][np.ix_(pi, pi)]
-        kappa = np.linalg.cond(Dg)
-        assert np.abs(Pg @ Dg - np.eye(len(pi))).max() < 50 * kappa * 6e-8
+        Pg = P[k][np.ix_(pi, pi)]
+        kappa = np.linalg.cond(Dk)
+        assert np.abs(Pg @ Dk - np.eye(len(pi))).max() < 50 * kappa * 6e-8
         if k > 0:
             Lk = L[k][np.ix_(pi, pi)]
             np.testing.assert_allclose(Lk, S["Ss"][k - 1], atol=1e-4 * np.abs(S["Ss"][k - 1]).max(), rtol=0)
-    np.testing.assert_allclose(rhs[:, pi], S["rhs"], atol=1e-4 * np.abs(S["rhs"]).max(), rtol=0)
 
 
 @pytest.mark.parametrize("precond", [0, 1])
@@ -151,19 +201,31 @@ def test_pcg_recovery_and_line_search_stages(G, oracle, name, mk, precond):
     N, K = prob.N, prob.N + 1
     dof = prob.model.dof
     pi = pad_idx(dof)
-    S = oracle.schur(prob, X, U, precond=precond)
     buf, off, _ = stage(G, prob, 11, X, U, lam, precond=precond)
-    nu = vec(buf, off, N, 0)[:, pi]
-    # PCG: the GPU multiplier meets the stopping rule on the oracle's FP64 system
+    # PCG on the GPU's own Schur system (read back, evaluated in FP64): the
+    # multiplier meets the relative stopping rule up to FP32 attainable accuracy
+    D = block(buf, off, "D", K)
+    L = block(buf, off, "L", K)
+    P = block(buf, off, "P", K)
+    rhs_g = vec(buf, off, N, 8)
+    nu_g = vec(buf, off, N, 0)
     from tests.test_oracle_kkt import blocks_to_dense
-    Sd = blocks_to_dense(S["Sd"], S["Ss"])
-    Pm = blocks_to_dense(S["Pd"], S["Ps"])
-    r0 = S["rhs"].ravel() - Sd @ lam.ravel()
-    r = S["rhs"].ravel() - Sd @ nu.ravel()
-    rel = np.sqrt(abs(r @ Pm @ r) / (r0 @ Pm @ r0))
-    exact = np.linalg.solve(Sd, S["rhs"].ravel())
-    err_nu = np.abs(nu.ravel() - exact).max() / np.abs(exact).max()
-    assert rel < 5e-3, rel
+    Sg = blocks_to_dense(D, L[1:])
+    Dinv = np.zeros_like(Sg)
+    for k in range(K):
+        Dinv[k * XM:(k + 1) * XM, k * XM:(k + 1) * XM] = P[k]
+    Og = Sg.copy()
+    for k in range(K):
+        Og[k * XM:(k + 1) * XM, k * XM:(k + 1) * XM] = 0
+    Phi = Dinv - Dinv @ Og @ Dinv if precond == 0 else Dinv
+    dnu = vec(buf, off, N, 9)
+    r0 = rhs_g.ravel()
+    r = rhs_g.ravel() - Sg @ dnu.ravel()
+    nu_g = dnu
+    rel = np.sqrt(abs(r @ Phi @ r) / (r0 @ Phi @ r0))
+    exact = np.linalg.solve(Sg, rhs_g.ravel())
+    err_nu = np.abs(nu_g.ravel() - exact).max() / np.abs(exact).max()
+    assert rel < 1e-4, rel
     assert err_nu < 5e-3, err_nu
     # recovery: dZ = -G^-1 (g + C^T nu) on the GPU's own linearisation and nu, in FP64
     h = prob.dt
@@ -174,17 +236,19 @@ def test_pcg_recovery_and_line_search_stages(G, oracle, name, mk, precond):
     Ri = knots(buf, off, "Rinv", N, US, 7)
     qg = knots(buf, off, "q", K, VS, XM)
     rg = knots(buf, off, "r", N, US, 7)
-    nup = vec(buf, off, N, 0)
+    nup = vec(buf, off, N, 9)
+    Dx = knots(buf, off, "Dx", K, VS, XM)
+    Du = knots(buf, off, "Du", N, US, 7)
     I7 = np.eye(7)
     dX_want = np.zeros((K, XM))
     dU_want = np.zeros((N, 7))
     for k in range(K):
-        t = qg[k] + nup[k]
+        t = Dx[k] + nup[k]
         if k < N:
             A = np.block([[I7 + h * h * Fq[k], h * I7 + h * h * Fv[k]], [h * Fq[k], I7 + h * Fv[k]]])
             Bm = np.vstack([h * h * Mi[k], h * Mi[k]])
             t = t - A.T @ nup[k + 1]
-            dU_want[k] = -Ri[k] * (rg[k] - Bm.T @ nup[k + 1])
+            dU_want[k] = -Ri[k] * (Du[k] - Bm.T @ nup[k + 1])
         Qf = np.zeros((14, 14))
         Qf[:7, :7] = Qi[k, :49].reshape(7, 7)
         Qf[7:, 7:] = np.diag(Qi[k, 49:])
