@@ -149,6 +149,32 @@ gato_status gato_step(gato_batch* b, const gato_problem* problems, int32_t n,
 gato_status gato_solve_plain(gato_batch* b, const gato_problem* problems, int32_t n,
                              int32_t max_sqp_iters, gato_result* results);
 
+/* gato_solve for callers that cannot allocate device memory: a real-time
+ * control loop that must not pay allocation latency or implicit device
+ * synchronisation once it runs, a controller with a fixed memory budget, or
+ * code hosted inside an application that owns every device allocation.  (The
+ * paper has no counterpart; this is a deployment variant of gato_solve.)
+ *
+ * Same solver and kernel as gato_solve, but it needs no gato_batch: its
+ * scratch (per-solve workspace, descriptors, models, launch order) is a set of
+ * fixed-size arrays compiled into the library, about 3.2 MiB held on every GPU
+ * that loads it until the process exits.  Limits: n <= 16 solves, N <= 64,
+ * n_models <= 8, and every problem must use GATO_MEM_DEVICE pointers; larger
+ * or host problems return GATO_E_INVALID and launch nothing.  `results` is a
+ * DEVICE array of n gato_result that the kernel writes.  The call is
+ * asynchronous on cuda_stream (a cudaStream_t, NULL = legacy default stream);
+ * synchronise the stream before reading X, U, lambda or results.  It calls no
+ * cudaMalloc or cudaFree.  The first call on each device looks up the device
+ * addresses of the arrays (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls share the same
+ * arrays, so calls whose kernels overlap on the GPU (another stream, another
+ * host thread) race: serialise them.  Nothing in the arrays has to start at
+ * zero (every call writes its scratch before reading it). */
+gato_status gato_solve_noalloc(const gato_model_desc* models, int32_t n_models,
+                               const gato_solver_params* params,
+                               const gato_problem* problems, int32_t n, int32_t max_sqp_iters,
+                               gato_result* results, void* cuda_stream);
+
 /* Waits for the batch stream, at most timeout_us microseconds (< 0 = forever);
  * GATO_E_TIMEOUT leaves the work running.  Uses a polling host wait, never a
  * device-side spin. */

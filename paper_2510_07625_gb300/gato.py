@@ -28,7 +28,7 @@ MEM_HOST, MEM_DEVICE = 0, 1
 EXPORTED = (
     "gato_default_params", "gato_create_batch", "gato_solve", "gato_step", "gato_solve_plain",
     "gato_sync", "gato_get_results", "gato_destroy_batch", "gato_status_string", "gato_last_error",
-    "gato_last_transfer_bytes", "gato_debug_plain_stage", "gato_debug_layout",
+    "gato_last_transfer_bytes", "gato_debug_plain_stage", "gato_debug_layout", "gato_solve_noalloc",
 )
 LAYOUT_NAMES = ("X", "U", "dX", "dU", "Fq", "Fv", "Minv", "qdd", "dTau", "Qinv", "Rinv", "q", "r",
                 "c", "Jk", "Linv", "links", "D", "L", "P", "vec", "scal", "Dx", "Du")
@@ -102,6 +102,9 @@ def load() -> C.CDLL:
     L.gato_debug_plain_stage.restype = C.c_int
     L.gato_debug_layout.argtypes = [bp, C.POINTER(C.c_int64)]
     L.gato_debug_layout.restype = C.c_int64
+    L.gato_solve_noalloc.argtypes = [C.POINTER(ModelDesc), C.c_int32, C.POINTER(SolverParams),
+                                     C.POINTER(Problem), C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]
+    L.gato_solve_noalloc.restype = C.c_int
     _lib = L
     return L
 
@@ -195,6 +198,14 @@ def gato_debug_plain_stage(handle, problems, stop_stage):
                                       buf.ctypes.data_as(C.c_void_p), total)
     _check(handle, s, "gato_debug_plain_stage")
     return buf, off
+
+
+def gato_solve_noalloc(models, n_models, params, problems, n, iters, results_dev_ptr, stream=0):
+    """Allocation-free solve: device problems only, results written to device memory."""
+    s = load().gato_solve_noalloc(models, n_models, C.byref(params), problems, n, iters,
+                                  C.c_void_p(results_dev_ptr), C.c_void_p(stream or 0))
+    if s != GATO_OK:
+        raise GatoError(s, f"gato_solve_noalloc: {gato_status_string(s)}")
 
 
 # ------------------------------------------------------------- conveniences
