@@ -131,8 +131,10 @@ void gato_default_params(gato_solver_params* out);
  * cudaStream_t; NULL = the legacy default stream).  *out is NULL on failure. */
 gato_status gato_create_batch(const gato_batch_desc* desc, void* cuda_stream, gato_batch** out);
 
-/* Runs up to max_sqp_iters SQP iterations (Alg. 1, repeated) for n solves in one
- * persistent fused launch (one CTA per solve, longest horizon first).  Host
+/* Runs up to max_sqp_iters SQP iterations (Alg. 1, repeated) for n solves in
+ * persistent fused launches: each solve is one thread-block cluster of
+ * ceil((N+1)/35) CTAs or more (gato_launch_config), one launch per cluster
+ * size, the launches running concurrently, longest horizon first.  Host
  * problems are staged through pinned memory; device problems are used in place.
  * Asynchronous on the batch stream; if `results` is non-NULL the call waits and
  * fills results[0..n-1], otherwise call gato_sync then gato_get_results. */
@@ -157,7 +159,7 @@ gato_status gato_solve_plain(gato_batch* b, const gato_problem* problems, int32_
  *
  * Same solver and kernel as gato_solve, but it needs no gato_batch: its
  * scratch (per-solve workspace, descriptors, models, launch order) is a set of
- * fixed-size arrays compiled into the library, about 3.2 MiB held on every GPU
+ * fixed-size arrays compiled into the library, about 3.3 MiB held on every GPU
  * that loads it until the process exits.  Limits: n <= 16 solves, N <= 64,
  * n_models <= 8, and every problem must use GATO_MEM_DEVICE pointers; larger
  * or host problems return GATO_E_INVALID and launch nothing.  `results` is a
@@ -174,6 +176,56 @@ gato_status gato_solve_noalloc(const gato_model_desc* models, int32_t n_models,
                                const gato_solver_params* params,
                                const gato_problem* problems, int32_t n, int32_t max_sqp_iters,
                                gato_result* results, void* cuda_stream);
+
+/* ---- launch configuration and autotuning (Sec. III's M-block mapping made tunable) ----
+ * How solves map onto the GPU.  variant: 0 automatic, 1 the latency form (the
+ * PCG's block rows held in registers, one CTA per SM), 2 the throughput form
+ * (off-diagonal rows read from shared memory, two CTAs per SM).
+ * knots_per_cta: 0 = 35 (the most one CTA holds), 2..35 spreads each solve
+ * over more CTAs.  cluster: 0 = per solve, 1..8 = every solve uses this many
+ * CTAs where its horizon allows (a uniform batch is then a single launch).
+ * A cluster never exceeds 8 CTAs nor holds a CTA with fewer than 2 knots
+ * (except the last). */
+typedef struct {
+  int32_t variant;
+  int32_t knots_per_cta;
+  int32_t cluster;
+} gato_launch_config;
+
+/* Forces a launch configuration for later calls; cfg = NULL returns to the
+ * autotuned / automatic choice.  GATO_E_INVALID for out-of-range fields. */
+gato_status gato_set_launch_config(gato_batch* b, const gato_launch_config* cfg);
+
+/* Times every candidate configuration (both variants x knots per CTA
+ * {35, 24, 17, 12, 9, 6} x uniform clusters, skipping duplicates and
+ * throughput forms whose shared memory does not fit two CTAs per SM) on these
+ * problems for max_sqp_iters iterations, `reps` timed runs each after one
+ * warm-up, every run from the problems' current iterate (X, U, lambda are
+ * restored afterwards: the call leaves them unchanged).  The fastest median
+ * becomes the batch's choice for calls with the same batch-size bucket (next
+ * power of two) and horizon bucket (max N / 16, rounded up), unless a
+ * configuration is forced.  Writes the winner to *best and its median
+ * milliseconds to *best_ms (either may be NULL).  Synchronous. */
+gato_status gato_autotune(gato_batch* b, const gato_problem* problems, int32_t n, int32_t max_sqp_iters,
+                          int32_t reps, gato_launch_config* best, float* best_ms);
+
+/* ---- CUDA graph capture of a solve ----
+ * Captures gato_solve(problems, n, max_sqp_iters) into a CUDA graph (all
+ * cluster-size launches, forked and joined, plus the copy of the results to
+ * pinned memory).  Every problem must use device pointers; the graph keeps the
+ * pointers, so refill X, U, x_s, references in place between replays.  The
+ * graph uses the batch's workspace: its replays are ordered with the batch's
+ * stream (the replay waits for earlier work there, later work waits for it),
+ * and it must not run concurrently with other calls on the batch.  The
+ * configuration in force at capture time is baked in. */
+typedef struct gato_graph gato_graph;
+gato_status gato_graph_create(gato_batch* b, const gato_problem* problems, int32_t n,
+                              int32_t max_sqp_iters, gato_graph** out);
+/* Replays the graph.  results non-NULL: waits and fills results[0..n-1];
+ * NULL: returns at once, gato_graph_wait(g, results) waits later. */
+gato_status gato_graph_launch(gato_graph* g, gato_result* results);
+gato_status gato_graph_wait(gato_graph* g, gato_result* results);
+void gato_graph_destroy(gato_graph* g);
 
 /* Waits for the batch stream, at most timeout_us microseconds (< 0 = forever);
  * GATO_E_TIMEOUT leaves the work running.  Uses a polling host wait, never a
@@ -200,9 +252,18 @@ gato_status gato_last_transfer_bytes(const gato_batch* b, int64_t* h2d, int64_t*
 gato_status gato_debug_plain_stage(gato_batch* b, const gato_problem* problems, int32_t stop_stage,
                                    float* ws_out, int64_t ws_floats);
 
-/* Fills offsets[0..23] (floats) of the workspace arrays in the order
+/* Per-stage cycle counters of the fused kernel (clock64 deltas taken by the
+ * first thread of each solve's first CTA at stage boundaries).  enable = 1
+ * allocates and zeroes the counters; the following gato_solve calls add to
+ * them; enable = 0 copies n x 16 counters (cycles) to `cycles` if non-NULL and
+ * frees them.  Order: load, mass matrix, forward dynamics, value pass + cost,
+ * tangents, Jacobians, KKT, Schur, block inverse, PCG start, PCG S-phase,
+ * PCG y-phase, PCG w/z-phase, recovery, line search, accept. */
+gato_status gato_debug_stage_cycles(gato_batch* b, int32_t enable, int64_t* cycles, int32_t n);
+
+/* Fills offsets[0..24] (floats) of the workspace arrays in the order
  * X U dX dU Fq Fv Minv qdd dTau Qinv Rinv q r c Jk Linv links D L P vec scal
- * dres_x dres_u,
+ * dres_x dres_u nu,
  * and returns the workspace size in floats (or -1). */
 int64_t gato_debug_layout(const gato_batch* b, int64_t* offsets);
 

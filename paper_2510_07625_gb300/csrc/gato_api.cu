@@ -58,6 +58,17 @@ struct gato_batch {
   int last_n = 0;
   bool pending = false;
   std::vector<HostCopyBack> copy_back;
+  std::vector<int> N_h;   // horizon of each solve of the current call
+  long long* timing_d = nullptr;  // per-stage cycle counters while profiling is on
+  // launch plans: one set by gato_set_launch_config, else the autotuner's
+  // choice for the call's (batch size, horizon) bucket, else automatic
+  bool forced = false;
+  LaunchPlan forced_plan;
+  struct Tuned { int n_bucket, n_key; LaunchPlan plan; };
+  std::vector<Tuned> tuned;
+  LaunchPlan cur_plan;            // plan of the call being prepared
+  cudaStream_t aux[7] = {};       // fork streams for concurrent cluster-size groups
+  cudaEvent_t fork_ev[8] = {};
   int64_t h2d_bytes = 0, d2h_bytes = 0;
   std::string err;
 };
@@ -72,6 +83,28 @@ gato_status fail(gato_batch* b, gato_status s, const std::string& msg) {
 gato_status cuda_fail(gato_batch* b, cudaError_t e, const char* where) {
   std::string m = std::string(where) + ": " + cudaGetErrorString(e);
   return fail(b, GATO_E_CUDA, m);
+}
+
+int pow2_bucket(int n) {
+  int b = 1;
+  while (b < n) b <<= 1;
+  return b;
+}
+
+int horizon_key(int nmax) { return (nmax + 15) / 16; }
+
+LaunchPlan plan_for(const gato_batch* b, int n, int nmax) {
+  LaunchPlan p;
+  if (b->forced) {
+    p = b->forced_plan;
+  } else {
+    for (const auto& t : b->tuned)
+      if (t.n_bucket == pow2_bucket(n) && t.n_key == horizon_key(nmax)) p = t.plan;
+  }
+  p.aux = b->aux;
+  p.ev = b->fork_ev;
+  p.n_aux = b->aux[0] ? 7 : 0;
+  return p;
 }
 
 bool finite_all(const float* a, size_t n) {
@@ -252,11 +285,12 @@ gato_status prepare(gato_batch* b, const gato_problem* probs, int n, int* nmax_o
       b->d2h_bytes += (int64_t)(K * nx + (size_t)N * nu + (p.lambda ? K * nx : 0)) * 4;
     }
   }
-  // longest horizon first: long solves start in the first wave
-  std::vector<int> idx(n);
-  std::iota(idx.begin(), idx.end(), 0);
-  std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return probs[a].N > probs[c].N; });
-  for (int i = 0; i < n; ++i) b->order_h[i] = idx[i];
+  // grouped by cluster size, longest horizon first within a group: long solves
+  // start in the first wave
+  b->N_h.resize(n);
+  for (int i = 0; i < n; ++i) b->N_h[i] = probs[i].N;
+  b->cur_plan = plan_for(b, n, nmax);
+  order_solves(b->N_h.data(), n, b->order_h, b->cur_plan);
   cudaError_t e;
   if (staged > 0) {
     e = cudaMemcpyAsync(b->stage_d, b->stage_h, staged * sizeof(float), cudaMemcpyHostToDevice, b->stream);
@@ -289,6 +323,94 @@ gato_status finish_launch(gato_batch* b, int n, gato_result* results) {
     if (s != GATO_OK) return s;
     return gato_get_results(b, results, n);
   }
+  return GATO_OK;
+}
+
+// The fused launches of a prepared call (descriptors and order on the device).
+cudaError_t launch_solve(gato_batch* b, int n, int nmax, int iters) {
+  FusedLaunch a;
+  a.probs = b->probs_d;
+  a.models = b->models_d;
+  a.order = b->order_d;
+  a.results = b->res_d;
+  a.ws = b->ws_d;
+  a.ws_stride = b->ws_stride;
+  a.layout = b->layout;
+  a.n = n;
+  a.nmax = nmax;
+  a.csize = 1;
+  a.iters = iters;
+  a.prm = to_params(b->params, iters);
+  a.timing = b->timing_d;
+  a.variant = 0;
+  return launch_fused_grouped(a, b->order_h, b->order_d, b->N_h.data(), n, b->stream, b->cur_plan);
+}
+
+// Copies of the iterates (X, U, lambda) of a call's problems, so that the
+// autotuner can start every timed run from the same point.
+struct IterateSnapshot {
+  std::vector<std::vector<float>> host;
+  float* dev = nullptr;
+  std::vector<size_t> off;
+  ~IterateSnapshot() { cudaFree(dev); }
+};
+
+size_t iterate_floats(const gato_batch* b, const gato_problem& p, int part) {
+  const size_t nx = 2 * b->model_dof[p.model], K = p.N + 1;
+  return part == 1 ? (size_t)p.N * (nx / 2) : K * nx;
+}
+
+float* iterate_ptr(const gato_problem& p, int part) {
+  return part == 0 ? p.X : part == 1 ? p.U : p.lambda;
+}
+
+gato_status snapshot_take(gato_batch* b, const gato_problem* p, int n, IterateSnapshot& s) {
+  size_t total = 0;
+  s.off.assign((size_t)n * 3, 0);
+  s.host.assign((size_t)n * 3, {});
+  for (int i = 0; i < n; ++i)
+    for (int part = 0; part < 3; ++part) {
+      if (!iterate_ptr(p[i], part)) continue;
+      const size_t m = iterate_floats(b, p[i], part);
+      if (p[i].mem == GATO_MEM_DEVICE) {
+        s.off[i * 3 + part] = total;
+        total += m;
+      } else {
+        s.host[i * 3 + part].assign(iterate_ptr(p[i], part), iterate_ptr(p[i], part) + m);
+      }
+    }
+  if (total && cudaMalloc(&s.dev, total * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(b, GATO_E_NOMEM, "autotune snapshot");
+  }
+  for (int i = 0; i < n; ++i)
+    for (int part = 0; part < 3; ++part)
+      if (iterate_ptr(p[i], part) && p[i].mem == GATO_MEM_DEVICE &&
+          cudaMemcpyAsync(s.dev + s.off[i * 3 + part], iterate_ptr(p[i], part),
+                          iterate_floats(b, p[i], part) * sizeof(float), cudaMemcpyDeviceToDevice,
+                          b->stream) != cudaSuccess)
+        return cuda_fail(b, cudaGetLastError(), "autotune snapshot");
+  return GATO_OK;
+}
+
+gato_status snapshot_restore(gato_batch* b, const gato_problem* p, int n, const IterateSnapshot& s) {
+  if (b->pending) {
+    gato_status st = gato_sync(b, -1);
+    if (st != GATO_OK) return st;
+  }
+  for (int i = 0; i < n; ++i)
+    for (int part = 0; part < 3; ++part) {
+      float* dst = iterate_ptr(p[i], part);
+      if (!dst) continue;
+      const size_t m = iterate_floats(b, p[i], part);
+      if (p[i].mem == GATO_MEM_DEVICE) {
+        if (cudaMemcpyAsync(dst, s.dev + s.off[i * 3 + part], m * sizeof(float), cudaMemcpyDeviceToDevice,
+                            b->stream) != cudaSuccess)
+          return cuda_fail(b, cudaGetLastError(), "autotune restore");
+      } else {
+        std::memcpy(dst, s.host[i * 3 + part].data(), m * sizeof(float));
+      }
+    }
   return GATO_OK;
 }
 
@@ -348,7 +470,7 @@ gato_status gato_create_batch(const gato_batch_desc* desc, void* cuda_stream, ga
     return GATO_E_INVALID;
   }
   const int nmax = desc->max_horizon;
-  b->layout = ws_layout(nmax, nmax > SMEM_BLOCKS_NMAX, false);
+  b->layout = ws_layout(nmax, false, false);
   b->ws_stride = b->layout.total;
   b->plain_layout = ws_layout(nmax, true, true);
   b->stage_stride = stage_floats(nmax);
@@ -366,6 +488,10 @@ gato_status gato_create_batch(const gato_batch_desc* desc, void* cuda_stream, ga
   ok = ok && cudaMallocHost(&b->res_h, nb * sizeof(Result)) == cudaSuccess;
   ok = ok && cudaMallocHost(&b->stage_h, nb * b->stage_stride * sizeof(float)) == cudaSuccess;
   ok = ok && cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; i < 7 && ok; ++i)
+    ok = cudaStreamCreateWithFlags(&b->aux[i], cudaStreamNonBlocking) == cudaSuccess;
+  for (int i = 0; i < 8 && ok; ++i)
+    ok = cudaEventCreateWithFlags(&b->fork_ev[i], cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     gato_destroy_batch(b);
@@ -392,11 +518,16 @@ void gato_destroy_batch(gato_batch* b) {
   cudaFree(b->ws_d);
   cudaFree(b->plain_ws_d);
   cudaFree(b->stage_d);
+  cudaFree(b->timing_d);
   cudaFreeHost(b->probs_h);
   cudaFreeHost(b->order_h);
   cudaFreeHost(b->res_h);
   cudaFreeHost(b->stage_h);
   if (b->done) cudaEventDestroy(b->done);
+  for (int i = 0; i < 7; ++i)
+    if (b->aux[i]) cudaStreamDestroy(b->aux[i]);
+  for (int i = 0; i < 8; ++i)
+    if (b->fork_ev[i]) cudaEventDestroy(b->fork_ev[i]);
   delete b;
 }
 
@@ -407,22 +538,7 @@ gato_status gato_solve(gato_batch* b, const gato_problem* problems, int32_t n,
   int nmax = 0;
   gato_status s = prepare(b, problems, n, &nmax);
   if (s != GATO_OK) return s;
-  FusedLaunch a;
-  a.probs = b->probs_d;
-  a.models = b->models_d;
-  a.order = b->order_d;
-  a.results = b->res_d;
-  a.ws = b->ws_d;
-  a.ws_stride = b->ws_stride;
-  a.layout = b->layout;
-  a.n = n;
-  a.nmax = nmax;
-  a.iters = max_sqp_iters;
-  a.prm = to_params(b->params, max_sqp_iters);
-  a.threads = 0;
-  if (nmax > SMEM_BLOCKS_NMAX && b->layout.Dm == 0)
-    return fail(b, GATO_E_INVALID, "horizon too long for this batch");
-  cudaError_t e = launch_fused(a, b->stream);
+  cudaError_t e = launch_solve(b, n, nmax, max_sqp_iters);
   if (e != cudaSuccess) return cuda_fail(b, e, "launch fused kernel");
   return finish_launch(b, n, results);
 }
@@ -440,8 +556,8 @@ gato_status gato_solve_plain(gato_batch* b, const gato_problem* problems, int32_
   if (s != GATO_OK) return s;
   const Params prm = to_params(b->params, max_sqp_iters);
   for (int i = 0; i < n; ++i) {
-    cudaError_t e = launch_plain(b->probs_d, b->models_d, b->res_d, i, b->plain_ws_d, b->plain_layout,
-                                 b->max_horizon, max_sqp_iters, prm, -1, b->stream);
+    cudaError_t e = launch_plain(b->probs_d, b->models_d, b->res_d, i, b->N_h[i], b->plain_ws_d,
+                                 b->plain_layout, b->max_horizon, max_sqp_iters, prm, -1, b->stream);
     if (e != cudaSuccess) return cuda_fail(b, e, "launch plain stages");
   }
   return finish_launch(b, n, results);
@@ -501,10 +617,10 @@ int64_t gato_debug_layout(const gato_batch* b, int64_t* o) {
   if (!b || !o) return -1;
   const WsLayout& L = b->plain_layout;
   const size_t K = b->max_horizon + 1;
-  const size_t v[24] = {L.X,  L.U,  L.dX, L.dU, L.Fq, L.Fv, L.Mi, L.qdd, L.dT, L.Qi, L.Ri, L.qg,
-                        L.rg, L.cv, L.Jk, L.Li, L.LV, L.Dm, L.Lm, L.Pm, L.vec, L.vec + 12 * K * VS,
-                        L.Dx, L.Du};
-  for (int i = 0; i < 24; ++i) o[i] = (int64_t)v[i];
+  const size_t v[25] = {L.X,  L.U,  L.dX, L.dU, L.Fq, L.Fv, L.Mi, L.qdd, L.dT, L.Qi, L.Ri, L.qg, L.rg,
+                        L.cv, L.Jk, L.Li, L.LV, L.Dm, L.Lm, L.Pm, L.vec, L.vec + NVEC * (K + 2) * VS,
+                        L.Dx, L.Du, L.nu};
+  for (int i = 0; i < 25; ++i) o[i] = (int64_t)v[i];
   return (int64_t)L.total;
 }
 
@@ -517,8 +633,8 @@ gato_status gato_debug_plain_stage(gato_batch* b, const gato_problem* problems, 
   gato_status s = prepare(b, problems, 1, &nmax);
   if (s != GATO_OK) return s;
   const Params prm = to_params(b->params, 1);
-  cudaError_t e = launch_plain(b->probs_d, b->models_d, b->res_d, 0, b->plain_ws_d, b->plain_layout,
-                               b->max_horizon, 1, prm, stop_stage, b->stream);
+  cudaError_t e = launch_plain(b->probs_d, b->models_d, b->res_d, 0, b->N_h[0], b->plain_ws_d,
+                               b->plain_layout, b->max_horizon, 1, prm, stop_stage, b->stream);
   if (e != cudaSuccess) return cuda_fail(b, e, "launch plain stages");
   e = cudaMemcpyAsync(ws_out, b->plain_ws_d, b->plain_layout.total * sizeof(float),
                       cudaMemcpyDeviceToHost, b->stream);
@@ -526,6 +642,309 @@ gato_status gato_debug_plain_stage(gato_batch* b, const gato_problem* problems, 
   e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return cuda_fail(b, e, "stage run");
   b->copy_back.clear();
+  return GATO_OK;
+}
+
+gato_status gato_debug_stage_cycles(gato_batch* b, int32_t enable, int64_t* cycles, int32_t n) {
+  if (!b) return GATO_E_INVALID;
+  if (b->pending) {
+    gato_status s = gato_sync(b, -1);
+    if (s != GATO_OK) return s;
+  }
+  const size_t bytes = (size_t)b->max_batch * T_COUNT * sizeof(long long);
+  if (enable) {
+    if (!b->timing_d && cudaMalloc(&b->timing_d, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(b, GATO_E_NOMEM, "timing buffer");
+    }
+    if (cudaMemsetAsync(b->timing_d, 0, bytes, b->stream) != cudaSuccess) return GATO_E_CUDA;
+    return GATO_OK;
+  }
+  if (!b->timing_d) return fail(b, GATO_E_INVALID, "stage timing was not enabled");
+  if (cycles) {
+    if (n < 1 || n > b->max_batch) return fail(b, GATO_E_INVALID, "bad solve count");
+    std::vector<long long> h((size_t)n * T_COUNT);
+    if (cudaMemcpy(h.data(), b->timing_d, h.size() * sizeof(long long), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return GATO_E_CUDA;
+    for (size_t i = 0; i < h.size(); ++i) cycles[i] = h[i];
+  }
+  cudaFree(b->timing_d);
+  b->timing_d = nullptr;
+  return GATO_OK;
+}
+
+struct gato_graph {
+  gato_batch* b = nullptr;
+  int n = 0;
+  ProbDesc* probs_d = nullptr;
+  int* order_d = nullptr;
+  Result* res_d = nullptr;
+  Result* res_h = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t in = nullptr, out = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool pending = false;
+};
+
+void gato_graph_destroy(gato_graph* g) {
+  if (!g) return;
+  if (g->pending && g->out) cudaEventSynchronize(g->out);
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  if (g->in) cudaEventDestroy(g->in);
+  if (g->out) cudaEventDestroy(g->out);
+  if (g->stream) cudaStreamDestroy(g->stream);
+  cudaFree(g->probs_d);
+  cudaFree(g->order_d);
+  cudaFree(g->res_d);
+  cudaFreeHost(g->res_h);
+  delete g;
+}
+
+gato_status gato_graph_create(gato_batch* b, const gato_problem* problems, int32_t n,
+                              int32_t max_sqp_iters, gato_graph** out) {
+  if (!out) return GATO_E_INVALID;
+  *out = nullptr;
+  if (!b) return GATO_E_INVALID;
+  if (max_sqp_iters < 1) return fail(b, GATO_E_INVALID, "max_sqp_iters must be >= 1");
+  if (!problems || n < 1 || n > b->max_batch) return fail(b, GATO_E_INVALID, "bad problem count");
+  for (int i = 0; i < n; ++i)
+    if (problems[i].mem != GATO_MEM_DEVICE)
+      return fail(b, GATO_E_INVALID, "a captured solve needs device problems");
+  int nmax = 0;
+  gato_status s = prepare(b, problems, n, &nmax);
+  if (s != GATO_OK) return s;
+  gato_graph* g = new (std::nothrow) gato_graph();
+  if (!g) return GATO_E_NOMEM;
+  g->b = b;
+  g->n = n;
+  bool ok = cudaMalloc(&g->probs_d, n * sizeof(ProbDesc)) == cudaSuccess &&
+            cudaMalloc(&g->order_d, n * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&g->res_d, n * sizeof(Result)) == cudaSuccess &&
+            cudaMallocHost(&g->res_h, n * sizeof(Result)) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&g->in, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&g->out, cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    gato_graph_destroy(g);
+    return fail(b, GATO_E_NOMEM, "graph buffers");
+  }
+  // the graph owns its descriptors: later calls on the batch rewrite the batch's
+  cudaError_t e = cudaMemcpyAsync(g->probs_d, b->probs_h, n * sizeof(ProbDesc), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(g->order_d, b->order_h, n * sizeof(int), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  size_t smem = 0;
+  for (int i = 0; i < n; ++i)
+    smem = std::max(smem, fused_smem_bytes(problems[i].N, cluster_size(problems[i].N, b->cur_plan.knots_per_cta,
+                                                                        b->cur_plan.cluster)));
+  if (e == cudaSuccess) e = configure_fused(smem);
+  if (e != cudaSuccess) {
+    gato_graph_destroy(g);
+    return cuda_fail(b, e, "graph set-up");
+  }
+  b->copy_back.clear();
+  FusedLaunch a;
+  a.probs = g->probs_d;
+  a.models = b->models_d;
+  a.order = g->order_d;
+  a.results = g->res_d;
+  a.ws = b->ws_d;
+  a.ws_stride = b->ws_stride;
+  a.layout = b->layout;
+  a.n = n;
+  a.nmax = nmax;
+  a.csize = 1;
+  a.iters = max_sqp_iters;
+  a.prm = to_params(b->params, max_sqp_iters);
+  a.timing = nullptr;
+  a.variant = 0;
+  e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t le = launch_fused_grouped(a, b->order_h, g->order_d, b->N_h.data(), n, g->stream, b->cur_plan);
+    if (le == cudaSuccess)
+      le = cudaMemcpyAsync(g->res_h, g->res_d, n * sizeof(Result), cudaMemcpyDeviceToHost, g->stream);
+    e = cudaStreamEndCapture(g->stream, &g->graph);
+    if (le != cudaSuccess) e = le;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    gato_graph_destroy(g);
+    return cuda_fail(b, e, "graph capture");
+  }
+  *out = g;
+  return GATO_OK;
+}
+
+gato_status gato_graph_wait(gato_graph* g, gato_result* results) {
+  if (!g) return GATO_E_INVALID;
+  if (g->pending) {
+    cudaError_t e = cudaEventSynchronize(g->out);
+    g->pending = false;
+    if (e != cudaSuccess) return cuda_fail(g->b, e, "graph replay");
+  }
+  if (results)
+    for (int i = 0; i < g->n; ++i) {
+      results[i].flags = g->res_h[i].flags;
+      results[i].sqp_iters = g->res_h[i].sqp_iters;
+      results[i].pcg_iters = g->res_h[i].pcg_iters;
+      results[i].kkt_residual = g->res_h[i].kkt;
+      results[i].merit = g->res_h[i].merit;
+    }
+  return GATO_OK;
+}
+
+gato_status gato_graph_launch(gato_graph* g, gato_result* results) {
+  if (!g) return GATO_E_INVALID;
+  gato_batch* b = g->b;
+  if (g->pending) {
+    gato_status s = gato_graph_wait(g, nullptr);
+    if (s != GATO_OK) return s;
+  }
+  if (b->pending) {
+    gato_status s = gato_sync(b, -1);
+    if (s != GATO_OK) return s;
+  }
+  // ordered after earlier work on the batch's stream, and later work after it
+  cudaError_t e = cudaEventRecord(g->in, b->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(g->stream, g->in, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(g->exec, g->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(g->out, g->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, g->out, 0);
+  if (e != cudaSuccess) return cuda_fail(b, e, "graph launch");
+  g->pending = true;
+  return results ? gato_graph_wait(g, results) : GATO_OK;
+}
+
+gato_status gato_set_launch_config(gato_batch* b, const gato_launch_config* cfg) {
+  if (!b) return GATO_E_INVALID;
+  if (!cfg) {
+    b->forced = false;
+    return GATO_OK;
+  }
+  if (cfg->variant < 0 || cfg->variant > 2 || cfg->knots_per_cta == 1 || cfg->knots_per_cta < 0 ||
+      cfg->knots_per_cta > KPC_MAX || cfg->cluster < 0 || cfg->cluster > 8)
+    return fail(b, GATO_E_INVALID, "launch config out of range");
+  b->forced = true;
+  b->forced_plan = LaunchPlan();
+  b->forced_plan.variant = cfg->variant;
+  b->forced_plan.knots_per_cta = cfg->knots_per_cta;
+  b->forced_plan.cluster = cfg->cluster;
+  return GATO_OK;
+}
+
+gato_status gato_autotune(gato_batch* b, const gato_problem* problems, int32_t n, int32_t max_sqp_iters,
+                          int32_t reps, gato_launch_config* best, float* best_ms) {
+  if (!b) return GATO_E_INVALID;
+  if (max_sqp_iters < 1 || reps < 1) return fail(b, GATO_E_INVALID, "max_sqp_iters and reps must be >= 1");
+  if (!problems || n < 1 || n > b->max_batch) return fail(b, GATO_E_INVALID, "bad problem count");
+  for (int i = 0; i < n; ++i) {
+    gato_status s = validate_problem(b, problems[i], i);
+    if (s != GATO_OK) return s;
+  }
+  if (b->pending) {
+    gato_status s = gato_sync(b, -1);
+    if (s != GATO_OK) return s;
+  }
+  int nmax = 1;
+  for (int i = 0; i < n; ++i) nmax = std::max(nmax, (int)problems[i].N);
+  IterateSnapshot snap;
+  gato_status s = snapshot_take(b, problems, n, snap);
+  if (s != GATO_OK) return s;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess) {
+    if (t0) cudaEventDestroy(t0);
+    cudaGetLastError();
+    return fail(b, GATO_E_NOMEM, "autotune events");
+  }
+  const bool was_forced = b->forced;
+  const LaunchPlan was_plan = b->forced_plan;
+  // candidates: both kernel forms x knots per CTA; configurations that give
+  // every solve the same cluster sizes as an earlier one are skipped
+  const int kpcs[] = {0, 24, 17, 12, 9, 6};
+  int cmax = 1;
+  for (int i = 0; i < n; ++i) cmax = std::max(cmax, cluster_for(problems[i].N));
+  struct Cand { int kpc, cluster; };
+  std::vector<Cand> cands;
+  for (int k : kpcs) cands.push_back({k, 0});
+  for (int c = cmax; c <= 8; c *= 2) cands.push_back({0, c});  // one launch for the whole batch
+  std::vector<std::vector<int>> seen;
+  float best_t = -1.f;
+  LaunchPlan best_p;
+  gato_status st = GATO_OK;
+  for (int variant = 1; variant <= 2 && st == GATO_OK; ++variant) {
+    seen.clear();
+    for (const Cand& cd : cands) {
+      std::vector<int> sizes(n);
+      size_t smem_max = 0;
+      for (int i = 0; i < n; ++i) {
+        sizes[i] = cluster_size(problems[i].N, cd.kpc, cd.cluster);
+        smem_max = std::max(smem_max, fused_smem_bytes(problems[i].N, sizes[i]));
+      }
+      if (std::find(seen.begin(), seen.end(), sizes) != seen.end()) continue;
+      seen.push_back(sizes);
+      // the throughput form only pays when two CTAs fit an SM
+      if (variant == 2 && 2 * (smem_max + 1024) > 233472) continue;
+      b->forced = true;
+      b->forced_plan = LaunchPlan();
+      b->forced_plan.variant = variant;
+      b->forced_plan.knots_per_cta = cd.kpc;
+      b->forced_plan.cluster = cd.cluster;
+      std::vector<float> ts;
+      for (int r = 0; r <= reps && st == GATO_OK; ++r) {  // r = 0 warms up
+        st = snapshot_restore(b, problems, n, snap);
+        if (st != GATO_OK) break;
+        int nm = 0;
+        st = prepare(b, problems, n, &nm);
+        if (st != GATO_OK) break;
+        cudaError_t e = cudaEventRecord(t0, b->stream);
+        if (e == cudaSuccess) e = launch_solve(b, n, nm, max_sqp_iters);
+        if (e == cudaSuccess) e = cudaEventRecord(t1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+        if (e != cudaSuccess) {
+          st = cuda_fail(b, e, "autotune run");
+          break;
+        }
+        b->copy_back.clear();
+        if (r > 0) ts.push_back(ms);
+      }
+      if (st != GATO_OK) break;
+      std::sort(ts.begin(), ts.end());
+      const float med = ts[ts.size() / 2];
+      if (best_t < 0.f || med < best_t) {
+        best_t = med;
+        best_p = b->forced_plan;
+      }
+    }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  b->forced = was_forced;
+  b->forced_plan = was_plan;
+  gato_status rs = snapshot_restore(b, problems, n, snap);
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess && rs == GATO_OK)
+    rs = cuda_fail(b, cudaGetLastError(), "autotune restore");
+  if (st != GATO_OK) return st;
+  if (rs != GATO_OK) return rs;
+  const int nb = pow2_bucket(n), nk = horizon_key(nmax);
+  b->tuned.erase(std::remove_if(b->tuned.begin(), b->tuned.end(),
+                                [&](const gato_batch::Tuned& t) { return t.n_bucket == nb && t.n_key == nk; }),
+                 b->tuned.end());
+  best_p.aux = nullptr;
+  best_p.ev = nullptr;
+  best_p.n_aux = 0;
+  b->tuned.push_back({nb, nk, best_p});
+  if (best) {
+    best->variant = best_p.variant;
+    best->knots_per_cta = best_p.knots_per_cta;
+    best->cluster = best_p.cluster;
+  }
+  if (best_ms) *best_ms = best_t;
   return GATO_OK;
 }
 

@@ -1,5 +1,5 @@
-// Internal launch interface between the C ABI (gato_api.cu) and the kernels
-// (gato_kernels.cu).  Not part of the public header.
+// Internal launch interface between the C ABI (gato_api.cu, gato_static.cu)
+// and the kernels (gato_kernels.cu).  Not part of the public header.
 #pragma once
 
 #include <cstddef>
@@ -10,39 +10,70 @@
 
 namespace gato {
 
-// Largest horizon whose Schur/preconditioner blocks fit in one CTA's shared memory.
-constexpr int SMEM_BLOCKS_NMAX = 75;
 // Opt-in shared memory per CTA on sm_103a (227 KB).
 constexpr size_t SMEM_LIMIT_BYTES = 232448;
-// Largest horizon the library accepts.
+// Largest horizon the library accepts (8 CTAs of KPC_MAX knots).
 constexpr int NMAX_LIMIT = 256;
 
 struct FusedLaunch {
-  const ProbDesc* probs;   // device [n]
+  const ProbDesc* probs;   // device [n_total]
   const DevModel* models;  // device
-  const int* order;        // device [n] or null
-  Result* results;         // device [n]
+  const int* order;        // device: solve index of each cluster
+  Result* results;         // device [n_total]
   float* ws;               // device workspace base
   size_t ws_stride;        // floats per solve
   WsLayout layout;         // layout of one solve's workspace
-  int n;                   // solves
-  int nmax;                // largest N in this launch (sets shared-memory layout)
+  int n;                   // clusters (solves) in this launch
+  int nmax;                // largest N in this launch (sets the shared-memory layout)
+  int csize;               // CTAs per cluster
   int iters;
   Params prm;
-  int threads;             // 0 = automatic
+  long long* timing;       // device [n_total][T_COUNT] cycle counters, or null
+  int variant;             // 0 = automatic, 1 = register rows (1 CTA/SM), 2 = 2 CTAs/SM
 };
 
-// One persistent fused launch: grid = n CTAs, one solve per CTA.
+// How solves map onto the GPU: the space the autotuner searches.
+struct LaunchPlan {
+  int variant = 0;        // 0 automatic, 1 block rows in registers (1 CTA/SM), 2 two CTAs/SM
+  int knots_per_cta = 0;  // 0 = KPC_MAX; smaller values spread a solve over more CTAs
+  int cluster = 0;        // > 0: every solve uses this many CTAs where it can (one launch)
+  // optional fork streams: cluster-size groups run concurrently on these
+  // (joined back into the caller's stream with the events)
+  const cudaStream_t* aux = nullptr;
+  const cudaEvent_t* ev = nullptr;  // [n_aux + 1]
+  int n_aux = 0;
+};
+
+int num_sms();
+bool use_throughput_variant(int n, int csize, int variant, size_t smem);
+
+// CTAs per cluster for horizon N under a knots-per-CTA target (0 = KPC_MAX):
+// at least cluster_for(N), at most 8, and never a CTA without knots.
+int cluster_size(int N, int knots_per_cta, int cluster = 0);
+
+// Sets the shared-memory attribute of both kernel forms for launches of up to
+// `smem` bytes (done by the launcher on demand; call it before stream capture).
+cudaError_t configure_fused(size_t smem);
+
+// One persistent fused launch: n clusters of csize CTAs, one solve each.
 cudaError_t launch_fused(const FusedLaunch& a, cudaStream_t s);
+
+// Launches the solves in `order_host` (sorted by cluster size, then horizon,
+// both descending; order_dev is its device copy) as one launch per cluster
+// size.  N_of[i] is the horizon of solve i.
+cudaError_t launch_fused_grouped(FusedLaunch base, const int* order_host, const int* order_dev,
+                                 const int* N_of, int n, cudaStream_t s, const LaunchPlan& plan);
+
+// Sorts solve indices by (cluster size, horizon), both descending, stable.
+void order_solves(const int* N_of, int n, int* order, const LaunchPlan& plan);
 
 // Plain form: every stage of every SQP iteration of solve `b` is its own launch.
 // `ws` must have the layout ws_layout(nmax, true, true).
 cudaError_t launch_plain(const ProbDesc* probs, const DevModel* models, Result* results, int b,
-                         float* ws, const WsLayout& L, int nmax, int iters, const Params& prm,
+                         int N_b, float* ws, const WsLayout& L, int nmax, int iters, const Params& prm,
                          int stop_stage, cudaStream_t s);
 
-int fused_threads_for(int nmax);
-size_t fused_smem_bytes(int nmax);
+size_t fused_smem_bytes(int nmax, int csize);
 
 enum PlainStage : int {
   PS_LOAD = 0, PS_MASS, PS_FD, PS_VALUE, PS_TANGENT, PS_JAC, PS_KKT, PS_SCHUR, PS_BINV, PS_PCG,

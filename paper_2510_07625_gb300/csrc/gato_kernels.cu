@@ -1,25 +1,159 @@
-// Launchers of the batched SQP kernels (plain form and dispatch of the fused form).
+// The batched SQP kernels and their launchers.
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
 #include "gato_kernels.cuh"
 
 namespace gato {
 
-int fused_threads_for(int nmax) { return nmax <= 35 ? 288 : 544; }
+size_t fused_smem_bytes(int nmax, int csize) {
+  return smem_floats(kpc_for(nmax, csize)) * sizeof(float);
+}
 
-size_t fused_smem_bytes(int nmax) {
-  return smem_floats(nmax, nmax <= SMEM_BLOCKS_NMAX) * sizeof(float);
+int cluster_size(int N, int knots_per_cta, int cluster) {
+  int c = cluster_for(N);
+  if (knots_per_cta >= 2) c = std::max(c, (N + 1 + knots_per_cta - 1) / knots_per_cta);
+  if (cluster > 0) c = std::max(c, cluster);
+  c = std::min(c, 8);
+  c = std::max(cluster_for(N), std::min(c, std::max(1, (N + 1) / 2)));  // at least 2 knots per CTA
+  // every CTA but the last holds kpc >= 2 knots, the last at least one
+  const int kpc = kpc_for(N, c);
+  return (N + 1 + kpc - 1) / kpc;
+}
+
+void order_solves(const int* N_of, int n, int* order, const LaunchPlan& plan) {
+  std::vector<int> idx(n);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+    const int ca = cluster_size(N_of[a], plan.knots_per_cta, plan.cluster);
+    const int cb = cluster_size(N_of[b], plan.knots_per_cta, plan.cluster);
+    if (ca != cb) return ca > cb;
+    return N_of[a] > N_of[b];
+  });
+  for (int i = 0; i < n; ++i) order[i] = idx[i];
+}
+
+int num_sms() {
+  static int sms[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  if (!sms[dev]) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    sms[dev] = v > 0 ? v : 1;
+  }
+  return sms[dev];
+}
+
+static size_t g_configured[2][64] = {};
+
+template <bool REG>
+static cudaError_t configure_t(size_t smem) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  size_t& done = g_configured[REG ? 0 : 1][dev];
+  if (smem > done) {
+    e = cudaFuncSetAttribute(sqp_fused<REG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    done = smem;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t configure_fused(size_t smem) {
+  if (smem > SMEM_LIMIT_BYTES) return cudaErrorInvalidValue;
+  cudaError_t e = configure_t<true>(smem);
+  if (e != cudaSuccess) return e;
+  num_sms();
+  return configure_t<false>(smem);
+}
+
+template <bool REG>
+static cudaError_t launch_fused_t(const FusedLaunch& a, size_t smem, cudaStream_t s) {
+  cudaError_t e = configure_t<REG>(smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(a.n * a.csize));
+  cfg.blockDim = dim3(NTHR);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)a.csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, sqp_fused<REG>, a);
+}
+
+bool use_throughput_variant(int n, int csize, int variant, size_t smem) {
+  if (variant == 1) return false;
+  if (variant == 2) return true;
+  // more CTAs than one per SM, and two of them fit an SM's shared memory
+  // (228 KB, 1 KB reserved per CTA): two CTAs per SM halve the waves
+  return (long long)n * csize > num_sms() && 2 * (smem + 1024) <= 233472;
 }
 
 cudaError_t launch_fused(const FusedLaunch& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  const bool sb = a.nmax <= SMEM_BLOCKS_NMAX;
-  const int nt = a.threads > 0 ? a.threads : fused_threads_for(a.nmax);
-  const size_t smem = smem_floats(a.nmax, sb) * sizeof(float);
+  if (a.csize < 1 || a.csize > 8) return cudaErrorInvalidValue;
+  const size_t smem = fused_smem_bytes(a.nmax, a.csize);
   if (smem > SMEM_LIMIT_BYTES) return cudaErrorInvalidValue;
-  if (nt == 288) return launch_fused_288(a, smem, sb, s);
-  return launch_fused_544(a, smem, sb, s);
+  if (use_throughput_variant(a.n, a.csize, a.variant, smem)) return launch_fused_t<false>(a, smem, s);
+  return launch_fused_t<true>(a, smem, s);
 }
+
+cudaError_t launch_fused_grouped(FusedLaunch base, const int* order_host, const int* order_dev,
+                                 const int* N_of, int n, cudaStream_t s, const LaunchPlan& plan) {
+  struct Group { int g0, g1, c; };
+  Group groups[8];
+  int ng = 0;
+  for (int g0 = 0; g0 < n;) {
+    const int c = cluster_size(N_of[order_host[g0]], plan.knots_per_cta, plan.cluster);
+    int g1 = g0 + 1;
+    while (g1 < n && cluster_size(N_of[order_host[g1]], plan.knots_per_cta, plan.cluster) == c) ++g1;
+    if (ng == 8) return cudaErrorInvalidValue;  // sizes are distinct and in 1..8
+    groups[ng++] = {g0, g1, c};
+    g0 = g1;
+  }
+  base.variant = plan.variant;
+  const bool fork = ng > 1 && plan.n_aux > 0 && plan.aux && plan.ev;
+  cudaError_t e;
+  if (fork) {
+    e = cudaEventRecord(plan.ev[plan.n_aux], s);
+    if (e != cudaSuccess) return e;
+  }
+  for (int i = 0; i < ng; ++i) {
+    FusedLaunch a = base;
+    a.order = order_dev + groups[i].g0;
+    a.n = groups[i].g1 - groups[i].g0;
+    a.csize = groups[i].c;
+    a.nmax = N_of[order_host[groups[i].g0]];
+    // the first group stays on the caller's stream, the others fork off it
+    cudaStream_t si = s;
+    if (fork && i > 0 && i - 1 < plan.n_aux) {
+      si = plan.aux[i - 1];
+      e = cudaStreamWaitEvent(si, plan.ev[plan.n_aux], 0);
+      if (e != cudaSuccess) return e;
+    }
+    e = launch_fused(a, si);
+    if (e != cudaSuccess) return e;
+    if (si != s) {
+      e = cudaEventRecord(plan.ev[i - 1], si);
+      if (e != cudaSuccess) return e;
+      e = cudaStreamWaitEvent(s, plan.ev[i - 1], 0);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_plain(const ProbDesc* probs, const DevModel* models, Result* results, int b,
-                         float* ws, const WsLayout& L, int nmax, int iters, const Params& prm,
+                         int N_b, float* ws, const WsLayout& L, int nmax, int iters, const Params& prm,
                          int stop_stage, cudaStream_t s) {
   PlainArgs a;
   a.probs = probs;
@@ -32,14 +166,20 @@ cudaError_t launch_plain(const ProbDesc* probs, const DevModel* models, Result* 
   a.iters = iters;
   a.prm = prm;
   a.it = 0;
-  const int nt = fused_threads_for(nmax);
-  auto go = [&](int stage) -> cudaError_t {
-    if (nt == 288)
-      sqp_plain_stage<288><<<1, 288, 0, s>>>(stage, a);
-    else
-      sqp_plain_stage<544><<<1, 544, 0, s>>>(stage, a);
-    return cudaGetLastError();
-  };
+  a.csize = cluster_for(N_b);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)a.csize);
+  cfg.blockDim = dim3(NTHR);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)a.csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  auto go = [&](int stage) -> cudaError_t { return cudaLaunchKernelEx(&cfg, sqp_plain_stage, stage, a); };
   cudaError_t e = go(PS_LOAD);
   if (e != cudaSuccess) return e;
   for (int it = 0;; ++it) {

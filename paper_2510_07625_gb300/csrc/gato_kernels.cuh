@@ -1,15 +1,17 @@
 // Kernel templates of the batched SQP solver (GATO, arXiv 2510.07625, Alg. 1).
 //
-// sqp_fused: the persistent fused form.  One CTA per solve runs every SQP
-//   iteration of that solve (linearise -> Schur -> PCG -> recover -> line
-//   search) with the PCG working set in shared memory, and exits on its own
-//   convergence.  Blocks are launched longest horizon first.
+// sqp_fused: the persistent fused form.  One thread-block cluster per solve
+//   runs every SQP iteration of that solve (linearise -> Schur -> PCG ->
+//   recover -> line search) with the PCG working set on chip (block rows in
+//   registers, vectors in shared memory) and exits on its own convergence.
+//   Clusters are launched longest horizon first.
 // sqp_plain_stage: the plain form used as the comparison baseline.  The same
 //   stage functions, but each stage of each SQP iteration of one solve is a
-//   separate single-CTA launch and every array lives in global memory.
+//   separate launch and every array lives in global memory.
 #pragma once
 
 #include "gato_internal.h"
+#include "gato_phases.cuh"
 
 namespace gato {
 
@@ -32,6 +34,7 @@ __device__ __forceinline__ void bind_workspace(Ctx& C, float* ws, const WsLayout
   C.Li = ws + L.Li;
   C.Dx = ws + L.Dx;
   C.Du = ws + L.Du;
+  C.nu = ws + L.nu;
   C.LV = reinterpret_cast<LinkRec*>(ws + L.LV);
 }
 
@@ -47,45 +50,49 @@ __device__ __forceinline__ void bind_problem(Ctx& C, const ProbDesc& P, const De
   C.M = M;
 }
 
-__device__ __forceinline__ void bind_vectors(Ctx& C, float* v, size_t VV) {
-  C.nu = v;
-  C.rr = v + VV;
-  C.pb0 = v + 2 * VV;
-  C.pb1 = v + 3 * VV;
-  C.qv = v + 4 * VV;
-  C.yv = v + 5 * VV;
-  C.wv = v + 6 * VV;
-  C.zv = v + 7 * VV;
-  C.rhs = v + 8 * VV;
-  C.dnu = v + 9 * VV;
-}
-
-__device__ __forceinline__ int sflags(const Ctx& C) {
-  return *reinterpret_cast<volatile int*>(C.scal + S_FLAGS);
+// Knot range of cluster rank r for a solve of horizon N on csize CTAs.
+__device__ __forceinline__ void bind_partition(Ctx& C, int rank, int csize) {
+  const int kpc = kpc_for(C.N, csize);
+  const int K = C.N + 1;
+  C.rank = rank;
+  C.csize = csize;
+  C.k0 = min(rank * kpc, K);
+  C.k1 = min(C.k0 + kpc, K);
 }
 
 // The whole SQP loop of one solve (Sec. II-A Steps 1-3, repeated).
-template <int NT>
+template <bool REG>
 __device__ void sqp_solve(Ctx& C, const ProbDesc& P, const Params& prm, int iters, Result* out) {
-  load_iterate<NT>(C, P);
+  int rbuf = 0;
+  long long tl = C.tm ? clock64() : 0;
+  load_iterate(C, P);
+  csync(C);
+  tstamp(C, T_LOAD, tl);
   int flags = 0, sqp = 0, pcg_total = 0;
   float kkt = 0.f, merit = 0.f;
   for (int it = 0;; ++it) {
     if (it == iters && !(prm.kkt_tol > 0.f)) break;
-    st_mass_bias<NT>(C);
+    st_mass_bias(C);
     __syncthreads();
-    st_forward_dynamics<NT>(C);
+    tstamp(C, T_MASS, tl);
+    st_forward_dynamics(C);
     __syncthreads();
-    st_value_and_cost<NT>(C);
+    tstamp(C, T_FD, tl);
+    st_value_and_cost(C);
     __syncthreads();
-    st_tangents<NT>(C);
+    tstamp(C, T_VALUE, tl);
+    st_tangents(C);
     __syncthreads();
-    st_dyn_jacobians<NT>(C);
-    __syncthreads();
-    st_kkt_merit<NT>(C, prm.mu);
+    tstamp(C, T_TANGENT, tl);
+    st_dyn_jacobians(C);
+    csync(C);  // defect c_k0 comes from the neighbour's last knot
+    tstamp(C, T_JAC, tl);
+    st_kkt_merit(C, prm.mu, rbuf);
+    tstamp(C, T_KKT, tl);
     kkt = C.scal[S_KKT];
     merit = C.scal[S_MERIT0];
-    if (sflags(C)) {
+    // the KKT stage left the cluster-wide non-finite flag in every CTA
+    if (*reinterpret_cast<volatile int*>(C.scal + S_FLAGS)) {
       flags |= F_NONFINITE;
       break;
     }
@@ -97,34 +104,39 @@ __device__ void sqp_solve(Ctx& C, const ProbDesc& P, const Params& prm, int iter
       flags |= F_MAXITER;
       break;
     }
-    st_schur<NT>(C);
+    st_schur(C);
     __syncthreads();
-    st_block_inverse<NT>(C);
-    __syncthreads();
-    if (sflags(C)) {
+    tstamp(C, T_SCHUR, tl);
+    st_block_inverse(C);
+    if (cluster_flag(C, rbuf)) {
       flags |= F_NONFINITE;
       break;
     }
+    tstamp(C, T_BINV, tl);
     bool hit = false;
-    pcg_total += st_pcg<NT>(C, prm.pcg_eps, prm.pcg_max, prm.precond, &hit);
+    pcg_total += st_pcg<REG>(C, prm.pcg_eps, prm.pcg_max, prm.precond, &hit, rbuf);
     if (hit) flags |= F_PCGMAX;
-    st_recover<NT>(C);
-    __syncthreads();
-    if (sflags(C)) {
+    if (C.tm && C.rank == 0 && threadIdx.x == 0) tl = clock64();
+    st_recover(C);
+    if (cluster_flag(C, rbuf)) {
       flags |= F_NONFINITE;
       break;
     }
-    st_line_search<NT>(C, prm.mu, prm.beta, prm.n_alpha);
-    const int choice = st_accept<NT>(C, prm.beta, prm.n_alpha);
+    tstamp(C, T_RECOVER, tl);
+    st_line_search(C, prm.mu, prm.beta, prm.n_alpha, rbuf);
+    tstamp(C, T_LS, tl);
+    const int choice = st_accept(C, prm.beta, prm.n_alpha);
+    csync(C);
+    tstamp(C, T_ACCEPT, tl);
     if (choice >= 0)
       merit = C.scal[S_MERITS + choice];
     else
       flags |= F_LSFAIL;
     ++sqp;
   }
-  __syncthreads();
-  store_iterate<NT>(C, P);
-  if (threadIdx.x == 0) {
+  csync(C);
+  store_iterate(C, P);
+  if (C.rank == 0 && threadIdx.x == 0) {
     out->flags = flags;
     out->sqp_iters = sqp;
     out->pcg_iters = pcg_total;
@@ -133,41 +145,63 @@ __device__ void sqp_solve(Ctx& C, const ProbDesc& P, const Params& prm, int iter
   }
 }
 
-template <int NT, bool SB>
-__global__ void __launch_bounds__(NT, 1) sqp_fused(FusedLaunch a) {
+// REG = true: 1 CTA per SM, all PCG block rows in registers (latency);
+// REG = false: 2 CTAs per SM, off-diagonal rows read from shared memory (throughput).
+template <bool REG>
+__global__ void __launch_bounds__(NTHR, REG ? 1 : 2) sqp_fused(FusedLaunch a) {
   extern __shared__ float4 smem4[];
   float* sm = reinterpret_cast<float*>(smem4);
-  const int b = a.order ? a.order[blockIdx.x] : blockIdx.x;
+  const int csize = a.csize;
+  const int rank = csize > 1 ? (int)cg::this_cluster().block_rank() : 0;
+  const int b = a.order ? a.order[blockIdx.x / csize] : blockIdx.x / csize;
   const ProbDesc P = a.probs[b];
   static_assert(sizeof(DevModel) <= 96 * sizeof(float), "model slot");
-  for (int i = threadIdx.x; i < (int)(sizeof(DevModel) / sizeof(float)); i += NT)
+  for (int i = threadIdx.x; i < (int)(sizeof(DevModel) / sizeof(float)); i += NTHR)
     sm[i] = reinterpret_cast<const float*>(a.models + P.model)[i];
   float* scal = sm + 96;
   float* red = scal + 64;
-  float* xs = red + 128;
-  float* vec = xs + 16;
-  const size_t K = (size_t)a.nmax + 1, VV = K * VS;
+  float* xs = red + 2 * RED_SLOTS * RED_W;
+  float* vb = xs + 16;
+  const int kpc = kpc_for(a.nmax, csize);
+  const int vstride = (kpc + 2) * VS;
+  float* blocks = vb + NVEC * vstride;
+  float* zblock = blocks + (3 * kpc + 1) * BS;  // 196 zeros (L_{N+1})
   float* ws = a.ws + (size_t)b * a.ws_stride;
   Ctx C;
   bind_problem(C, P, reinterpret_cast<const DevModel*>(sm));
   bind_workspace(C, ws, a.layout);
-  bind_vectors(C, vec, VV);
-  if (SB) {
-    float* blocks = vec + NVEC_SMEM * VV;
-    C.Dm = blocks;
-    C.Lm = blocks + K * BS;
-    C.Pm = blocks + 2 * K * BS;
-  } else {
-    C.Dm = ws + a.layout.Dm;
-    C.Lm = ws + a.layout.Lm;
-    C.Pm = ws + a.layout.Pm;
-  }
+  bind_partition(C, rank, csize);
   C.xs = xs;
   C.red = red;
   C.scal = scal;
+  C.tm = a.timing ? a.timing + (size_t)b * T_COUNT : nullptr;
+  C.Dm = blocks;
+  C.Lm = blocks + kpc * BS;
+  C.Pm = blocks + (2 * kpc + 1) * BS;
+  C.bk0 = C.k0;
+  C.Lz = zblock;
+  C.vb = vb;
+  C.vstride = vstride;
+  C.vk0 = C.k0 - 1;
+  C.vbl = nullptr;
+  C.vbr = nullptr;
+  C.vk0l = C.vk0r = 0;
+  if (csize > 1) {
+    cg::cluster_group cl = cg::this_cluster();
+    const int skpc = kpc_for(C.N, csize);
+    if (rank > 0 && C.k0 > 0 && C.k0 < C.k1) {
+      C.vbl = cl.map_shared_rank(vb, rank - 1);
+      C.vk0l = min((rank - 1) * skpc, C.N + 1) - 1;
+    }
+    if (rank < csize - 1 && C.k1 <= C.N && C.k0 < C.k1) {
+      C.vbr = cl.map_shared_rank(vb, rank + 1);
+      C.vk0r = C.k1 - 1;
+    }
+  }
   if (threadIdx.x < 64) scal[threadIdx.x] = 0.f;
+  for (int i = threadIdx.x; i < 196; i += NTHR) zblock[i] = 0.f;
   __syncthreads();
-  sqp_solve<NT>(C, P, a.prm, a.iters, a.results + b);
+  sqp_solve<REG>(C, P, a.prm, a.iters, a.results + b);
 }
 
 // ----------------------------------------------------------------- plain form
@@ -178,39 +212,48 @@ struct PlainArgs {
   Result* results;
   float* ws;
   WsLayout layout;
-  int b, nmax, iters, it;
+  int b, nmax, iters, it, csize;
   Params prm;
 };
 
-enum : int { S_DONE = 12, S_NSQP = 13, S_NPCG = 14, S_RFLAGS = 15 };
-
-template <int NT>
-__global__ void __launch_bounds__(NT, 1) sqp_plain_stage(int stage, PlainArgs a) {
-  __shared__ float red[128];
+__global__ void __launch_bounds__(NTHR, 1) sqp_plain_stage(int stage, PlainArgs a) {
+  __shared__ float red[2 * RED_SLOTS * RED_W];
+  __shared__ float zeros196[196];
+  for (int i = threadIdx.x; i < 196; i += NTHR) zeros196[i] = 0.f;
+  __syncthreads();
+  const int csize = a.csize;
+  const int rank = csize > 1 ? (int)cg::this_cluster().block_rank() : 0;
   const ProbDesc P = a.probs[a.b];
-  const size_t K = (size_t)a.nmax + 1, VV = K * VS;
+  const size_t K = (size_t)a.nmax + 1;
   Ctx C;
   bind_problem(C, P, a.models + P.model);
   bind_workspace(C, a.ws, a.layout);
-  float* vec = a.ws + a.layout.vec;
-  bind_vectors(C, vec, VV);
+  bind_partition(C, rank, csize);
   C.Dm = a.ws + a.layout.Dm;
   C.Lm = a.ws + a.layout.Lm;
   C.Pm = a.ws + a.layout.Pm;
-  C.scal = vec + 12 * VV;
+  C.bk0 = 0;
+  C.Lz = zeros196;
+  C.vb = a.ws + a.layout.vec;
+  C.vstride = (int)((K + 2) * VS);
+  C.vk0 = -1;
+  C.vbl = C.vbr = nullptr;
+  C.vk0l = C.vk0r = 0;
+  C.scal = C.vb + NVEC * C.vstride;
   C.xs = C.scal + 64;
   C.red = red;
+  C.tm = nullptr;
   const Params& prm = a.prm;
   int* rflags = reinterpret_cast<int*>(C.scal + S_RFLAGS);
+  int rbuf = 0;
   if (stage == PS_LOAD) {
-    if (threadIdx.x < 64) C.scal[threadIdx.x] = 0.f;
-    __syncthreads();
-    load_iterate<NT>(C, P);
+    if (rank == 0 && threadIdx.x < 64) C.scal[threadIdx.x] = 0.f;
+    load_iterate(C, P);
     return;
   }
   if (stage == PS_STORE) {
-    store_iterate<NT>(C, P);
-    if (threadIdx.x == 0) {
+    store_iterate(C, P);
+    if (rank == 0 && threadIdx.x == 0) {
       Result* out = a.results + a.b;
       out->flags = *rflags;
       out->sqp_iters = (int)C.scal[S_NSQP];
@@ -221,19 +264,21 @@ __global__ void __launch_bounds__(NT, 1) sqp_plain_stage(int stage, PlainArgs a)
     return;
   }
   if (C.scal[S_DONE] != 0.f) return;
+  const bool lead = rank == 0 && threadIdx.x == 0;
   switch (stage) {
-    case PS_MASS: st_mass_bias<NT>(C); break;
-    case PS_FD: st_forward_dynamics<NT>(C); break;
-    case PS_VALUE: st_value_and_cost<NT>(C); break;
-    case PS_TANGENT: st_tangents<NT>(C); break;
-    case PS_JAC: st_dyn_jacobians<NT>(C); break;
+    case PS_MASS: st_mass_bias(C); break;
+    case PS_FD: st_forward_dynamics(C); break;
+    case PS_VALUE: st_value_and_cost(C); break;
+    case PS_TANGENT: st_tangents(C); break;
+    case PS_JAC: st_dyn_jacobians(C); break;
     case PS_KKT: {
-      st_kkt_merit<NT>(C, prm.mu);
-      if (threadIdx.x == 0) {
+      st_kkt_merit(C, prm.mu, rbuf);
+      const bool bad = *reinterpret_cast<volatile int*>(C.scal + S_FLAGS) != 0;
+      if (lead) {
         C.scal[S_MERITF] = C.scal[S_MERIT0];
         int f = *rflags;
         bool done = false;
-        if (sflags(C)) {
+        if (bad) {
           f |= F_NONFINITE;
           done = true;
         } else if (prm.kkt_tol > 0.f && C.scal[S_KKT] <= prm.kkt_tol) {
@@ -248,36 +293,36 @@ __global__ void __launch_bounds__(NT, 1) sqp_plain_stage(int stage, PlainArgs a)
       }
       break;
     }
-    case PS_SCHUR: st_schur<NT>(C); break;
+    case PS_SCHUR: st_schur(C); break;
     case PS_BINV:
-      st_block_inverse<NT>(C);
-      __syncthreads();
-      if (threadIdx.x == 0 && sflags(C)) {
+      st_block_inverse(C);
+      csync(C);
+      if (lead && *reinterpret_cast<volatile int*>(C.scal + S_FLAGS)) {
         *rflags |= F_NONFINITE;
         C.scal[S_DONE] = 1.f;
       }
       break;
     case PS_PCG: {
       bool hit = false;
-      const int n = st_pcg<NT>(C, prm.pcg_eps, prm.pcg_max, prm.precond, &hit);
-      if (threadIdx.x == 0) {
+      const int n = st_pcg<true>(C, prm.pcg_eps, prm.pcg_max, prm.precond, &hit, rbuf);
+      if (lead) {
         C.scal[S_NPCG] += (float)n;
         if (hit) *rflags |= F_PCGMAX;
       }
       break;
     }
     case PS_RECOVER:
-      st_recover<NT>(C);
-      __syncthreads();
-      if (threadIdx.x == 0 && sflags(C)) {
+      st_recover(C);
+      csync(C);
+      if (lead && *reinterpret_cast<volatile int*>(C.scal + S_FLAGS)) {
         *rflags |= F_NONFINITE;
         C.scal[S_DONE] = 1.f;
       }
       break;
-    case PS_LS: st_line_search<NT>(C, prm.mu, prm.beta, prm.n_alpha); break;
+    case PS_LS: st_line_search(C, prm.mu, prm.beta, prm.n_alpha, rbuf); break;
     case PS_ACCEPT: {
-      const int choice = st_accept<NT>(C, prm.beta, prm.n_alpha);
-      if (threadIdx.x == 0) {
+      const int choice = st_accept(C, prm.beta, prm.n_alpha);
+      if (lead) {
         if (choice >= 0)
           C.scal[S_MERITF] = C.scal[S_MERITS + choice];
         else
@@ -289,22 +334,5 @@ __global__ void __launch_bounds__(NT, 1) sqp_plain_stage(int stage, PlainArgs a)
     default: break;
   }
 }
-
-// Launches one instantiation of the fused kernel.
-template <int NT, bool SB>
-cudaError_t launch_fused_t(const FusedLaunch& a, size_t smem, cudaStream_t s) {
-  static size_t configured = 0;
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(sqp_fused<NT, SB>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
-  sqp_fused<NT, SB><<<a.n, NT, smem, s>>>(a);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_fused_288(const FusedLaunch& a, size_t smem, bool sb, cudaStream_t s);
-cudaError_t launch_fused_544(const FusedLaunch& a, size_t smem, bool sb, cudaStream_t s);
 
 }  // namespace gato

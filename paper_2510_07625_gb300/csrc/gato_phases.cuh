@@ -1,21 +1,41 @@
 // The stages of one SQP iteration (GATO, arXiv 2510.07625, Alg. 1) as
-// block-level device functions.  One thread block works on one solve.
+// device functions run by a thread-block cluster that owns one solve.
 //
-// Thread mapping for knot-row work: each warp covers 4 knots with 7 lanes per
-// knot (lanes 28..31 idle); lane j of a knot owns state rows j (q_j) and j+7
-// (qd_j) of every block row of that knot.  The 7 lanes of a knot share a warp,
-// so dependencies inside one knot need only __syncwarp; dependencies between
-// knots and the dot-product reductions use __syncthreads.
+// Partition: the cluster's C CTAs split the block rows (knots) 0..N of the
+// solve into contiguous ranges [k0, k1) of at most KPC_MAX knots; a CTA does
+// every per-knot computation of its own range.  Inside a CTA each warp covers
+// 4 knots with 7 lanes per knot (lanes 28..31 idle); lane j owns rows j (q_j)
+// and j+7 (qd_j) of every block row of its knot, so dependencies inside a knot
+// need only __syncwarp.  Dependencies between knots and the reductions use
+// cluster barriers (block barriers when C = 1).
 //
-// Storage: a solve's hot arrays (Schur blocks, preconditioner blocks, PCG
-// vectors) are addressed through the Ctx pointers, which the fused kernel
-// points at shared memory and the plain form at global memory.  Blocks are
-// 14x14 column-major with stride BS; vectors use stride VS per knot.
+// PCG working set: each thread keeps its two rows of D_k, L_k, L_{k+1}^T and
+// D_k^-1 (112 floats) in registers for the whole solve; vectors live in a
+// per-CTA window of knots [k0-1, k1] whose halo knots are written by the
+// neighbour CTAs through distributed shared memory (the plain form keeps every
+// vector in global memory and skips the pushes).
+//
+// Reductions are compensated (double-float) and deterministic: each warp's
+// partial goes to a slot of every CTA of the cluster, and every warp then
+// reduces all slots with the same fixed tree.
 #pragma once
+
+#include <cooperative_groups.h>
 
 #include "gato_device.cuh"
 
 namespace gato {
+
+namespace cg = cooperative_groups;
+
+constexpr int NWARP = 9;             // warps per CTA
+constexpr int NTHR = 32 * NWARP;     // threads per CTA
+constexpr int KPC_MAX = 4 * NWARP - 1;  // knots per CTA (one slot spare for L_{k1})
+constexpr int NVEC = 9;              // vector slots
+constexpr int RED_SLOTS = 8 * NWARP; // per-warp partial slots (up to 8 CTAs)
+constexpr int RED_W = 8;             // floats per slot
+
+enum : int { V_RR = 0, V_P0, V_P1, V_Q, V_Y, V_W, V_Z, V_RHS, V_DNU };
 
 struct Ctx {
   int N, dof, cost_kind;
@@ -24,22 +44,51 @@ struct Ctx {
   const float* x_ref;   // user layout, (N+1) x 2*dof
   const float* ee_ref;  // (N+1) x 3
   const DevModel* M;
-  float* xs;            // padded x_s [VS]
+  // cluster partition
+  int rank, csize, k0, k1;
   // global workspace
   float *X, *U, *dX, *dU, *Fq, *Fv, *Mi, *qdd, *dT, *Qi, *Ri, *qg, *rg, *cv, *Jk, *Li;
   float *Dx, *Du;       // dual residual d = g + C^T nu at the current linearisation
+  float* nu;            // multiplier (global, all knots)
   LinkRec* LV;
-  // hot arrays (shared or global)
-  float *Dm, *Lm, *Pm, *nu, *rr, *pb0, *pb1, *qv, *yv, *wv, *zv, *rhs, *dnu;
-  // reductions (always shared): red[2][32][2], scal[64]
+  float* xs;            // padded x_s [VS]
+  // Schur / preconditioner blocks: knot k at index k - bk0
+  float *Dm, *Lm, *Pm;
+  int bk0;
+  const float* Lz;  // a 14x14 block of zeros (stands for L_{N+1})
+  // vectors: slot s of knot k at vb + s * vstride + (k - vk0) * VS
+  float* vb;
+  int vstride, vk0;
+  float* vbl;  // left neighbour's window (distributed shared memory) or null
+  int vk0l;
+  float* vbr;  // right neighbour's window or null
+  int vk0r;
+  // reductions: red[2][RED_SLOTS][RED_W] in this CTA's shared memory
   float* red;
   float* scal;
+  // optional per-stage cycle counters (rank 0, thread 0), see TimingSlot
+  long long* tm;
 };
+
+// Slots of the per-stage cycle counters.
+enum TimingSlot : int {
+  T_LOAD = 0, T_MASS, T_FD, T_VALUE, T_TANGENT, T_JAC, T_KKT, T_SCHUR, T_BINV, T_PCG_INIT, T_PCG_S,
+  T_PCG_Y, T_PCG_WZ, T_RECOVER, T_LS, T_ACCEPT, T_COUNT
+};
+
+// Adds the cycles since *last to counter `slot` (rank 0, thread 0 only).
+__device__ __forceinline__ void tstamp(const Ctx& C, int slot, long long& last) {
+  if (C.tm && C.rank == 0 && threadIdx.x == 0) {
+    const long long t = clock64();
+    C.tm[slot] += t - last;
+    last = t;
+  }
+}
 
 // scal[] slots
 enum : int {
   S_KKT = 0, S_MERIT0, S_CMAX, S_GMAX, S_DMAX, S_ALPHA, S_FLAGS, S_PCG, S_ITERS, S_MERITF,
-  S_CHOICE, S_REDBUF, S_MERITS = 16  // S_MERITS..S_MERITS+15: trial merits
+  S_CHOICE, S_REDBUF, S_DONE, S_NSQP, S_NPCG, S_RFLAGS, S_MERITS = 16  // S_MERITS..+15
 };
 
 // Per-knot strides of the global workspace arrays.
@@ -47,13 +96,13 @@ constexpr int FQS = 49, QIS = 56, DTS = 14 * 8, LIS = 196;
 
 struct WsLayout {
   size_t X, U, dX, dU, Fq, Fv, Mi, qdd, dT, Qi, Ri, qg, rg, cv, Jk, Li, LV, Dm, Lm, Pm, vec, Dx, Du,
-      total;
+      nu, total;
 };
 
 __host__ __device__ inline size_t align32(size_t n) { return (n + 31) & ~size_t(31); }
 
 // Offsets (floats) of one solve's workspace for horizon up to Nmax.  Blocks and
-// vectors are included only when `global_hot` (plain form or long horizons).
+// vectors are included only for the plain form (everything global).
 __host__ __device__ inline WsLayout ws_layout(int Nmax, bool global_blocks, bool global_vecs) {
   WsLayout L;
   size_t o = 0;
@@ -77,6 +126,7 @@ __host__ __device__ inline WsLayout ws_layout(int Nmax, bool global_blocks, bool
   L.LV = o; o += align32(Nmax * QM * LVS);
   L.Dx = o; o += align32(K * VS);
   L.Du = o; o += align32(Nmax * US);
+  L.nu = o; o += align32(K * VS);
   if (global_blocks) {
     L.Dm = o; o += align32(K * BS);
     L.Lm = o; o += align32(K * BS);
@@ -85,7 +135,7 @@ __host__ __device__ inline WsLayout ws_layout(int Nmax, bool global_blocks, bool
     L.Dm = L.Lm = L.Pm = 0;
   }
   if (global_vecs) {
-    L.vec = o; o += align32(12 * K * VS + 128);
+    L.vec = o; o += align32(NVEC * (K + 2) * VS + 64 + 16);
   } else {
     L.vec = 0;
   }
@@ -93,23 +143,52 @@ __host__ __device__ inline WsLayout ws_layout(int Nmax, bool global_blocks, bool
   return L;
 }
 
-// Vector slots of the fused kernel's shared-memory layout.
-constexpr int NVEC_SMEM = 10;
-
-// Shared-memory floats of the fused kernel for horizon Nmax.
-__host__ __device__ inline size_t smem_floats(int Nmax, bool smem_blocks) {
-  const size_t K = Nmax + 1;
-  size_t f = 96 /*model*/ + 64 /*scal*/ + 128 /*red*/ + 16 /*xs*/;
-  f += NVEC_SMEM * K * VS;  // nu rr p0 p1 q y w z rhs + 1 spare
-  if (smem_blocks) f += 3 * K * BS;
+// Shared-memory floats of one fused CTA owning at most `kpc` knots.
+__host__ __device__ inline size_t smem_floats(int kpc) {
+  size_t f = 96 /*model*/ + 64 /*scal*/ + 2 * RED_SLOTS * RED_W + 16 /*xs*/;
+  f += NVEC * (size_t)(kpc + 2) * VS;
+  f += (size_t)(3 * kpc + 1) * BS + 196;  // blocks + a zero block
   return align32(f);
 }
+
+// Cluster size for horizon N: the fewest CTAs with at most KPC_MAX knots each.
+__host__ __device__ inline int cluster_for(int N) { return (N + 1 + KPC_MAX - 1) / KPC_MAX; }
+__host__ __device__ inline int kpc_for(int N, int C) { return (N + 1 + C - 1) / C; }
 
 // ------------------------------------------------------------ small helpers
 
 __device__ __forceinline__ int pad_state(int ui, int dof) { return ui < dof ? ui : QM + (ui - dof); }
 
 __device__ __forceinline__ float& blk(float* base, int k, int r, int c) { return base[k * BS + c * XM + r]; }
+__device__ __forceinline__ float& bD(const Ctx& C, int k, int r, int c) { return blk(C.Dm, k - C.bk0, r, c); }
+__device__ __forceinline__ float& bL(const Ctx& C, int k, int r, int c) { return blk(C.Lm, k - C.bk0, r, c); }
+__device__ __forceinline__ float& bP(const Ctx& C, int k, int r, int c) { return blk(C.Pm, k - C.bk0, r, c); }
+
+__device__ __forceinline__ float* vec(const Ctx& C, int s, int k) {
+  return C.vb + s * C.vstride + (k - C.vk0) * VS;
+}
+
+// After the owner of knot k wrote rows j, j+7 of slot s, copy them into the
+// halo of the neighbour CTA that reads knot k.
+__device__ __forceinline__ void push_rows(const Ctx& C, int s, int k, int j, float v0, float v1) {
+  if (C.vbl && k == C.k0) {
+    float* d = C.vbl + s * C.vstride + (k - C.vk0l) * VS;
+    d[j] = v0;
+    d[j + QM] = v1;
+  }
+  if (C.vbr && k == C.k1 - 1) {
+    float* d = C.vbr + s * C.vstride + (k - C.vk0r) * VS;
+    d[j] = v0;
+    d[j + QM] = v1;
+  }
+}
+
+__device__ __forceinline__ void csync(const Ctx& C) {
+  if (C.csize > 1)
+    cg::this_cluster().sync();
+  else
+    __syncthreads();
+}
 
 __device__ __forceinline__ float xref_at(const Ctx& C, int k, int i) {
   const int nx = 2 * C.dof;
@@ -161,92 +240,136 @@ __device__ __forceinline__ float Qinv_elem(const float* Qi, int r, int c) {
   return 0.f;
 }
 
-template <int NT>
-__device__ __forceinline__ DF block_df_sum(const Ctx& C, DF v) {
-  constexpr int NW = NT / 32;
+__device__ __forceinline__ void flag_nonfinite(const Ctx& C) {
+  atomicOr(reinterpret_cast<int*>(C.scal + S_FLAGS), F_NONFINITE);
+}
+
+// ------------------------------------------------------------- reductions
+
+// Each warp contributes `nv` floats; lane 0 writes them into slot
+// [buf][rank * NWARP + warp] of every CTA in the cluster.
+__device__ __forceinline__ void red_publish(const Ctx& C, int buf, const float* v, int nv) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int buf = (int)C.scal[S_REDBUF];
-  v = warp_df_sum(v);
-  __syncthreads();  // everyone has read S_REDBUF
   if (lane == 0) {
-    C.red[(buf * 32 + warp) * 2] = v.hi;
-    C.red[(buf * 32 + warp) * 2 + 1] = v.lo;
+    const int slot = (buf * RED_SLOTS + C.rank * NWARP + warp) * RED_W;
+    if (C.csize > 1) {
+      cg::cluster_group cl = cg::this_cluster();
+      for (int r = 0; r < C.csize; ++r) {
+        float* dst = cl.map_shared_rank(C.red, r);
+        for (int i = 0; i < nv; ++i) dst[slot + i] = v[i];
+      }
+    } else {
+      for (int i = 0; i < nv; ++i) C.red[slot + i] = v[i];
+    }
   }
-  if (threadIdx.x == 0) C.scal[S_REDBUF] = (float)(buf ^ 1);
-  __syncthreads();
-  // every warp reduces the per-warp partials with the same shuffle tree, so all
-  // threads hold the same (deterministic) total without another barrier
-  DF s = lane < NW ? DF{C.red[(buf * 32 + lane) * 2], C.red[(buf * 32 + lane) * 2 + 1]} : df_zero();
+}
+
+// Cluster-wide compensated sum; every thread returns the same value.
+__device__ __forceinline__ DF cluster_df_sum(const Ctx& C, DF v, int& buf) {
+  const int lane = threadIdx.x & 31;
+  v = warp_df_sum(v);
+  const float pv[2] = {v.hi, v.lo};
+  red_publish(C, buf, pv, 2);
+  csync(C);
+  const int ns = C.csize * NWARP;
+  DF s = df_zero();
+  for (int i = lane; i < ns; i += 32) {
+    const float* p = C.red + (buf * RED_SLOTS + i) * RED_W;
+    s = df_addd(s, DF{p[0], p[1]});
+  }
+  buf ^= 1;
   return warp_df_sum(s);
 }
 
-template <int NT>
-__device__ __forceinline__ float block_max(const Ctx& C, float v, int slot) {
-  constexpr int NW = NT / 32;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  v = warp_max(v);
-  __syncthreads();
-  if (lane == 0) C.red[(slot * 32 + warp) * 2] = v;
-  __syncthreads();
-  float m = 0.f;
-  for (int w = 0; w < NW; ++w) m = fmaxf(m, C.red[(slot * 32 + w) * 2]);
-  return m;
+// Cluster-wide maxima of 4 values and compensated sums of 2 values.
+__device__ __forceinline__ void cluster_max4_sum2(const Ctx& C, float* mx, DF* sm, int& buf) {
+  const int lane = threadIdx.x & 31;
+  float v[RED_W];
+  for (int i = 0; i < 4; ++i) v[i] = warp_max(mx[i]);
+  for (int i = 0; i < 2; ++i) {
+    const DF t = warp_df_sum(sm[i]);
+    v[4 + 2 * i] = t.hi;
+    v[5 + 2 * i] = t.lo;
+  }
+  red_publish(C, buf, v, RED_W);
+  csync(C);
+  const int ns = C.csize * NWARP;
+  float m[4] = {0.f, 0.f, 0.f, 0.f};
+  DF s[2] = {df_zero(), df_zero()};
+  for (int i = lane; i < ns; i += 32) {
+    const float* p = C.red + (buf * RED_SLOTS + i) * RED_W;
+    for (int q = 0; q < 4; ++q) m[q] = fmaxf(m[q], p[q]);
+    for (int q = 0; q < 2; ++q) s[q] = df_addd(s[q], DF{p[4 + 2 * q], p[5 + 2 * q]});
+  }
+  for (int q = 0; q < 4; ++q) mx[q] = warp_max(m[q]);
+  for (int q = 0; q < 2; ++q) sm[q] = warp_df_sum(s[q]);
+  buf ^= 1;
 }
 
-#define KNOT_LOOP(NT_, NLAST)                                                     \
-  const int lane_ = threadIdx.x & 31, warp_ = threadIdx.x >> 5;                   \
-  const int slot_ = lane_ / 7, j = lane_ - 7 * (lane_ / 7);                       \
-  for (int kb_ = 4 * warp_; kb_ <= (NLAST); kb_ += 4 * ((NT_) / 32))              \
-    for (int k = kb_ + slot_, once_ = 1; once_; once_ = 0)                        \
-      for (const bool act = (lane_ < 28) && (k <= (NLAST)); once_; once_ = 0)
+// Cluster-wide OR of the non-finite flag (every CTA takes the same branch).
+__device__ __forceinline__ bool cluster_flag(const Ctx& C, int& buf) {
+  float mx[4] = {0.f, 0.f, 0.f, 0.f};
+  DF sm[2] = {df_zero(), df_zero()};
+  if (*reinterpret_cast<volatile int*>(C.scal + S_FLAGS)) mx[0] = 1.f;
+  cluster_max4_sum2(C, mx, sm, buf);
+  return mx[0] > 0.f;
+}
+
+// The knot a thread owns in knot-row work: k = k0 + 4 warp + lane / 7.
+#define OWN_KNOT(Cx)                                                           \
+  const int lane_ = threadIdx.x & 31, warp_ = threadIdx.x >> 5;                \
+  const int j = lane_ - 7 * (lane_ / 7);                                       \
+  const int k = (Cx).k0 + 4 * warp_ + lane_ / 7;                               \
+  const bool act = (lane_ < 28) && (k < (Cx).k1)
 
 // ------------------------------------------------------------------ loading
 
-// Copies the solve's iterate from user layout into the padded workspace.
-template <int NT>
-__device__ void load_iterate(const Ctx& C, const ProbDesc& P) {
+// Copies the CTA's knots of the iterate from user layout into the padded
+// workspace and the multiplier into the global nu.
+__device__ inline void load_iterate(const Ctx& C, const ProbDesc& P) {
   const int N = C.N, dof = C.dof, nx = 2 * dof;
-  for (int i = threadIdx.x; i < (N + 1) * VS; i += NT) C.X[i] = 0.f;
-  for (int i = threadIdx.x; i < N * US; i += NT) C.U[i] = 0.f;
-  for (int i = threadIdx.x; i < (N + 1) * VS; i += NT) C.nu[i] = 0.f;
+  const int ke = C.k1 < N ? C.k1 : N;  // dynamics knots [k0, ke)
+  for (int i = threadIdx.x; i < (C.k1 - C.k0) * VS; i += NTHR) {
+    C.X[C.k0 * VS + i] = 0.f;
+    C.nu[C.k0 * VS + i] = 0.f;
+  }
+  for (int i = threadIdx.x; i < (ke - C.k0) * US; i += NTHR) C.U[C.k0 * US + i] = 0.f;
   if (threadIdx.x < VS) C.xs[threadIdx.x] = 0.f;
   __syncthreads();
-  for (int i = threadIdx.x; i < (N + 1) * nx; i += NT) {
-    const int k = i / nx, ui = i - k * nx;
-    C.X[k * VS + pad_state(ui, dof)] = P.X[i];
-    if (P.lam) C.nu[k * VS + pad_state(ui, dof)] = P.lam[i];
+  for (int i = threadIdx.x; i < (C.k1 - C.k0) * nx; i += NTHR) {
+    const int k = C.k0 + i / nx, ui = i % nx;
+    C.X[k * VS + pad_state(ui, dof)] = P.X[k * nx + ui];
+    if (P.lam) C.nu[k * VS + pad_state(ui, dof)] = P.lam[k * nx + ui];
   }
-  for (int i = threadIdx.x; i < N * dof; i += NT) {
-    const int k = i / dof, ui = i - k * dof;
-    C.U[k * US + ui] = P.U[i];
+  for (int i = threadIdx.x; i < (ke - C.k0) * dof; i += NTHR) {
+    const int k = C.k0 + i / dof, ui = i % dof;
+    C.U[k * US + ui] = P.U[k * dof + ui];
   }
   if (threadIdx.x < nx) C.xs[pad_state(threadIdx.x, dof)] = P.x_s[threadIdx.x];
-  __syncthreads();
 }
 
-template <int NT>
-__device__ void store_iterate(const Ctx& C, const ProbDesc& P) {
+__device__ inline void store_iterate(const Ctx& C, const ProbDesc& P) {
   const int N = C.N, dof = C.dof, nx = 2 * dof;
-  for (int i = threadIdx.x; i < (N + 1) * nx; i += NT) {
-    const int k = i / nx, ui = i - k * nx;
-    P.X[i] = C.X[k * VS + pad_state(ui, dof)];
-    if (P.lam) P.lam[i] = C.nu[k * VS + pad_state(ui, dof)];
+  const int ke = C.k1 < N ? C.k1 : N;
+  for (int i = threadIdx.x; i < (C.k1 - C.k0) * nx; i += NTHR) {
+    const int k = C.k0 + i / nx, ui = i % nx;
+    P.X[k * nx + ui] = C.X[k * VS + pad_state(ui, dof)];
+    if (P.lam) P.lam[k * nx + ui] = C.nu[k * VS + pad_state(ui, dof)];
   }
-  for (int i = threadIdx.x; i < N * dof; i += NT) {
-    const int k = i / dof, ui = i - k * dof;
-    P.U[i] = C.U[k * US + ui];
+  for (int i = threadIdx.x; i < (ke - C.k0) * dof; i += NTHR) {
+    const int k = C.k0 + i / dof, ui = i % dof;
+    P.U[k * dof + ui] = C.U[k * US + ui];
   }
 }
 
 // --------------------------------------------------- stage 1: linearisation
 
 // Mass-matrix columns (unit-acceleration RNEA) and bias forces per knot.
-template <int NT>
-__device__ void st_mass_bias(const Ctx& C) {
-  const int N = C.N;
+__device__ inline void st_mass_bias(const Ctx& C) {
+  const int ke = C.k1 < C.N ? C.k1 : C.N;
   const DevModel& M = *C.M;
-  for (int it = threadIdx.x; it < N * 8; it += NT) {
-    const int k = it >> 3, col = it & 7;
+  for (int it = threadIdx.x; it < (ke - C.k0) * 8; it += NTHR) {
+    const int k = C.k0 + (it >> 3), col = it & 7;
     float sq[QM], cq[QM], qd[QM], acc[QM], tau[QM];
     const float* x = C.X + k * VS;
 #pragma unroll
@@ -267,16 +390,18 @@ __device__ void st_mass_bias(const Ctx& C) {
 }
 
 // Cholesky of M, explicit M^-1, qdd = M^-1 (u - bias), dynamics defects.
-template <int NT>
-__device__ void st_forward_dynamics(const Ctx& C) {
+__device__ inline void st_forward_dynamics(const Ctx& C) {
   const int N = C.N;
+  const int ke = C.k1 < N ? C.k1 : N;
   const float h = C.h;
-  for (int k = threadIdx.x; k <= N; k += NT) {
-    if (k == N) {
+  const int items = (ke - C.k0) + (C.k0 == 0 ? 1 : 0);
+  for (int it = threadIdx.x; it < items; it += NTHR) {
+    if (it == ke - C.k0) {  // c_0 = x_s - x_0, by the CTA owning knot 0
 #pragma unroll
       for (int i = 0; i < XM; ++i) C.cv[i] = C.xs[i] - C.X[i];
       continue;
     }
+    const int k = C.k0 + it;
     float Ml[28];
 #pragma unroll
     for (int i = 0; i < QM; ++i)
@@ -286,8 +411,7 @@ __device__ void st_forward_dynamics(const Ctx& C) {
 #pragma unroll
     for (int i = 0; i < QM; ++i)
       if (i >= C.dof) Ml[i * (i + 1) / 2 + i] = 1.f;
-    const bool ok = chol7(Ml);
-    if (!ok) atomicOr(reinterpret_cast<int*>(C.scal + S_FLAGS), F_NONFINITE);
+    if (!chol7(Ml)) flag_nonfinite(C);
     float b[QM];
 #pragma unroll
     for (int i = 0; i < QM; ++i) b[i] = C.U[k * US + i] - C.qdd[k * US + i];
@@ -384,30 +508,30 @@ __device__ __forceinline__ void knot_cost(const Ctx& C, int k) {
   C.Jk[k] = J;
 }
 
+
 // Value RNEA at the dynamics solution (stored for the tangent pass) + costs.
-template <int NT>
-__device__ void st_value_and_cost(const Ctx& C) {
-  const int N = C.N;
-  for (int it = threadIdx.x; it < 2 * N + 1; it += NT) {
-    if (it < N) {
-      const int k = it;
+__device__ inline void st_value_and_cost(const Ctx& C) {
+  const int ke = C.k1 < C.N ? C.k1 : C.N;
+  const int nd = ke - C.k0, nc = C.k1 - C.k0;
+  for (int it = threadIdx.x; it < nd + nc; it += NTHR) {
+    if (it < nd) {
+      const int k = C.k0 + it;
       float sq[QM], cq[QM], tau[QM];
       const float* x = C.X + k * VS;
 #pragma unroll
       for (int i = 0; i < QM; ++i) sincosf(x[i], &sq[i], &cq[i]);
       rnea_value(*C.M, sq, cq, x + QM, C.qdd + k * US, C.M->g, tau, C.LV + k * QM);
     } else {
-      knot_cost(C, it - N);
+      knot_cost(C, C.k0 + it - nd);
     }
   }
 }
 
 // Directional derivatives of ID along every q_j and qd_j.
-template <int NT>
-__device__ void st_tangents(const Ctx& C) {
-  const int N = C.N;
-  for (int it = threadIdx.x; it < N * 14; it += NT) {
-    const int k = it / 14, d = it - 14 * k;
+__device__ inline void st_tangents(const Ctx& C) {
+  const int ke = C.k1 < C.N ? C.k1 : C.N;
+  for (int it = threadIdx.x; it < (ke - C.k0) * 14; it += NTHR) {
+    const int k = C.k0 + it / 14, d = it % 14;
     float dtau[QM];
     rnea_tangent(*C.M, C.LV + k * QM, C.X + k * VS + QM, d >= QM, d % QM, dtau);
 #pragma unroll
@@ -416,11 +540,10 @@ __device__ void st_tangents(const Ctx& C) {
 }
 
 // dqdd/dq = -M^-1 dID/dq, dqdd/dqd = -M^-1 dID/dqd.
-template <int NT>
-__device__ void st_dyn_jacobians(const Ctx& C) {
-  const int N = C.N;
-  for (int it = threadIdx.x; it < N * 98; it += NT) {
-    const int k = it / 98, e = it - 98 * k;
+__device__ inline void st_dyn_jacobians(const Ctx& C) {
+  const int ke = C.k1 < C.N ? C.k1 : C.N;
+  for (int it = threadIdx.x; it < (ke - C.k0) * 98; it += NTHR) {
+    const int k = C.k0 + it / 98, e = it % 98;
     const int which = e / 49, r = (e % 49) / QM, c = e % QM;
     const float* Mi = C.Mi + k * FQS + r * QM;
     const float* col = C.dT + k * DTS + (which * QM + c) * 8;
@@ -435,14 +558,13 @@ __device__ void st_dyn_jacobians(const Ctx& C) {
 // Also stores the dual residual d = g + C^T nu, accumulated with compensated
 // sums: near convergence d is a small difference of O(|nu|) terms, and the
 // step is recovered from it through G^-1 (R^-1 = 1/w_u amplifies its error).
-template <int NT>
-__device__ void st_kkt_merit(const Ctx& C, float mu) {
+__device__ inline void st_kkt_merit(const Ctx& C, float mu, int& rbuf) {
   const int N = C.N;
   const float h = C.h, h2 = C.h * C.h;
-  float cmax = 0.f, gmax = 0.f, dmax = 0.f;
-  bool bad = false;
-  DF jsum = df_zero(), csum = df_zero();
-  KNOT_LOOP(NT, N) {
+  float mx[4] = {0.f, 0.f, 0.f, 0.f};  // |c|, |g|, |d|, non-finite
+  DF sm[2] = {df_zero(), df_zero()};   // J, ||c||_1
+  {
+    OWN_KNOT(C);
     if (act) {
       const float* nu = C.nu + k * VS;
       DF d0 = df_add(df_add(df_zero(), C.qg[k * VS + j]), nu[j]);
@@ -471,42 +593,39 @@ __device__ void st_kkt_merit(const Ctx& C, float mu) {
       const float dv[2] = {df_val(d0), df_val(d1)};
       C.Dx[k * VS + j] = dv[0];
       C.Dx[k * VS + j + QM] = dv[1];
+      bool bad = false;
       for (int t = 0; t < 2; ++t) {
         const int i = j + QM * t;
         const float cvi = C.cv[k * VS + i];
-        cmax = fmaxf(cmax, fabsf(cvi));
-        csum = df_add(csum, fabsf(cvi));
+        mx[0] = fmaxf(mx[0], fabsf(cvi));
+        sm[1] = df_add(sm[1], fabsf(cvi));
         const float g = C.qg[k * VS + i];
-        gmax = fmaxf(gmax, fabsf(g));
-        dmax = fmaxf(dmax, fabsf(dv[t]));
+        mx[1] = fmaxf(mx[1], fabsf(g));
+        mx[2] = fmaxf(mx[2], fabsf(dv[t]));
         bad = bad || !isfinite(cvi) || !isfinite(dv[t]);
       }
       if (k < N) {
         const float g = C.rg[k * US + j];
         const float duv = df_val(du);
         C.Du[k * US + j] = duv;
-        gmax = fmaxf(gmax, fabsf(g));
-        dmax = fmaxf(dmax, fabsf(duv));
+        mx[1] = fmaxf(mx[1], fabsf(g));
+        mx[2] = fmaxf(mx[2], fabsf(duv));
         bad = bad || !isfinite(duv);
       }
       if (j == 0) {
-        jsum = df_add(jsum, C.Jk[k]);
+        sm[0] = df_add(sm[0], C.Jk[k]);
         bad = bad || !isfinite(C.Jk[k]);
       }
+      if (bad) mx[3] = 1.f;
     }
   }
-  // fmaxf drops NaN, so non-finite values are flagged separately
-  const float badf = block_max<NT>(C, bad ? 1.f : 0.f, 0);
-  cmax = block_max<NT>(C, cmax, 1);
-  gmax = block_max<NT>(C, gmax, 0);
-  dmax = block_max<NT>(C, dmax, 1);
-  const float J = df_val(block_df_sum<NT>(C, jsum));
-  const float c1 = df_val(block_df_sum<NT>(C, csum));
+  if (*reinterpret_cast<volatile int*>(C.scal + S_FLAGS)) mx[3] = 1.f;
+  cluster_max4_sum2(C, mx, sm, rbuf);
+  const float J = df_val(sm[0]), c1 = df_val(sm[1]);
   if (threadIdx.x == 0) {
-    C.scal[S_KKT] = fmaxf(cmax, dmax / fmaxf(1.f, gmax));
+    C.scal[S_KKT] = fmaxf(mx[0], mx[2] / fmaxf(1.f, mx[1]));
     C.scal[S_MERIT0] = J + mu * c1;
-    if (badf > 0.f || !isfinite(J))
-      atomicOr(reinterpret_cast<int*>(C.scal + S_FLAGS), F_NONFINITE);
+    if (mx[3] > 0.f || !isfinite(J)) flag_nonfinite(C);
   }
   __syncthreads();
 }
@@ -518,415 +637,483 @@ __device__ void st_kkt_merit(const Ctx& C, float mu) {
 // Right-hand side for the multiplier correction dnu = nu - nu_0: zeta_k and
 // gamma of Eq. 5 with the gradient g replaced by the dual residual
 // d = g + C^T nu_0, i.e. rhs = -c - C G^-1 d = gamma - S nu_0, the initial
-// residual of the warm-started PCG, formed without cancellation.
-template <int NT>
-__device__ void st_schur(const Ctx& C) {
+// residual of the warm-started PCG, formed without cancellation.  A CTA also
+// forms L_{k1} (the block its last row multiplies by L^T) from its own knot.
+__device__ inline void st_schur(const Ctx& C) {
   const int N = C.N;
   const float h = C.h;
-  KNOT_LOOP(NT, N) {
-    const int kk = k - 1;  // the dynamics knot feeding block row k
-    if (act && k == 0) {
-      const float* Qi = C.Qi;
-      for (int t = 0; t < 2; ++t) {
-        const int i = j + QM * t;
-        float acc = 0.f;
-        for (int c = 0; c < XM; ++c) {
-          const float qv = Qinv_elem(Qi, i, c);
-          blk(C.Dm, 0, i, c) = qv;
-          acc += qv * C.Dx[c];
-          blk(C.Lm, 0, i, c) = 0.f;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = lane - 7 * (lane / 7);
+  const int k = C.k0 + 4 * warp + lane / 7;
+  const bool act = (lane < 28) && (k < C.k1);
+  const bool actL = (lane < 28) && (k <= C.k1) && (k <= N) && (k > 0);
+  const int kk = k - 1;  // the dynamics knot feeding block row k
+  if (act && k == 0) {
+    const float* Qi = C.Qi;
+    for (int t = 0; t < 2; ++t) {
+      const int i = j + QM * t;
+      float acc = 0.f;
+      for (int c = 0; c < XM; ++c) {
+        const float qv = Qinv_elem(Qi, i, c);
+        bD(C, 0, i, c) = qv;
+        acc += qv * C.Dx[c];
+        bL(C, 0, i, c) = 0.f;
+      }
+      vec(C, V_RHS, 0)[i] = -C.cv[i] - acc;
+    }
+  }
+  if (actL) {
+    const float* Fq = C.Fq + kk * FQS;
+    const float* Fv = C.Fv + kk * FQS;
+    const float* Qi = C.Qi + kk * QIS;
+    for (int t = 0; t < 2; ++t) {
+      const int i = j + QM * t;
+      float Arow[XM];
+#pragma unroll
+      for (int l = 0; l < XM; ++l) Arow[l] = A_elem(Fq, Fv, h, i, l);
+#pragma unroll
+      for (int c = 0; c < XM; ++c) {
+        float a;
+        if (c < QM) {
+          a = 0.f;
+#pragma unroll
+          for (int l = 0; l < QM; ++l) a += Arow[l] * Qi[l * QM + c];
+        } else {
+          a = Arow[c] * Qi[49 + c - QM];
         }
-        C.rhs[i] = -C.cv[i] - acc;
+        bL(C, k, i, c) = -a;
       }
     }
-    if (act && k > 0) {
-      const float* Fq = C.Fq + kk * FQS;
-      const float* Fv = C.Fv + kk * FQS;
-      const float* Qi = C.Qi + kk * QIS;
-      for (int t = 0; t < 2; ++t) {
-        const int i = j + QM * t;
-        float Arow[XM];
+  }
+  __syncwarp();
+  if (act && k > 0) {
+    const float* Fq = C.Fq + kk * FQS;
+    const float* Fv = C.Fv + kk * FQS;
+    const float* Mi = C.Mi + kk * FQS;
+    const float* Ri = C.Ri + kk * US;
+    const float* Qi1 = C.Qi + k * QIS;
+    for (int t = 0; t < 2; ++t) {
+      const int i = j + QM * t;
+      float Arow[XM];
 #pragma unroll
-        for (int l = 0; l < XM; ++l) Arow[l] = A_elem(Fq, Fv, h, i, l);
+      for (int l = 0; l < XM; ++l) Arow[l] = A_elem(Fq, Fv, h, i, l);
+      const float si = t == 0 ? h * h : h;
+      float BRrow[QM];
 #pragma unroll
-        for (int c = 0; c < XM; ++c) {
-          float a;
-          if (c < QM) {
-            a = 0.f;
+      for (int m = 0; m < QM; ++m) BRrow[m] = si * Mi[j * QM + m] * Ri[m];
+      for (int c = 0; c < XM; ++c) {
+        // theta = -A L^T + B R^-1 B^T + Q_{k}^-1   (A Q^-1 A^T = -A L^T)
+        float a = 0.f;
 #pragma unroll
-            for (int l = 0; l < QM; ++l) a += Arow[l] * Qi[l * QM + c];
-          } else {
-            a = Arow[c] * Qi[49 + c - QM];
-          }
-          blk(C.Lm, k, i, c) = -a;
-        }
+        for (int l = 0; l < XM; ++l) a -= Arow[l] * bL(C, k, c, l);
+        const int cm = c < QM ? c : c - QM;
+        const float sc = c < QM ? h * h : h;
+        float bb = 0.f;
+#pragma unroll
+        for (int m = 0; m < QM; ++m) bb += BRrow[m] * Mi[cm * QM + m];
+        bD(C, k, i, c) = a + sc * bb + Qinv_elem(Qi1, i, c);
       }
-    }
-    __syncwarp();
-    if (act && k > 0) {
-      const float* Fq = C.Fq + kk * FQS;
-      const float* Fv = C.Fv + kk * FQS;
-      const float* Mi = C.Mi + kk * FQS;
-      const float* Ri = C.Ri + kk * US;
-      const float* Qi1 = C.Qi + k * QIS;
-      for (int t = 0; t < 2; ++t) {
-        const int i = j + QM * t;
-        float Arow[XM];
+      // zeta with d: L_k d_{k-1} - B R^-1 d_u,{k-1} + Q_k^-1 d_k
+      float z = 0.f;
 #pragma unroll
-        for (int l = 0; l < XM; ++l) Arow[l] = A_elem(Fq, Fv, h, i, l);
-        const float si = t == 0 ? h * h : h;
-        float BRrow[QM];
+      for (int l = 0; l < XM; ++l) z += bL(C, k, i, l) * C.Dx[kk * VS + l];
 #pragma unroll
-        for (int m = 0; m < QM; ++m) BRrow[m] = si * Mi[j * QM + m] * Ri[m];
-        for (int c = 0; c < XM; ++c) {
-          // theta = -A L^T + B R^-1 B^T + Q_{k}^-1   (A Q^-1 A^T = -A L^T)
-          float a = 0.f;
+      for (int m = 0; m < QM; ++m) z -= BRrow[m] * C.Du[kk * US + m];
 #pragma unroll
-          for (int l = 0; l < XM; ++l) a -= Arow[l] * blk(C.Lm, k, c, l);
-          const int cm = c < QM ? c : c - QM;
-          const float sc = c < QM ? h * h : h;
-          float bb = 0.f;
-#pragma unroll
-          for (int m = 0; m < QM; ++m) bb += BRrow[m] * Mi[cm * QM + m];
-          blk(C.Dm, k, i, c) = a + sc * bb + Qinv_elem(Qi1, i, c);
-        }
-        // zeta with d: L_k d_{k-1} - B R^-1 d_u,{k-1} + Q_k^-1 d_k
-        float z = 0.f;
-#pragma unroll
-        for (int l = 0; l < XM; ++l) z += blk(C.Lm, k, i, l) * C.Dx[kk * VS + l];
-#pragma unroll
-        for (int m = 0; m < QM; ++m) z -= BRrow[m] * C.Du[kk * US + m];
-#pragma unroll
-        for (int l = 0; l < XM; ++l) z += Qinv_elem(Qi1, i, l) * C.Dx[k * VS + l];
-        C.rhs[k * VS + i] = -C.cv[k * VS + i] - z;
-      }
+      for (int l = 0; l < XM; ++l) z += Qinv_elem(Qi1, i, l) * C.Dx[k * VS + l];
+      vec(C, V_RHS, k)[i] = -C.cv[k * VS + i] - z;
     }
   }
 }
 
 // D_k^-1 by Cholesky: the 7 lanes of a knot factor D_k in place in Pm, invert
 // the factor column by column into Li, and form L^-T L^-1.
-template <int NT>
-__device__ void st_block_inverse(const Ctx& C) {
-  const int N = C.N;
+__device__ inline void st_block_inverse(const Ctx& C) {
   bool bad = false;
-  KNOT_LOOP(NT, N) {
-    float* P = C.Pm;
-    float* Li = C.Li + (act ? k : 0) * LIS;
-    if (act)
-      for (int t = 0; t < 2; ++t) {
-        const int i = j + QM * t;
-        for (int c = 0; c < XM; ++c) blk(P, k, i, c) = blk(C.Dm, k, i, c);
-      }
-    __syncwarp();
-    for (int c = 0; c < XM; ++c) {
-      if (act && (c % QM) == j) {
-        const float d2 = blk(P, k, c, c);
-        bad = bad || !(d2 > 0.f);
-        blk(P, k, c, c) = sqrtf(fmaxf(d2, 1e-30f));
-      }
-      __syncwarp();
-      if (act) {
-        const float d = blk(P, k, c, c);
-        for (int t = 0; t < 2; ++t) {
-          const int i = j + QM * t;
-          if (i > c) blk(P, k, i, c) = blk(P, k, i, c) / d;
-        }
-      }
-      __syncwarp();
-      if (act) {
-        for (int t = 0; t < 2; ++t) {
-          const int i = j + QM * t;
-          if (i > c) {
-            const float lic = blk(P, k, i, c);
-            for (int l = c + 1; l <= i; ++l) blk(P, k, i, l) -= lic * blk(P, k, l, c);
-          }
-        }
-      }
-      __syncwarp();
+  OWN_KNOT(C);
+  float* Li = C.Li + (act ? k : 0) * LIS;
+  if (act)
+    for (int t = 0; t < 2; ++t) {
+      const int i = j + QM * t;
+      for (int c = 0; c < XM; ++c) bP(C, k, i, c) = bD(C, k, i, c);
     }
-    // columns j and j+7 of L^-1 (lower triangular, column-major in Li)
-    if (act)
-      for (int t = 0; t < 2; ++t) {
-        const int cc = j + QM * t;
-        for (int i = 0; i < cc; ++i) Li[cc * XM + i] = 0.f;
-        Li[cc * XM + cc] = 1.f / blk(P, k, cc, cc);
-        for (int i = cc + 1; i < XM; ++i) {
-          float s = 0.f;
-          for (int l = cc; l < i; ++l) s += blk(P, k, i, l) * Li[cc * XM + l];
-          Li[cc * XM + i] = -s / blk(P, k, i, i);
-        }
-      }
+  __syncwarp();
+  for (int c = 0; c < XM; ++c) {
+    if (act && (c % QM) == j) {
+      const float d2 = bP(C, k, c, c);
+      bad = bad || !(d2 > 0.f);
+      bP(C, k, c, c) = sqrtf(fmaxf(d2, 1e-30f));
+    }
     __syncwarp();
-    if (act)
+    if (act) {
+      const float d = bP(C, k, c, c);
       for (int t = 0; t < 2; ++t) {
         const int i = j + QM * t;
-        for (int c = 0; c < XM; ++c) {
-          float s = 0.f;
-          for (int l = (i > c ? i : c); l < XM; ++l) s += Li[i * XM + l] * Li[c * XM + l];
-          blk(P, k, i, c) = s;
+        if (i > c) bP(C, k, i, c) = bP(C, k, i, c) / d;
+      }
+    }
+    __syncwarp();
+    if (act) {
+      for (int t = 0; t < 2; ++t) {
+        const int i = j + QM * t;
+        if (i > c) {
+          const float lic = bP(C, k, i, c);
+          for (int l = c + 1; l <= i; ++l) bP(C, k, i, l) -= lic * bP(C, k, l, c);
         }
       }
+    }
     __syncwarp();
   }
-  if (bad) atomicOr(reinterpret_cast<int*>(C.scal + S_FLAGS), F_NONFINITE);
+  // columns j and j+7 of L^-1 (lower triangular, column-major in Li)
+  if (act)
+    for (int t = 0; t < 2; ++t) {
+      const int cc = j + QM * t;
+      for (int i = 0; i < cc; ++i) Li[cc * XM + i] = 0.f;
+      Li[cc * XM + cc] = 1.f / bP(C, k, cc, cc);
+      for (int i = cc + 1; i < XM; ++i) {
+        float s = 0.f;
+        for (int l = cc; l < i; ++l) s += bP(C, k, i, l) * Li[cc * XM + l];
+        Li[cc * XM + i] = -s / bP(C, k, i, i);
+      }
+    }
+  __syncwarp();
+  if (act)
+    for (int t = 0; t < 2; ++t) {
+      const int i = j + QM * t;
+      for (int c = 0; c < XM; ++c) {
+        float s = 0.f;
+        for (int l = (i > c ? i : c); l < XM; ++l) s += Li[i * XM + l] * Li[c * XM + l];
+        bP(C, k, i, c) = s;
+      }
+    }
+  __syncwarp();
+  if (bad) flag_nonfinite(C);
 }
 
 // ------------------------------------------------------------ stage 3: PCG
 
-// Rows j, j+7 of (S v)_k, where v_k' is produced by `vf(k', c)`.
-template <class VF>
-__device__ __forceinline__ void s_rows(const Ctx& C, int N, int k, int j, VF vf, float& o0, float& o1) {
-  float a0 = 0.f, a1 = 0.f;
-  const int i0 = j, i1 = j + QM;
-#pragma unroll 2
-  for (int c = 0; c < XM; ++c) {
-    const float v0 = vf(k, c);
-    a0 += blk(C.Dm, k, i0, c) * v0;
-    a1 += blk(C.Dm, k, i1, c) * v0;
-    if (k > 0) {
-      const float vm = vf(k - 1, c);
-      a0 += blk(C.Lm, k, i0, c) * vm;
-      a1 += blk(C.Lm, k, i1, c) * vm;
-    }
-    if (k < N) {
-      const float vp = vf(k + 1, c);
-      a0 += blk(C.Lm, k + 1, c, i0) * vp;
-      a1 += blk(C.Lm, k + 1, c, i1) * vp;
-    }
-  }
-  o0 = a0;
-  o1 = a1;
-}
+// Two rows of the off-diagonal blocks of S and of D^-1.  With REG = true all
+// of them live in registers (the latency variant, 1 CTA per SM); with
+// REG = false only the D^-1 rows do and L_k / L_{k+1}^T are read from their
+// blocks (the throughput variant, 2 CTAs per SM).  The diagonal blocks D_k,
+// used once per iteration, are always read from their block.  Values and
+// arithmetic order are the same in both, so the results are bitwise equal.
+template <bool REG>
+struct RowRegs;
 
-// Rows j, j+7 of (O v)_k: the off-diagonal part of S only.
-__device__ __forceinline__ void o_rows(const Ctx& C, int N, int k, int j, const float* v, float& o0,
-                                       float& o1) {
-  float a0 = 0.f, a1 = 0.f;
-  const int i0 = j, i1 = j + QM;
-#pragma unroll 2
-  for (int c = 0; c < XM; ++c) {
-    if (k > 0) {
-      const float vm = v[(k - 1) * VS + c];
-      a0 += blk(C.Lm, k, i0, c) * vm;
-      a1 += blk(C.Lm, k, i1, c) * vm;
-    }
-    if (k < N) {
-      const float vp = v[(k + 1) * VS + c];
-      a0 += blk(C.Lm, k + 1, c, i0) * vp;
-      a1 += blk(C.Lm, k + 1, c, i1) * vp;
+template <>
+struct RowRegs<true> {
+  float L0[XM], L1[XM];  // rows j, j+7 of L_k (zero for k = 0)
+  float U0[XM], U1[XM];  // columns j, j+7 of L_{k+1} (zero for k = N)
+  float P0[XM], P1[XM];  // rows j, j+7 of D_k^-1
+  __device__ __forceinline__ float l0(int c) const { return L0[c]; }
+  __device__ __forceinline__ float l1(int c) const { return L1[c]; }
+  __device__ __forceinline__ float u0(int c) const { return U0[c]; }
+  __device__ __forceinline__ float u1(int c) const { return U1[c]; }
+  __device__ __forceinline__ void load(const Ctx& C, int k, int j, bool act) {
+    const int i0 = j, i1 = j + QM;
+#pragma unroll
+    for (int c = 0; c < XM; ++c) {
+      L0[c] = (act && k > 0) ? bL(C, k, i0, c) : 0.f;
+      L1[c] = (act && k > 0) ? bL(C, k, i1, c) : 0.f;
+      U0[c] = (act && k < C.N) ? bL(C, k + 1, c, i0) : 0.f;
+      U1[c] = (act && k < C.N) ? bL(C, k + 1, c, i1) : 0.f;
+      P0[c] = act ? bP(C, k, i0, c) : 0.f;
+      P1[c] = act ? bP(C, k, i1, c) : 0.f;
     }
   }
-  o0 = a0;
-  o1 = a1;
-}
+};
 
-__device__ __forceinline__ void p_rows(const Ctx& C, int k, int j, const float* v, float& o0, float& o1) {
-  float a0 = 0.f, a1 = 0.f;
-#pragma unroll 2
-  for (int c = 0; c < XM; ++c) {
-    const float vc = v[k * VS + c];
-    a0 += blk(C.Pm, k, j, c) * vc;
-    a1 += blk(C.Pm, k, j + QM, c) * vc;
+template <>
+struct RowRegs<false> {
+  const float* Lr;  // &L_k(j, 0): element (j, c) at Lr[c * XM], row j+7 at +7
+  const float* Ur;  // &L_{k+1}(0, j): element (c, j) at Ur[c], column j+7 at +7 * XM
+  float P0[XM], P1[XM];
+  __device__ __forceinline__ float l0(int c) const { return Lr[c * XM]; }
+  __device__ __forceinline__ float l1(int c) const { return Lr[c * XM + QM]; }
+  __device__ __forceinline__ float u0(int c) const { return Ur[c]; }
+  __device__ __forceinline__ float u1(int c) const { return Ur[QM * XM + c]; }
+  __device__ __forceinline__ void load(const Ctx& C, int k, int j, bool act) {
+    // k = 0 has L_0 = 0 stored; k = N reads the zero block L_{N+1} slot below
+    const int kk = act ? k : C.k0;
+    Lr = &bL(C, kk, j, 0);
+    Ur = (act && k < C.N) ? &bL(C, k + 1, 0, j) : C.Lz + j * XM;
+#pragma unroll
+    for (int c = 0; c < XM; ++c) {
+      P0[c] = act ? bP(C, k, j, c) : 0.f;
+      P1[c] = act ? bP(C, k, j + QM, c) : 0.f;
+    }
   }
-  o0 = a0;
-  o1 = a1;
+};
+
+// Cluster-wide compensated sums of two values (one reduction for both).
+__device__ __forceinline__ void cluster_df_sum2(float* red, int rank, int csize, DF& a, DF& b, int& buf) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    DF ya, yb;
+    ya.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
+    ya.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
+    yb.hi = __shfl_xor_sync(0xffffffffu, b.hi, o);
+    yb.lo = __shfl_xor_sync(0xffffffffu, b.lo, o);
+    a = df_addd(a, ya);
+    b = df_addd(b, yb);
+  }
+  if (lane == 0) {
+    const int slot = (buf * RED_SLOTS + rank * NWARP + warp) * RED_W;
+    const float4 v = make_float4(a.hi, a.lo, b.hi, b.lo);
+    if (csize > 1) {
+      cg::cluster_group cl = cg::this_cluster();
+      for (int r = 0; r < csize; ++r) *reinterpret_cast<float4*>(cl.map_shared_rank(red, r) + slot) = v;
+    } else {
+      *reinterpret_cast<float4*>(red + slot) = v;
+    }
+  }
+  if (csize > 1)
+    cg::this_cluster().sync();
+  else
+    __syncthreads();
+  a = df_zero();
+  b = df_zero();
+  for (int i = lane; i < csize * NWARP; i += 32) {
+    const float4 v = *reinterpret_cast<const float4*>(red + (buf * RED_SLOTS + i) * RED_W);
+    a = df_addd(a, DF{v.x, v.y});
+    b = df_addd(b, DF{v.z, v.w});
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    DF ya, yb;
+    ya.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
+    ya.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
+    yb.hi = __shfl_xor_sync(0xffffffffu, b.hi, o);
+    yb.lo = __shfl_xor_sync(0xffffffffu, b.lo, o);
+    a = df_addd(a, ya);
+    b = df_addd(b, yb);
+  }
+  buf ^= 1;
 }
 
 // Preconditioned CG (Sec. II-B, III-B) for the multiplier correction
 // S dnu = rhs, started from dnu = 0; nu_0 + dnu equals the warm-started PCG
 // iterate on S nu = gamma.  Stair preconditioner (Eq. 6) applied as
-// D^-1 - D^-1 O D^-1 (reading c4).  Stops when sqrt(eta / eta_0) <= eps
-// (reading c8).  Returns iterations.
-template <int NT>
-__device__ int st_pcg(const Ctx& C, float eps, int maxit, int precond, bool* hit_max) {
-  const int N = C.N;
+// D^-1 - D^-1 O D^-1 (reading c4).  Stops when sqrt(eta / eta_0) <= eps with
+// eta = r'u (reading c8).  Returns iterations.
+//
+// Evaluation order: the Chronopoulos-Gear arrangement of PCG, whose iterates
+// equal standard PCG's in exact arithmetic.  S is applied to u = Phi r
+// (w = S u) and s = S p is carried by s = w + beta s, so r'u and w'u come from
+// one compensated reduction per iteration; then
+// delta = w'u - beta r'u / alpha_prev, alpha = r'u / delta.  Three barriers
+// per iteration: the y halo (stair only), the u halo, the reduction.  Every
+// address and scalar the loop needs is set up before it.
+template <bool REG>
+__device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bool* hit_max, int& rbuf) {
   const bool stair = (precond == 0);
   *hit_max = false;
-  // dnu = 0, r = rhs ; y = D^-1 r
-  {
-    KNOT_LOOP(NT, N) {
-      if (act) {
-        C.dnu[k * VS + j] = 0.f;
-        C.dnu[k * VS + j + QM] = 0.f;
-        C.rr[k * VS + j] = C.rhs[k * VS + j];
-        C.rr[k * VS + j + QM] = C.rhs[k * VS + j + QM];
-      }
-      __syncwarp();
-      if (act) {
-        float y0, y1;
-        p_rows(C, k, j, C.rr, y0, y1);
-        C.yv[k * VS + j] = y0;
-        C.yv[k * VS + j + QM] = y1;
-        if (!stair) {
-          C.zv[k * VS + j] = y0;
-          C.zv[k * VS + j + QM] = y1;
-        }
-      }
-    }
+  long long tlast = C.tm ? clock64() : 0;
+  OWN_KNOT(C);
+  RowRegs<REG> R;
+  R.load(C, k, j, act);
+  // zero every vector slot of the window (halos at the ends stay zero)
+  for (int i = threadIdx.x; i < NVEC * C.vstride; i += NTHR) {
+    const int s = i / C.vstride;
+    if (s != V_RHS) C.vb[i] = 0.f;
   }
-  __syncthreads();
-  DF part = df_zero();
-  {
-    KNOT_LOOP(NT, N) {
-      if (act && stair) {
-        float w0, w1;
-        o_rows(C, N, k, j, C.yv, w0, w1);
-        C.wv[k * VS + j] = w0;
-        C.wv[k * VS + j + QM] = w1;
-      }
-      __syncwarp();
-      if (act) {
-        if (stair) {
-          float t0, t1;
-          p_rows(C, k, j, C.wv, t0, t1);
-          C.zv[k * VS + j] = C.yv[k * VS + j] - t0;
-          C.zv[k * VS + j + QM] = C.yv[k * VS + j + QM] - t1;
-        }
-        part = df_fma(part, C.rr[k * VS + j], C.zv[k * VS + j]);
-        part = df_fma(part, C.rr[k * VS + j + QM], C.zv[k * VS + j + QM]);
-      }
-    }
+  float* const red = C.red;
+  const int rank = C.rank, csize = C.csize;
+  const int ka = act ? k : C.k0;  // a valid knot for the address set-up of idle lanes
+  const int vstr = C.vstride;
+  float* const wb = vec(C, 0, ka);  // slot s of this knot at wb + s * vstr
+#define SLOT(s) (wb + (s) * vstr)
+  // neighbour window of this knot's rows (slot s at pb + s * vstr), boundary knots only
+  float* pb = nullptr;
+  if (act && C.vbl && k == C.k0) pb = C.vbl + (k - C.vk0l) * VS;
+  if (act && C.vbr && k == C.k1 - 1) pb = C.vbr + (k - C.vk0r) * VS;
+#define PUSH(s, a, b)                     \
+  if (pb) {                               \
+    pb[(s) * vstr + J] = (a);             \
+    pb[(s) * vstr + J7] = (b);            \
   }
-  float eta = df_val(block_df_sum<NT>(C, part));
-  const float eta0 = eta;
-  if (!(eta0 > 1e-30f)) return 0;
+  const float* const Drow0 = &bD(C, ka, j, 0);  // D_k row j: element c at Drow0[c * XM]
+  float* const rr = SLOT(V_RR);
+  float* const yv = SLOT(V_Y);
+  float* const uv = SLOT(V_Z);
+  float* const tv = SLOT(V_W);
+  float* const dn = SLOT(V_DNU);
+  const int J = j, J7 = j + QM;
+  // p, s and the own rows of u, w stay in registers
+  float p0 = 0.f, p1 = 0.f, s0 = 0.f, s1 = 0.f, u0 = 0.f, u1 = 0.f, w0 = 0.f, w1 = 0.f;
+  if (csize > 1) cg::this_cluster().sync(); else __syncthreads();
+  if (act) {
+    rr[J] = SLOT(V_RHS)[J];
+    rr[J7] = SLOT(V_RHS)[J7];
+  }
   int it = 0;
-  float beta = 0.f;
-  bool first = true;
-  float* pold = C.pb0;
-  float* pnew = C.pb1;
+  float gamma = 0.f, gamma0 = 0.f, alpha = 0.f;
   while (true) {
-    // q = S p_new with p_new = z + beta p_old computed on the fly
-    DF pq = df_zero();
-    {
-      const float* zv = C.zv;
-      KNOT_LOOP(NT, N) {
-        if (act) {
-          auto pf = [&](int kk, int c) {
-            return first ? zv[kk * VS + c] : zv[kk * VS + c] + beta * pold[kk * VS + c];
-          };
-          float s0, s1;
-          s_rows(C, N, k, j, pf, s0, s1);
-          const float p0 = pf(k, j), p1 = pf(k, j + QM);
-          pnew[k * VS + j] = p0;
-          pnew[k * VS + j + QM] = p1;
-          C.qv[k * VS + j] = s0;
-          C.qv[k * VS + j + QM] = s1;
-          pq = df_fma(pq, p0, s0);
-          pq = df_fma(pq, p1, s1);
-        }
+    // u = Phi r: y = D^-1 r; u = y - D^-1 (O y)
+    __syncwarp();
+    if (act) {
+      float y0 = 0.f, y1 = 0.f;
+#pragma unroll
+      for (int c = 0; c < XM; ++c) {
+        y0 += R.P0[c] * rr[c];
+        y1 += R.P1[c] * rr[c];
       }
-    }
-    const float pqv = df_val(block_df_sum<NT>(C, pq));
-    const float alpha = eta / pqv;
-    DF rz = df_zero();
-    {
-      KNOT_LOOP(NT, N) {
-        if (act) {
-          for (int t = 0; t < 2; ++t) {
-            const int i = k * VS + j + QM * t;
-            C.dnu[i] += alpha * pnew[i];
-            C.rr[i] -= alpha * C.qv[i];
-          }
-        }
-        __syncwarp();
-        if (act) {
-          float y0, y1;
-          p_rows(C, k, j, C.rr, y0, y1);
-          C.yv[k * VS + j] = y0;
-          C.yv[k * VS + j + QM] = y1;
-          if (!stair) {
-            C.zv[k * VS + j] = y0;
-            C.zv[k * VS + j + QM] = y1;
-            rz = df_fma(rz, C.rr[k * VS + j], y0);
-            rz = df_fma(rz, C.rr[k * VS + j + QM], y1);
-          }
-        }
+      u0 = y0;
+      u1 = y1;
+      if (stair) {
+        yv[J] = y0;
+        yv[J7] = y1;
+        PUSH(V_Y, y0, y1);
+      } else {
+        uv[J] = y0;
+        uv[J7] = y1;
+        PUSH(V_Z, y0, y1);
       }
     }
     if (stair) {
-      __syncthreads();
-      KNOT_LOOP(NT, N) {
-        if (act) {
-          float w0, w1;
-          o_rows(C, N, k, j, C.yv, w0, w1);
-          C.wv[k * VS + j] = w0;
-          C.wv[k * VS + j + QM] = w1;
+      if (csize > 1) cg::this_cluster().sync(); else __syncthreads();
+      tstamp(C, T_PCG_Y, tlast);
+      if (act) {
+        float t0 = 0.f, t1 = 0.f;
+#pragma unroll
+        for (int c = 0; c < XM; ++c) {
+          t0 += R.l0(c) * yv[c - VS];
+          t1 += R.l1(c) * yv[c - VS];
+          t0 += R.u0(c) * yv[c + VS];
+          t1 += R.u1(c) * yv[c + VS];
         }
-        __syncwarp();
-        if (act) {
-          float t0, t1;
-          p_rows(C, k, j, C.wv, t0, t1);
-          const float z0 = C.yv[k * VS + j] - t0, z1 = C.yv[k * VS + j + QM] - t1;
-          C.zv[k * VS + j] = z0;
-          C.zv[k * VS + j + QM] = z1;
-          rz = df_fma(rz, C.rr[k * VS + j], z0);
-          rz = df_fma(rz, C.rr[k * VS + j + QM], z1);
+        tv[J] = t0;
+        tv[J7] = t1;
+      }
+      __syncwarp();
+      if (act) {
+        float q0 = 0.f, q1 = 0.f;
+#pragma unroll
+        for (int c = 0; c < XM; ++c) {
+          q0 += R.P0[c] * tv[c];
+          q1 += R.P1[c] * tv[c];
         }
+        u0 -= q0;
+        u1 -= q1;
+        uv[J] = u0;
+        uv[J7] = u1;
+        PUSH(V_Z, u0, u1);
       }
     }
-    const float eta_new = df_val(block_df_sum<NT>(C, rz));
-    ++it;
-    if (!(eta_new > 0.f) || sqrtf(eta_new / eta0) <= eps) break;
-    if (it >= maxit) {
-      *hit_max = true;
-      break;
+    if (csize > 1) cg::this_cluster().sync(); else __syncthreads();
+    // w = S u
+    DF ru = df_zero(), wu = df_zero();
+    if (act) {
+      float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+      for (int c = 0; c < XM; ++c) {
+        const float v0 = uv[c];
+        a0 += Drow0[c * XM] * v0;
+        a1 += Drow0[c * XM + QM] * v0;
+        const float vm = uv[c - VS];
+        a0 += R.l0(c) * vm;
+        a1 += R.l1(c) * vm;
+        const float vp = uv[c + VS];
+        a0 += R.u0(c) * vp;
+        a1 += R.u1(c) * vp;
+      }
+      w0 = a0;
+      w1 = a1;
+      ru = df_fma(ru, rr[J], u0);
+      ru = df_fma(ru, rr[J7], u1);
+      wu = df_fma(wu, w0, u0);
+      wu = df_fma(wu, w1, u1);
     }
-    beta = eta_new / eta;
-    eta = eta_new;
-    first = false;
-    float* t = pold;
-    pold = pnew;
-    pnew = t;
+    tstamp(C, T_PCG_S, tlast);
+    cluster_df_sum2(red, rank, csize, ru, wu, rbuf);
+    tstamp(C, T_PCG_WZ, tlast);
+    const float gnew = df_val(ru), eps_wu = df_val(wu);
+    float beta;
+    if (it == 0) {
+      gamma0 = gnew;
+      if (!(gamma0 > 1e-30f)) break;
+      beta = 0.f;
+      alpha = gnew / eps_wu;
+    } else {
+      if (!(gnew > 0.f) || sqrtf(gnew / gamma0) <= eps) break;
+      if (it >= maxit) {
+        *hit_max = true;
+        break;
+      }
+      beta = gnew / gamma;
+      alpha = gnew / (eps_wu - beta * gnew / alpha);
+    }
+    gamma = gnew;
+    // p = u + beta p; s = w + beta s; dnu += alpha p; r -= alpha s
+    if (act) {
+      p0 = u0 + beta * p0;
+      p1 = u1 + beta * p1;
+      s0 = w0 + beta * s0;
+      s1 = w1 + beta * s1;
+      dn[J] += alpha * p0;
+      dn[J7] += alpha * p1;
+      rr[J] -= alpha * s0;
+      rr[J7] -= alpha * s1;
+    }
+    ++it;
   }
-  __syncthreads();
+  // the correction's boundary rows go to the neighbours for the recovery
+  if (act) {
+    PUSH(V_DNU, dn[J], dn[J7]);
+  }
+  if (csize > 1) cg::this_cluster().sync(); else __syncthreads();
   return it;
+#undef PUSH
+#undef SLOT
 }
 
 // ------------------------------------------------- stage 4: step recovery
 
 // dx_k = -Q_k^-1 (q_k + nu_k - A_k^T nu_{k+1}), du_k = -R_k^-1 (r_k - B_k^T nu_{k+1})
 // (Eq. 4, reading c1), evaluated as -G^-1 (d + C^T dnu); then nu += dnu.
-template <int NT>
-__device__ void st_recover(const Ctx& C) {
+__device__ inline void st_recover(const Ctx& C) {
   const int N = C.N;
   const float h = C.h;
   bool bad = false;
-  KNOT_LOOP(NT, N) {
-    float bt = 0.f;
-    if (act) {
-      float at0 = 0.f, at1 = 0.f;
-      if (k < N) {
-        float cf[QM];
-        at_factor(C.dnu + (k + 1) * VS, h, cf);
-        at_rows(C.Fq + k * FQS, C.Fv + k * FQS, C.dnu + (k + 1) * VS, cf, h, j, at0, at1);
-        bt = bt_row(C.Mi + k * FQS, cf, j);
-      }
-      C.wv[k * VS + j] = C.Dx[k * VS + j] + C.dnu[k * VS + j] - at0;
-      C.wv[k * VS + j + QM] = C.Dx[k * VS + j + QM] + C.dnu[k * VS + j + QM] - at1;
+  OWN_KNOT(C);
+  float bt = 0.f;
+  float* wv = act ? vec(C, V_W, k) : nullptr;
+  if (act) {
+    const float* dn = vec(C, V_DNU, k);
+    float at0 = 0.f, at1 = 0.f;
+    if (k < N) {
+      const float* dn1 = vec(C, V_DNU, k + 1);
+      float cf[QM];
+      at_factor(dn1, h, cf);
+      at_rows(C.Fq + k * FQS, C.Fv + k * FQS, dn1, cf, h, j, at0, at1);
+      bt = bt_row(C.Mi + k * FQS, cf, j);
     }
-    __syncwarp();
-    if (act) {
-      const float* Qi = C.Qi + k * QIS;
-      float a = 0.f;
-#pragma unroll
-      for (int l = 0; l < QM; ++l) a += Qi[j * QM + l] * C.wv[k * VS + l];
-      const float dx0 = -a;
-      const float dx1 = -Qi[49 + j] * C.wv[k * VS + j + QM];
-      C.dX[k * VS + j] = dx0;
-      C.dX[k * VS + j + QM] = dx1;
-      bad = bad || !isfinite(dx0) || !isfinite(dx1);
-      if (k < N) {
-        const float du = -C.Ri[k * US + j] * (C.Du[k * US + j] - bt);
-        C.dU[k * US + j] = du;
-        bad = bad || !isfinite(du);
-      }
-      C.nu[k * VS + j] += C.dnu[k * VS + j];
-      C.nu[k * VS + j + QM] += C.dnu[k * VS + j + QM];
-    }
+    wv[j] = C.Dx[k * VS + j] + dn[j] - at0;
+    wv[j + QM] = C.Dx[k * VS + j + QM] + dn[j + QM] - at1;
   }
-  if (bad) atomicOr(reinterpret_cast<int*>(C.scal + S_FLAGS), F_NONFINITE);
+  __syncwarp();
+  if (act) {
+    const float* Qi = C.Qi + k * QIS;
+    float a = 0.f;
+#pragma unroll
+    for (int l = 0; l < QM; ++l) a += Qi[j * QM + l] * wv[l];
+    const float dx0 = -a;
+    const float dx1 = -Qi[49 + j] * wv[j + QM];
+    C.dX[k * VS + j] = dx0;
+    C.dX[k * VS + j + QM] = dx1;
+    bad = bad || !isfinite(dx0) || !isfinite(dx1);
+    if (k < N) {
+      const float du = -C.Ri[k * US + j] * (C.Du[k * US + j] - bt);
+      C.dU[k * US + j] = du;
+      bad = bad || !isfinite(du);
+    }
+    const float* dn = vec(C, V_DNU, k);
+    C.nu[k * VS + j] += dn[j];
+    C.nu[k * VS + j + QM] += dn[j + QM];
+  }
+  if (bad) flag_nonfinite(C);
 }
 
 // ------------------------------------------------- stage 5: line search
@@ -959,14 +1146,15 @@ __device__ __forceinline__ float trial_cost(const Ctx& C, int k, const float* x,
   return J;
 }
 
+
 // Merit (Eq. 3) of Z + alpha_i dZ for alpha_i = beta^-i (Eq. 7), i < n_alpha:
-// one thread per (alpha, knot), contributions reduced per alpha in a fixed order.
-template <int NT>
-__device__ void st_line_search(const Ctx& C, float mu, float beta, int n_alpha) {
-  const int N = C.N, K = N + 1;
-  float* contrib = C.yv;  // [n_alpha][K] (free during the line search)
-  for (int it = threadIdx.x; it < n_alpha * K; it += NT) {
-    const int a = it / K, k = it - a * K;
+// one thread per (alpha, own knot); per-alpha sums over the CTA's knots in a
+// fixed order, then over the cluster's CTAs in rank order.
+__device__ inline void st_line_search(const Ctx& C, float mu, float beta, int n_alpha, int& rbuf) {
+  const int N = C.N, K = C.k1 - C.k0;
+  float* contrib = vec(C, V_Y, C.k0);  // [n_alpha][K] (free during the line search)
+  for (int it = threadIdx.x; it < n_alpha * K; it += NTHR) {
+    const int a = it / K, k = C.k0 + it % K;
     float alpha = 1.f;
     for (int i = 0; i < a; ++i) alpha /= beta;
     float x[XM], u[QM];
@@ -988,35 +1176,54 @@ __device__ void st_line_search(const Ctx& C, float mu, float beta, int n_alpha) 
       }
       v = trial_cost(C, k, x, u) + mu * c1;
     } else {
+      v = trial_cost(C, k, x, nullptr);
+    }
+    if (k == 0) {
       float c0 = 0.f;
 #pragma unroll
-      for (int i = 0; i < XM; ++i) {
-        const float x0 = C.X[i] + alpha * C.dX[i];
-        c0 += fabsf(C.xs[i] - x0);
-      }
-      v = trial_cost(C, k, x, nullptr) + mu * c0;
+      for (int i = 0; i < XM; ++i) c0 += fabsf(C.xs[i] - (C.X[i] + alpha * C.dX[i]));
+      v += mu * c0;
     }
-    contrib[a * K + k] = v;
+    contrib[a * K + (k - C.k0)] = v;
   }
   __syncthreads();
-  // warp a sums the contributions of alpha_a in knot order (lane-strided, then a fixed tree)
+  // warp a: this CTA's partial of alpha_a (lane-strided over its knots, fixed tree)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int NW = NT / 32;
-  for (int a = warp; a < n_alpha; a += NW) {
+  float* slots = C.red + rbuf * RED_SLOTS * RED_W;  // [rank][alpha] pairs
+  for (int a = warp; a < n_alpha; a += NWARP) {
     DF s = df_zero();
-    for (int k = lane; k < K; k += 32) s = df_add(s, contrib[a * K + k]);
+    for (int kk = lane; kk < K; kk += 32) s = df_add(s, contrib[a * K + kk]);
     s = warp_df_sum(s);
     if (lane == 0) {
-      const float m = df_val(s);
-      C.scal[S_MERITS + a] = isfinite(m) ? m : INFINITY;
+      const int o = (C.rank * MAX_ALPHA + a) * 2;
+      if (C.csize > 1) {
+        cg::cluster_group cl = cg::this_cluster();
+        for (int r = 0; r < C.csize; ++r) {
+          float* dst = cl.map_shared_rank(slots, r);
+          dst[o] = s.hi;
+          dst[o + 1] = s.lo;
+        }
+      } else {
+        slots[o] = s.hi;
+        slots[o + 1] = s.lo;
+      }
     }
   }
+  csync(C);
+  if (threadIdx.x < n_alpha) {
+    const int a = threadIdx.x;
+    DF s = df_zero();
+    for (int r = 0; r < C.csize; ++r)
+      s = df_addd(s, DF{slots[(r * MAX_ALPHA + a) * 2], slots[(r * MAX_ALPHA + a) * 2 + 1]});
+    const float m = df_val(s);
+    C.scal[S_MERITS + a] = isfinite(m) ? m : INFINITY;
+  }
+  rbuf ^= 1;
   __syncthreads();
 }
 
 // Argmin with ties to the smallest index; accept only a strict decrease (c7).
-template <int NT>
-__device__ int st_accept(const Ctx& C, float beta, int n_alpha) {
+__device__ inline int st_accept(const Ctx& C, float beta, int n_alpha) {
   const int N = C.N;
   int best = 0;
   for (int a = 1; a < n_alpha; ++a)
@@ -1026,10 +1233,10 @@ __device__ int st_accept(const Ctx& C, float beta, int n_alpha) {
   if (choice >= 0) {
     float alpha = 1.f;
     for (int i = 0; i < choice; ++i) alpha /= beta;
-    for (int i = threadIdx.x; i < (N + 1) * VS; i += NT) C.X[i] += alpha * C.dX[i];
-    for (int i = threadIdx.x; i < N * US; i += NT) C.U[i] += alpha * C.dU[i];
+    const int ke = C.k1 < N ? C.k1 : N;
+    for (int i = threadIdx.x; i < (C.k1 - C.k0) * VS; i += NTHR) C.X[C.k0 * VS + i] += alpha * C.dX[C.k0 * VS + i];
+    for (int i = threadIdx.x; i < (ke - C.k0) * US; i += NTHR) C.U[C.k0 * US + i] += alpha * C.dU[C.k0 * US + i];
   }
-  __syncthreads();
   return choice;
 }
 

@@ -24,7 +24,7 @@ constexpr int kMaxModels = 8;
 constexpr int kMaxDevices = 64;
 // Floats of one solve's workspace at N = 64 (Schur blocks in shared memory);
 // checked against ws_layout() at set-up.
-constexpr size_t kWsStride = 52224;
+constexpr size_t kWsStride = 53248;
 
 static __device__ __align__(256) float g_scratch[kMaxSolves * kWsStride];
 static __device__ __align__(256) ProbDesc g_probs[kMaxSolves];
@@ -132,7 +132,7 @@ extern "C" gato_status gato_solve_noalloc(const gato_model_desc* models, int32_t
   }
   ProbDesc pd[kMaxSolves];
   int order[kMaxSolves];
-  int nmax = 1;
+  int Ns[kMaxSolves];
   for (int i = 0; i < n; ++i) {
     const gato_problem& p = problems[i];
     if (!problem_ok(p, n_models)) return GATO_E_INVALID;
@@ -150,19 +150,10 @@ extern "C" gato_status gato_solve_noalloc(const gato_model_desc* models, int32_t
     d.X = p.X;
     d.U = p.U;
     d.lam = p.lambda;
-    nmax = p.N > nmax ? p.N : nmax;
-    order[i] = i;
+    Ns[i] = p.N;
   }
-  // longest horizon first (insertion sort keeps equal horizons in input order)
-  for (int i = 1; i < n; ++i) {
-    const int v = order[i];
-    int j = i - 1;
-    while (j >= 0 && problems[order[j]].N < problems[v].N) {
-      order[j + 1] = order[j];
-      --j;
-    }
-    order[j + 1] = v;
-  }
+  // grouped by cluster size, longest horizon first within a group
+  order_solves(Ns, n, order, LaunchPlan());
   DevicePtrs* P = nullptr;
   gato_status s = setup_device(&P);
   if (s != GATO_OK) return s;
@@ -183,7 +174,8 @@ extern "C" gato_status gato_solve_noalloc(const gato_model_desc* models, int32_t
   a.ws_stride = kWsStride;
   a.layout = ws_layout(kMaxHorizon, false, false);
   a.n = n;
-  a.nmax = nmax;
+  a.nmax = 1;
+  a.csize = 1;
   a.iters = max_sqp_iters;
   a.prm.mu = sp.mu;
   a.prm.beta = sp.beta;
@@ -193,8 +185,9 @@ extern "C" gato_status gato_solve_noalloc(const gato_model_desc* models, int32_t
   a.prm.precond = sp.precond;
   a.prm.kkt_tol = sp.kkt_tol;
   a.prm.max_iter = max_sqp_iters;
-  a.threads = 0;
-  if (launch_fused(a, stream) != cudaSuccess) {
+  a.timing = nullptr;
+  a.variant = 0;
+  if (launch_fused_grouped(a, order, P->order, Ns, n, stream, LaunchPlan()) != cudaSuccess) {
     cudaGetLastError();
     return GATO_E_CUDA;
   }

@@ -29,9 +29,11 @@ EXPORTED = (
     "gato_default_params", "gato_create_batch", "gato_solve", "gato_step", "gato_solve_plain",
     "gato_sync", "gato_get_results", "gato_destroy_batch", "gato_status_string", "gato_last_error",
     "gato_last_transfer_bytes", "gato_debug_plain_stage", "gato_debug_layout", "gato_solve_noalloc",
+    "gato_debug_stage_cycles", "gato_set_launch_config", "gato_autotune", "gato_graph_create",
+    "gato_graph_launch", "gato_graph_wait", "gato_graph_destroy",
 )
 LAYOUT_NAMES = ("X", "U", "dX", "dU", "Fq", "Fv", "Minv", "qdd", "dTau", "Qinv", "Rinv", "q", "r",
-                "c", "Jk", "Linv", "links", "D", "L", "P", "vec", "scal", "Dx", "Du")
+                "c", "Jk", "Linv", "links", "D", "L", "P", "vec", "scal", "Dx", "Du", "nu")
 
 
 class ModelDesc(C.Structure):
@@ -56,6 +58,10 @@ class Problem(C.Structure):
                 ("cost_kind", C.c_int32), ("w", C.c_float * 6), ("mem", C.c_int32),
                 ("x_s", C.c_void_p), ("x_ref", C.c_void_p), ("ee_ref", C.c_void_p),
                 ("X", C.c_void_p), ("U", C.c_void_p), ("lam", C.c_void_p)]
+
+
+class LaunchConfig(C.Structure):
+    _fields_ = [("variant", C.c_int32), ("knots_per_cta", C.c_int32), ("cluster", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -105,6 +111,21 @@ def load() -> C.CDLL:
     L.gato_solve_noalloc.argtypes = [C.POINTER(ModelDesc), C.c_int32, C.POINTER(SolverParams),
                                      C.POINTER(Problem), C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]
     L.gato_solve_noalloc.restype = C.c_int
+    L.gato_debug_stage_cycles.argtypes = [bp, C.c_int32, C.c_void_p, C.c_int32]
+    L.gato_debug_stage_cycles.restype = C.c_int
+    L.gato_set_launch_config.argtypes = [bp, C.POINTER(LaunchConfig)]
+    L.gato_set_launch_config.restype = C.c_int
+    L.gato_autotune.argtypes = [bp, C.POINTER(Problem), C.c_int32, C.c_int32, C.c_int32,
+                                C.POINTER(LaunchConfig), C.POINTER(C.c_float)]
+    L.gato_autotune.restype = C.c_int
+    L.gato_graph_create.argtypes = [bp, C.POINTER(Problem), C.c_int32, C.c_int32, C.POINTER(C.c_void_p)]
+    L.gato_graph_create.restype = C.c_int
+    L.gato_graph_launch.argtypes = [bp, C.POINTER(Result)]
+    L.gato_graph_launch.restype = C.c_int
+    L.gato_graph_wait.argtypes = [bp, C.POINTER(Result)]
+    L.gato_graph_wait.restype = C.c_int
+    L.gato_graph_destroy.argtypes = [bp]
+    L.gato_graph_destroy.restype = None
     _lib = L
     return L
 
@@ -186,7 +207,7 @@ def gato_last_transfer_bytes(handle):
 
 
 def gato_debug_layout(handle):
-    off = (C.c_int64 * 24)()
+    off = (C.c_int64 * 25)()
     total = load().gato_debug_layout(C.c_void_p(handle), off)
     return total, dict(zip(LAYOUT_NAMES, list(off)))
 
@@ -200,12 +221,66 @@ def gato_debug_plain_stage(handle, problems, stop_stage):
     return buf, off
 
 
+STAGE_NAMES = ("load", "mass", "fd", "value_cost", "tangents", "jacobians", "kkt", "schur",
+               "block_inverse", "pcg_init", "pcg_S", "pcg_y", "pcg_wz", "recover", "line_search",
+               "accept")
+
+
+def gato_debug_stage_cycles(handle, enable, n=0):
+    """enable=1: start counting; enable=0: return an (n, 16) array of cycles and stop."""
+    out = np.zeros((max(n, 1), 16), np.int64)
+    s = load().gato_debug_stage_cycles(C.c_void_p(handle), enable,
+                                       out.ctypes.data if (not enable and n) else None, n)
+    _check(handle, s, "gato_debug_stage_cycles")
+    return None if enable else out[:n]
+
+
 def gato_solve_noalloc(models, n_models, params, problems, n, iters, results_dev_ptr, stream=0):
     """Allocation-free solve: device problems only, results written to device memory."""
     s = load().gato_solve_noalloc(models, n_models, C.byref(params), problems, n, iters,
                                   C.c_void_p(results_dev_ptr), C.c_void_p(stream or 0))
     if s != GATO_OK:
         raise GatoError(s, f"gato_solve_noalloc: {gato_status_string(s)}")
+
+
+def gato_set_launch_config(handle, variant=None, knots_per_cta=0, cluster=0):
+    """variant None clears the forced configuration."""
+    if variant is None:
+        s = load().gato_set_launch_config(C.c_void_p(handle), None)
+    else:
+        cfg = LaunchConfig(variant, knots_per_cta, cluster)
+        s = load().gato_set_launch_config(C.c_void_p(handle), C.byref(cfg))
+    _check(handle, s, "gato_set_launch_config")
+
+
+def gato_autotune(handle, problems, n, iters, reps=3):
+    cfg, ms = LaunchConfig(), C.c_float()
+    s = load().gato_autotune(C.c_void_p(handle), problems, n, iters, reps, C.byref(cfg), C.byref(ms))
+    _check(handle, s, "gato_autotune")
+    return dict(variant=cfg.variant, knots_per_cta=cfg.knots_per_cta, cluster=cfg.cluster), ms.value
+
+
+def gato_graph_create(handle, problems, n, iters) -> int:
+    g = C.c_void_p()
+    s = load().gato_graph_create(C.c_void_p(handle), problems, n, iters, C.byref(g))
+    _check(handle, s, "gato_graph_create")
+    return g.value
+
+
+def gato_graph_launch(graph, results=None):
+    s = load().gato_graph_launch(C.c_void_p(graph), results)
+    if s != GATO_OK:
+        raise GatoError(s, f"gato_graph_launch: {gato_status_string(s)}")
+
+
+def gato_graph_wait(graph, results=None):
+    s = load().gato_graph_wait(C.c_void_p(graph), results)
+    if s != GATO_OK:
+        raise GatoError(s, f"gato_graph_wait: {gato_status_string(s)}")
+
+
+def gato_graph_destroy(graph):
+    load().gato_graph_destroy(C.c_void_p(graph))
 
 
 # ------------------------------------------------------------- conveniences
@@ -261,12 +336,56 @@ class Batch:
     def solve_async(self, problems, n, iters):
         gato_solve(self.handle, problems, n, iters, None)
 
+    def set_launch_config(self, variant=None, knots_per_cta=0, cluster=0):
+        gato_set_launch_config(self.handle, variant, knots_per_cta, cluster)
+
+    def autotune(self, problems, n, iters, reps=3):
+        """Times the launch configurations on these problems; returns (config, median ms)."""
+        return gato_autotune(self.handle, problems, n, iters, reps)
+
+    def capture(self, problems, n, iters):
+        """A CUDA graph of one solve call on device problems."""
+        return Graph(self, problems, n, iters)
+
     def sync(self, timeout_us=-1):
         return gato_sync(self.handle, timeout_us)
 
     def close(self):
         if getattr(self, "handle", None):
             gato_destroy_batch(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Graph:
+    """A captured solve (gato_graph_*); replay() returns the per-solve results."""
+
+    def __init__(self, batch: Batch, problems, n, iters):
+        self.batch = batch
+        self.n = n
+        self.handle = gato_graph_create(batch.handle, problems, n, iters)
+
+    def replay(self, wait=True):
+        if not wait:
+            gato_graph_launch(self.handle, None)
+            return None
+        res = (Result * self.n)()
+        gato_graph_launch(self.handle, res)
+        return res
+
+    def wait(self):
+        res = (Result * self.n)()
+        gato_graph_wait(self.handle, res)
+        return res
+
+    def close(self):
+        if getattr(self, "handle", None):
+            gato_graph_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -41,12 +41,14 @@ def rel(a, b):
     return np.abs(np.asarray(a) - np.asarray(b)).max() / max(1.0, np.abs(b).max())
 
 
-def gpu_solve(G, probs, iters, plain=False, X=None, U=None, lam=None, **prm):
+def gpu_solve(G, probs, iters, plain=False, X=None, U=None, lam=None, launch=None, **prm):
     models = []
     for p in probs:
         if p.model not in models:
             models.append(p.model)
     B = G.Batch(models, len(probs), max(p.N for p in probs), **prm)
+    if launch is not None:
+        B.set_launch_config(*launch)
     hp = G.HostProblems(B, probs, X=X, U=U, lam=lam)
     res = B.solve(hp.arr, hp.n, iters, plain=plain)
     out = G.results_to_dicts(res, hp.n)
@@ -96,12 +98,12 @@ def test_batch_invariance_bitwise(G):
         np.testing.assert_array_equal(alone["U"], together[i]["U"])
 
 
-def _per_step_parity(G, oracle, prob, iters, factor=30.0):
+def _per_step_parity(G, oracle, prob, iters, factor=30.0, launch=None):
     """Each GPU SQP step against the oracle step from the same iterate."""
     X, U, lam = oracle.cold_start(prob)
     worst = 0.0
     for it in range(iters):
-        g = gpu_solve(G, [prob], 1, X=[X], U=[U], lam=[lam])[0]
+        g = gpu_solve(G, [prob], 1, X=[X], U=[U], lam=[lam], launch=launch)[0]
         o = oracle.solve(prob, max_iter=1, X=X, U=U, lam=lam)
         sens, dmax = qp_sensitivity(oracle, prob, X, U, lam)
         if g["sqp_iters"] == 1 and len(o["alpha_idx"]) == 1 and o["alpha_idx"][0] >= 0:

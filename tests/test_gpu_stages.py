@@ -56,10 +56,14 @@ def block(buf, off, name, K):
     return np.transpose(a, (0, 2, 1))  # stored column-major
 
 
+# vector slots of the plain form's global window (one halo knot at each end)
+V_RR, V_P0, V_P1, V_Q, V_Y, V_W, V_Z, V_RHS, V_DNU = range(9)
+
+
 def vec(buf, off, k_max, idx):
-    VV = (k_max + 1) * VS
-    base = off["vec"] + idx * VV
-    return buf[base:base + VV].reshape(k_max + 1, VS)[:, :XM]
+    VV = (k_max + 3) * VS
+    base = off["vec"] + idx * VV + VS
+    return buf[base:base + (k_max + 1) * VS].reshape(k_max + 1, VS)[:, :XM]
 
 
 PROBS = [
@@ -145,7 +149,7 @@ def test_schur_and_preconditioner_stage(G, oracle, name, mk):
     D = block(buf, off, "D", K)
     L = block(buf, off, "L", K)
     P = block(buf, off, "P", K)
-    rhs = vec(buf, off, prob.N, 8)
+    rhs = vec(buf, off, prob.N, V_RHS)
     # (1) the stage's own arithmetic: Eq. 5 blocks and the correction rhs
     #     recomputed in FP64 from the GPU's inputs to this stage
     Fq = buf[off["Fq"]:off["Fq"] + N * 49].reshape(N, 7, 7)
@@ -207,8 +211,8 @@ def test_pcg_recovery_and_line_search_stages(G, oracle, name, mk, precond):
     D = block(buf, off, "D", K)
     L = block(buf, off, "L", K)
     P = block(buf, off, "P", K)
-    rhs_g = vec(buf, off, N, 8)
-    nu_g = vec(buf, off, N, 0)
+    rhs_g = vec(buf, off, N, V_RHS)
+    nu_g = knots(buf, off, "nu", K, VS, XM)
     from tests.test_oracle_kkt import blocks_to_dense
     Sg = blocks_to_dense(D, L[1:])
     Dinv = np.zeros_like(Sg)
@@ -218,7 +222,7 @@ def test_pcg_recovery_and_line_search_stages(G, oracle, name, mk, precond):
     for k in range(K):
         Og[k * XM:(k + 1) * XM, k * XM:(k + 1) * XM] = 0
     Phi = Dinv - Dinv @ Og @ Dinv if precond == 0 else Dinv
-    dnu = vec(buf, off, N, 9)
+    dnu = vec(buf, off, N, V_DNU)
     r0 = rhs_g.ravel()
     r = rhs_g.ravel() - Sg @ dnu.ravel()
     nu_g = dnu
@@ -236,7 +240,7 @@ def test_pcg_recovery_and_line_search_stages(G, oracle, name, mk, precond):
     Ri = knots(buf, off, "Rinv", N, US, 7)
     qg = knots(buf, off, "q", K, VS, XM)
     rg = knots(buf, off, "r", N, US, 7)
-    nup = vec(buf, off, N, 9)
+    nup = vec(buf, off, N, V_DNU)
     Dx = knots(buf, off, "Dx", K, VS, XM)
     Du = knots(buf, off, "Du", N, US, 7)
     I7 = np.eye(7)
