@@ -4,8 +4,11 @@ Workload (the figure-eight sweep at N=64, 7-DoF, per the headline metric):
 B=256 end-effector tracking solves, N=64 knots, dt=0.01 s, 10 SQP iterations
 per solve call, FP32 with compensated PCG dots and merit sums.  A "step" is one
 gato_solve call over the whole batch from the cold start.  Extra keys report
-the p50/p99 latency of the B=32 call (10 and 3 SQP iterations) and the plain
-one-solve-per-launch GPU form at B=32.
+the p50/p99 latency of the B=32 call (10 and 3 SQP iterations), the plain
+one-solve-per-launch GPU form at B=32, the uneven mix (128 solves, N in
+16..128, two arms, per-solve stop at KKT 1e-5 or 20 iterations) replayed from a
+CUDA graph, and the serving loop under Poisson arrivals (1k-20k ticks/s over
+128 resident sessions of that mix, 3 SQP iterations per tick).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -191,6 +194,8 @@ def run_gpu(args):
     if rank == 0:
         lat = latency_runs(gato, I, torch, stream, flush, launch_cfg=True)
         plain = plain_form(gato, I, torch)
+        uneven = uneven_graph(gato, I, torch)
+        serve = serving_runs(gato, I)
         e2e = e2e_run(gato, I, args)
         cpu = cpu_baseline()
         out = {
@@ -203,7 +208,7 @@ def run_gpu(args):
                        "B": B_MAIN, "N": N_MAIN, "sqp_iters": ITERS, "dof": 7,
                        "parallelism": f"replicas x{ws}", "l2": "flushed between timed launches (512 MB write)",
                        "launch": launch},
-            "latency_ms": lat, "plain_gpu_form": plain,
+            "latency_ms": lat, "plain_gpu_form": plain, "uneven_graph": uneven, "serving": serve,
             "speedup_vs_plain_B32": round(plain["solves_per_s_B32"] and lat["B32_iters10"]["solves_per_s"]
                                           / plain["solves_per_s_B32"], 2),
             "pcg_iters_per_solve": round(pcg / dp.n, 1), "sqp_iters_per_solve": round(sqp / dp.n, 2),
@@ -273,6 +278,57 @@ def plain_form(gato, I, torch, reps=3):
     t = statistics.median(ts)
     return {"solves_per_s_B32": round(B_LAT / t, 1), "ms_per_call_B32": round(1e3 * t, 2),
             "launches_per_solve_iter": 12}
+
+
+def uneven_graph(gato, I, torch, reps=10):
+    """The uneven mix captured once in a CUDA graph and replayed (device events)."""
+    probs = I.config_uneven(128)
+    B = gato.Batch([I.arm7(), I.arm6()], len(probs), 128, kkt_tol=1e-5)
+    dp = gato.DeviceProblems(B, probs)
+    graph = B.capture(dp.arr, dp.n, 20)
+    ts, res = [], None
+    for rep in range(reps + 2):
+        dp.reset()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        s = torch.cuda.current_stream()
+        e0.record(s)
+        graph.replay(wait=False)
+        e1.record(s)
+        res = graph.wait()
+        torch.cuda.synchronize()
+        if rep >= 2:
+            ts.append(e0.elapsed_time(e1))
+    conv = sum(1 for i in range(dp.n) if res[i].flags & gato.SOLVE_CONVERGED)
+    iters = [res[i].sqp_iters for i in range(dp.n)]
+    graph.close()
+    B.close()
+    t = statistics.median(ts)
+    return {"solves": len(probs), "ms_per_replay": round(t, 4), "solves_per_s": round(len(probs) / (t / 1e3), 1),
+            "converged": conv, "sqp_iters_mean": round(sum(iters) / len(iters), 2), "sqp_iters_max": max(iters)}
+
+
+def serving_runs(gato, I, rates=(1000.0, 5000.0, 20000.0), duration_s=1.0):
+    """Serving loop: Poisson ticks over 128 resident sessions of the uneven mix."""
+    from paper_2510_07625_gb300 import serving
+
+    probs = I.config_uneven(128)
+    srv = serving.Server([I.arm7(), I.arm6()], 128, 128, max_batch=128, max_inflight=4, sqp_iters=3)
+    sids = [srv.open(p) for p in probs]
+    # warm every session up with one tick (cold start -> warm start)
+    for s, p in zip(sids, probs):
+        t = srv.submit(s, p.x_s, False)
+        srv.poll(t, -1)
+    out = {"sessions": len(sids), "sqp_iters_per_tick": 3, "max_inflight": 4,
+           "capacity": srv.stats()["capacity"]}
+    runs = []
+    for rate in rates:
+        r, _ = serving.poisson_load(srv, sids, probs, rate, duration_s, seed=int(rate))
+        runs.append(r)
+    out["runs"] = runs
+    srv.close()
+    return out
 
 
 def e2e_run(gato, I, args):

@@ -227,6 +227,101 @@ gato_status gato_graph_launch(gato_graph* g, gato_result* results);
 gato_status gato_graph_wait(gato_graph* g, gato_result* results);
 void gato_graph_destroy(gato_graph* g);
 
+/* ---- serving loop: continuous batching of MPC control ticks ----
+ * A server keeps each session's trajectory (X, U, lambda, x_s, reference)
+ * resident on the device.  A request is one control tick of a session: a new
+ * measured state x_s, optionally a one-knot warm-start shift (X_k <- X_{k+1},
+ * U_k <- U_{k+1}, lambda_k <- lambda_{k+1}; the last knot keeps its value),
+ * then sqp_iters SQP iterations.  A worker thread launches every pending
+ * request together whenever one of max_inflight launch contexts is free, so
+ * requests that arrive while others run join the next launch and their work
+ * overlaps on the GPU.  A request's arithmetic depends only on its own
+ * session (cluster size fixed by its horizon), so its result is the same
+ * alone and in any mix.  Thread-safe: any host thread may submit and poll. */
+typedef struct gato_server gato_server;
+
+typedef struct {
+  int32_t max_sessions;      /* resident trajectories wanted (slots) */
+  int32_t max_horizon;       /* largest N of a session (<= 256) */
+  int32_t max_batch;         /* requests per launch (halved until memory allows) */
+  int32_t max_inflight;      /* launch contexts on the GPU at once, 1..8 */
+  int32_t sqp_iters;         /* SQP iterations per request */
+  int64_t mem_budget_bytes;  /* device memory the server may reserve; 0 = 90% of free */
+} gato_server_desc;
+
+typedef struct {
+  gato_result result;
+  float u0[7];               /* first control of the new solution (dof entries used) */
+  float x1[14];              /* its predicted state at knot 1 (2*dof entries used) */
+  int64_t submit_ns, done_ns;/* steady-clock times of submission and completion */
+} gato_reply;
+
+typedef struct {
+  int32_t capacity;          /* session slots admitted by memory */
+  int32_t sessions_open;
+  int32_t max_batch, max_inflight;
+  int64_t submitted, completed, launches, pending;
+  int64_t reserved_bytes;    /* device memory held by the server */
+} gato_server_stats;
+
+/* Creates a server over the models and solver parameters of models_desc
+ * (its max_batch / max_horizon are ignored).  Device memory is reserved here:
+ * max_inflight launch contexts of max_batch solves each (max_batch halves
+ * until they fit half the budget), then as many session slots as the rest of
+ * the budget holds, at most max_sessions (see gato_server_stats).  Uses the
+ * current CUDA device.  GATO_E_NOMEM if not even one slot fits. */
+gato_status gato_server_create(const gato_batch_desc* models_desc, const gato_server_desc* d,
+                               gato_server** out);
+
+/* Admits a session from a host problem (mem = GATO_MEM_HOST; X, U, lambda
+ * may be NULL for the cold start).  GATO_E_BUSY when every slot is taken:
+ * retry after a gato_server_close.  Synchronous (copies the slot image). */
+gato_status gato_server_open(gato_server* s, const gato_problem* p, int32_t* session);
+
+/* Queues one control tick: x_s is a host array of 2*dof floats, shift != 0
+ * shifts the warm start by one knot first.  GATO_E_BUSY if the session still
+ * has a request pending or on the GPU (ticks of a session are sequential). */
+gato_status gato_server_submit(gato_server* s, int32_t session, const float* x_s, int32_t shift,
+                               int64_t* ticket);
+
+/* Waits up to timeout_us (0 = just check, < 0 = forever) for a ticket and
+ * consumes it: GATO_OK with *out filled (out may be NULL), GATO_E_TIMEOUT if
+ * it is not done yet, GATO_E_INVALID for an unknown or consumed ticket. */
+gato_status gato_server_poll(gato_server* s, int64_t ticket, int64_t timeout_us, gato_reply* out);
+
+/* Copies a session's resident X [(N+1)*2dof], U [N*dof], lambda [(N+1)*2dof]
+ * to host arrays (any may be NULL).  GATO_E_BUSY while it has a request. */
+gato_status gato_server_read(gato_server* s, int32_t session, float* X, float* U, float* lambda);
+
+/* Frees a session's slot (GATO_E_BUSY while it has a request). */
+gato_status gato_server_close(gato_server* s, int32_t session);
+
+gato_status gato_server_get_stats(gato_server* s, gato_server_stats* out);
+
+/* Load driver for measuring the loop (config: Poisson arrivals of MPC ticks).
+ * Replays an arrival schedule on the calling thread: arrival i, due at
+ * t_arrival[i] seconds after the call starts (sorted), is a tick of client
+ * client[i] (an index into sessions[0..n_sessions)), whose new state is the
+ * client's last predicted state x1 (x_init[c*14..] before its first reply)
+ * plus noise[i*14..] (2*dof entries used), submitted with a one-knot shift.
+ * A client's ticks are sequential: an arrival for a busy client waits for
+ * its previous reply.  latency_ms[i] = completion time - scheduled arrival
+ * (host steady clock), so waiting of any kind is included.  Every session
+ * must be open and idle; one drive at a time. */
+typedef struct {
+  int64_t completed;
+  double elapsed_s;
+  int64_t launches;      /* kernel batches launched during the drive */
+  int64_t max_backlog;   /* most arrivals waiting for a busy client at once */
+} gato_drive_stats;
+gato_status gato_server_drive(gato_server* s, const int32_t* sessions, int32_t n_sessions,
+                              const float* x_init, const double* t_arrival, const int32_t* client,
+                              const float* noise, int64_t n, float* latency_ms, gato_drive_stats* out);
+const char* gato_server_last_error(const gato_server* s);
+
+/* Stops the worker, waits for launches in flight, frees everything. */
+void gato_server_destroy(gato_server* s);
+
 /* Waits for the batch stream, at most timeout_us microseconds (< 0 = forever);
  * GATO_E_TIMEOUT leaves the work running.  Uses a polling host wait, never a
  * device-side spin. */

@@ -416,6 +416,15 @@ gato_status snapshot_restore(gato_batch* b, const gato_problem* p, int n, const 
 
 }  // namespace
 
+// Helpers for the serving loop (gato_server.cu), which keeps its model table
+// and parameters in a one-solve batch.
+namespace gato {
+gato_status batch_validate_problem(gato_batch* b, const gato_problem& p) { return validate_problem(b, p, 0); }
+const DevModel* batch_models_device(const gato_batch* b) { return b->models_d; }
+int batch_model_dof(const gato_batch* b, int model) { return b->model_dof[model]; }
+Params batch_params(const gato_batch* b, int iters) { return to_params(b->params, iters); }
+}  // namespace gato
+
 extern "C" {
 
 void gato_default_params(gato_solver_params* o) {

@@ -11,6 +11,7 @@
 // padded rows of every matrix and vector stay exactly zero.
 #pragma once
 
+#include <type_traits>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -68,43 +69,68 @@ enum : int {
 };
 
 // ----------------------------------------------------------------- 3-vectors
+// Templated on the scalar: float on the hot path, double for the FP64
+// evaluation of the merit's dynamics.  A scalar factor converts to the
+// vector's type (the scalar argument does not take part in deduction).
 
-struct V3 {
-  float x, y, z;
+template <typename T>
+struct Vec3 {
+  T x, y, z;
 };
+using V3 = Vec3<float>;
+template <typename T>
+struct Same {
+  using type = T;
+};
+template <typename T>
+__device__ __forceinline__ Vec3<T> v3t(T x, T y, T z) { return Vec3<T>{x, y, z}; }
 __device__ __forceinline__ V3 v3(float x, float y, float z) { return V3{x, y, z}; }
-__device__ __forceinline__ V3 vzero() { return V3{0.f, 0.f, 0.f}; }
-__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return V3{a.x + b.x, a.y + b.y, a.z + b.z}; }
-__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return V3{a.x - b.x, a.y - b.y, a.z - b.z}; }
-__device__ __forceinline__ V3 operator*(float s, V3 a) { return V3{s * a.x, s * a.y, s * a.z}; }
-__device__ __forceinline__ V3 cross(V3 a, V3 b) {
-  return V3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+template <typename T = float>
+__device__ __forceinline__ Vec3<T> vzero() { return Vec3<T>{T(0), T(0), T(0)}; }
+template <typename T>
+__device__ __forceinline__ Vec3<T> operator+(Vec3<T> a, Vec3<T> b) { return Vec3<T>{a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <typename T>
+__device__ __forceinline__ Vec3<T> operator-(Vec3<T> a, Vec3<T> b) { return Vec3<T>{a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <typename T>
+__device__ __forceinline__ Vec3<T> operator*(typename Same<T>::type s, Vec3<T> a) {
+  return Vec3<T>{s * a.x, s * a.y, s * a.z};
 }
-__device__ __forceinline__ float dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ V3 mulI(V3 I, V3 v) { return V3{I.x * v.x, I.y * v.y, I.z * v.z}; }
+template <typename T>
+__device__ __forceinline__ Vec3<T> cross(Vec3<T> a, Vec3<T> b) {
+  return Vec3<T>{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+template <typename T>
+__device__ __forceinline__ T dot(Vec3<T> a, Vec3<T> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <typename T>
+__device__ __forceinline__ Vec3<T> mulI(Vec3<T> I, Vec3<T> v) { return Vec3<T>{I.x * v.x, I.y * v.y, I.z * v.z}; }
 
 // Coordinates of a parent-frame vector in the child frame rotated by q about axis a.
-__device__ __forceinline__ V3 rotT(int a, float s, float c, V3 v) {
-  if (a == 2) return V3{c * v.x + s * v.y, -s * v.x + c * v.y, v.z};
-  if (a == 1) return V3{c * v.x - s * v.z, v.y, s * v.x + c * v.z};
-  return V3{v.x, c * v.y + s * v.z, -s * v.y + c * v.z};
+template <typename T>
+__device__ __forceinline__ Vec3<T> rotT(int a, T s, T c, Vec3<T> v) {
+  if (a == 2) return Vec3<T>{c * v.x + s * v.y, -s * v.x + c * v.y, v.z};
+  if (a == 1) return Vec3<T>{c * v.x - s * v.z, v.y, s * v.x + c * v.z};
+  return Vec3<T>{v.x, c * v.y + s * v.z, -s * v.y + c * v.z};
 }
 // Child-frame vector expressed in the parent frame.
-__device__ __forceinline__ V3 rot(int a, float s, float c, V3 v) {
-  if (a == 2) return V3{c * v.x - s * v.y, s * v.x + c * v.y, v.z};
-  if (a == 1) return V3{c * v.x + s * v.z, v.y, -s * v.x + c * v.z};
-  return V3{v.x, c * v.y - s * v.z, s * v.y + c * v.z};
+template <typename T>
+__device__ __forceinline__ Vec3<T> rot(int a, T s, T c, Vec3<T> v) {
+  if (a == 2) return Vec3<T>{c * v.x - s * v.y, s * v.x + c * v.y, v.z};
+  if (a == 1) return Vec3<T>{c * v.x + s * v.z, v.y, -s * v.x + c * v.z};
+  return Vec3<T>{v.x, c * v.y - s * v.z, s * v.y + c * v.z};
 }
 // e_a x v
-__device__ __forceinline__ V3 ecross(int a, V3 v) {
-  if (a == 2) return V3{-v.y, v.x, 0.f};
-  if (a == 1) return V3{v.z, 0.f, -v.x};
-  return V3{0.f, -v.z, v.y};
+template <typename T>
+__device__ __forceinline__ Vec3<T> ecross(int a, Vec3<T> v) {
+  if (a == 2) return Vec3<T>{-v.y, v.x, T(0)};
+  if (a == 1) return Vec3<T>{v.z, T(0), -v.x};
+  return Vec3<T>{T(0), -v.z, v.y};
 }
-__device__ __forceinline__ V3 unitv(int a) {
-  return a == 0 ? V3{1.f, 0.f, 0.f} : (a == 1 ? V3{0.f, 1.f, 0.f} : V3{0.f, 0.f, 1.f});
+template <typename T = float>
+__device__ __forceinline__ Vec3<T> unitv(int a) {
+  return a == 0 ? Vec3<T>{T(1), T(0), T(0)} : (a == 1 ? Vec3<T>{T(0), T(1), T(0)} : Vec3<T>{T(0), T(0), T(1)});
 }
-__device__ __forceinline__ float comp(int a, V3 v) { return a == 0 ? v.x : (a == 1 ? v.y : v.z); }
+template <typename T>
+__device__ __forceinline__ T comp(int a, Vec3<T> v) { return a == 0 ? v.x : (a == 1 ? v.y : v.z); }
 
 // ------------------------------------------------------ compensated sums (Dot2)
 // Error-free transformations (Knuth TwoSum, FMA-based TwoProduct) keep a
@@ -172,66 +198,73 @@ struct LinkRec {  // value-pass quantities of one link (link coordinates)
 };
 static_assert(sizeof(LinkRec) == LVS * sizeof(float), "link record size");
 
-__device__ __forceinline__ V3 mcom(const DevModel& M, int i) {
-  return V3{M.com[3 * i], M.com[3 * i + 1], M.com[3 * i + 2]};
+template <typename T = float>
+__device__ __forceinline__ Vec3<T> mcom(const DevModel& M, int i) {
+  return Vec3<T>{T(M.com[3 * i]), T(M.com[3 * i + 1]), T(M.com[3 * i + 2])};
 }
-__device__ __forceinline__ V3 minert(const DevModel& M, int i) {
-  return V3{M.Ic[3 * i], M.Ic[3 * i + 1], M.Ic[3 * i + 2]};
+template <typename T = float>
+__device__ __forceinline__ Vec3<T> minert(const DevModel& M, int i) {
+  return Vec3<T>{T(M.Ic[3 * i]), T(M.Ic[3 * i + 1]), T(M.Ic[3 * i + 2])};
 }
 
 // Inverse dynamics tau = ID(q, qd, qdd) by RNEA.  sq/cq are sin/cos of q.
 // `grav` is the magnitude of gravity along -z (0 turns it off).  When rec is
-// non-null the link quantities are stored for a later tangent pass.
-__device__ __forceinline__ void rnea_value(const DevModel& M, const float* sq, const float* cq,
-                                           const float* qd, const float* qdd, float grav,
-                                           float* tau, LinkRec* rec) {
-  V3 F[QM], Nm[QM];
-  V3 wp = vzero(), wdp = vzero(), ap = v3(0.f, 0.f, grav);
+// non-null (float only) the link quantities are stored for a tangent pass.
+template <typename T>
+__device__ __forceinline__ void rnea_value(const DevModel& M, const T* sq, const T* cq, const T* qd,
+                                           const T* qdd, T grav, T* tau, LinkRec* rec) {
+  using W = Vec3<T>;
+  W F[QM], Nm[QM];
+  W wp = vzero<T>(), wdp = vzero<T>(), ap = v3t<T>(T(0), T(0), grav);
 #pragma unroll
   for (int i = 0; i < QM; ++i) {
     const int a = M.axis[i];
-    const float s = sq[i], c = cq[i];
-    const V3 r = v3(0.f, 0.f, i > 0 ? M.L[i - 1] : 0.f);
-    const V3 ao = ap + cross(wdp, r) + cross(wp, cross(wp, r));
-    const V3 wpT = rotT(a, s, c, wp);
-    const V3 wdpT = rotT(a, s, c, wdp);
-    const V3 e = unitv(a);
-    const V3 w = wpT + qd[i] * e;
-    const V3 wd = wdpT + qd[i] * cross(wpT, e) + qdd[i] * e;
-    const V3 acc = rotT(a, s, c, ao);
-    const V3 cm = mcom(M, i), Ii = minert(M, i);
-    const V3 ac = acc + cross(wd, cm) + cross(w, cross(w, cm));
-    F[i] = M.m[i] * ac;
+    const T s = sq[i], c = cq[i];
+    const W r = v3t<T>(T(0), T(0), i > 0 ? T(M.L[i - 1]) : T(0));
+    const W ao = ap + cross(wdp, r) + cross(wp, cross(wp, r));
+    const W wpT = rotT(a, s, c, wp);
+    const W wdpT = rotT(a, s, c, wdp);
+    const W e = unitv<T>(a);
+    const W w = wpT + qd[i] * e;
+    const W wd = wdpT + qd[i] * cross(wpT, e) + qdd[i] * e;
+    const W acc = rotT(a, s, c, ao);
+    const W cm = mcom<T>(M, i), Ii = minert<T>(M, i);
+    const W ac = acc + cross(wd, cm) + cross(w, cross(w, cm));
+    F[i] = T(M.m[i]) * ac;
     Nm[i] = mulI(Ii, wd) + cross(w, mulI(Ii, w));
-    if (rec) {
-      rec[i].s = s;
-      rec[i].c = c;
-      rec[i].wpT = wpT;
-      rec[i].wdpT = wdpT;
-      rec[i].w = w;
-      rec[i].wd = wd;
-      rec[i].a = acc;
+    if constexpr (std::is_same<T, float>::value) {
+      if (rec) {
+        rec[i].s = s;
+        rec[i].c = c;
+        rec[i].wpT = wpT;
+        rec[i].wdpT = wdpT;
+        rec[i].w = w;
+        rec[i].wd = wd;
+        rec[i].a = acc;
+      }
     }
     wp = w;
     wdp = wd;
     ap = acc;
   }
-  V3 fc = vzero(), nc = vzero();
+  W fc = vzero<T>(), nc = vzero<T>();
 #pragma unroll
   for (int i = QM - 1; i >= 0; --i) {
-    V3 f = F[i];
-    V3 n = Nm[i] + cross(mcom(M, i), F[i]);
+    W f = F[i];
+    W n = Nm[i] + cross(mcom<T>(M, i), F[i]);
     if (i < QM - 1) {
       const int a1 = M.axis[i + 1];
-      const V3 Rf = rot(a1, sq[i + 1], cq[i + 1], fc);
-      const V3 Rn = rot(a1, sq[i + 1], cq[i + 1], nc);
+      const W Rf = rot(a1, sq[i + 1], cq[i + 1], fc);
+      const W Rn = rot(a1, sq[i + 1], cq[i + 1], nc);
       f = f + Rf;
-      n = n + Rn + cross(v3(0.f, 0.f, M.L[i]), Rf);
+      n = n + Rn + cross(v3t<T>(T(0), T(0), T(M.L[i])), Rf);
     }
     tau[i] = comp(M.axis[i], n);
-    if (rec) {
-      rec[i].f = f;
-      rec[i].n = n;
+    if constexpr (std::is_same<T, float>::value) {
+      if (rec) {
+        rec[i].f = f;
+        rec[i].n = n;
+      }
     }
     fc = f;
     nc = n;
@@ -367,20 +400,25 @@ __device__ __forceinline__ bool forward_dynamics(const DevModel& M, const float*
   return ok;
 }
 
-// End-effector position and its 3x7 Jacobian (row-major) in base coordinates.
-__device__ __forceinline__ void fk_ee(const DevModel& M, const float* q, float* p, float* J) {
-  float R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};  // row-major, columns are the frame axes
-  V3 pos = vzero();
-  V3 pj[QM], ej[QM];
+// End-effector position and (float only, J non-null) its 3x7 Jacobian
+// (row-major) in base coordinates.
+template <typename T>
+__device__ __forceinline__ void fk_ee(const DevModel& M, const T* q, T* p, float* J) {
+  T R[9] = {T(1), T(0), T(0), T(0), T(1), T(0), T(0), T(0), T(1)};  // row-major, columns are the frame axes
+  Vec3<T> pos = vzero<T>();
+  Vec3<T> pj[QM], ej[QM];
 #pragma unroll
   for (int i = 0; i < QM; ++i) {
-    if (i > 0) pos = pos + M.L[i - 1] * v3(R[2], R[5], R[8]);
-    float s, c;
-    sincosf(q[i], &s, &c);
+    if (i > 0) pos = pos + T(M.L[i - 1]) * v3t<T>(R[2], R[5], R[8]);
+    T s, c;
+    if constexpr (std::is_same<T, float>::value)
+      sincosf(q[i], &s, &c);
+    else
+      sincos(q[i], &s, &c);
     const int a = M.axis[i];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-      const float c0 = R[3 * r], c1 = R[3 * r + 1], c2 = R[3 * r + 2];
+      const T c0 = R[3 * r], c1 = R[3 * r + 1], c2 = R[3 * r + 2];
       if (a == 2) {
         R[3 * r] = c * c0 + s * c1;
         R[3 * r + 1] = -s * c0 + c * c1;
@@ -393,21 +431,56 @@ __device__ __forceinline__ void fk_ee(const DevModel& M, const float* q, float* 
       }
     }
     pj[i] = pos;
-    ej[i] = v3(R[a], R[3 + a], R[6 + a]);
+    ej[i] = v3t<T>(R[a], R[3 + a], R[6 + a]);
   }
-  const V3 pe = pos + M.L[QM - 1] * v3(R[2], R[5], R[8]);
+  const Vec3<T> pe = pos + T(M.L[QM - 1]) * v3t<T>(R[2], R[5], R[8]);
   p[0] = pe.x;
   p[1] = pe.y;
   p[2] = pe.z;
-  if (J) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (J) {
 #pragma unroll
-    for (int i = 0; i < QM; ++i) {
-      const V3 col = cross(ej[i], pe - pj[i]);
-      J[i] = col.x;
-      J[QM + i] = col.y;
-      J[2 * QM + i] = col.z;
+      for (int i = 0; i < QM; ++i) {
+        const Vec3<T> col = cross(ej[i], pe - pj[i]);
+        J[i] = col.x;
+        J[QM + i] = col.y;
+        J[2 * QM + i] = col.z;
+      }
     }
   }
+}
+
+// Forward dynamics to FP64 accuracy, for the merit (Eq. 3) of line-search
+// trial points: qdd solves ID(q, qd, qdd) = u with the inverse dynamics
+// evaluated in FP64.  The FP32 factor of M only preconditions the fixed-point
+// iteration  qdd <- qdd + M^-1 (u - ID(q, qd, qdd))  (iterative refinement),
+// which contracts by about kappa(M) * 2^-24 per step: three steps from zero
+// reach FP64 accuracy for kappa(M) up to ~1e4.  Returns false if the FP32
+// factorisation failed.
+static __device__ __noinline__ bool forward_dynamics_f64(const DevModel& M, const float* q, const float* qd,
+                                            const float* u, double* qdd) {
+  float sqf[QM], cqf[QM], Ml[QM * (QM + 1) / 2];
+  double sq[QM], cq[QM], qdv[QM], tau[QM];
+#pragma unroll
+  for (int i = 0; i < QM; ++i) {
+    sincosf(q[i], &sqf[i], &cqf[i]);
+    sincos((double)q[i], &sq[i], &cq[i]);
+    qdv[i] = qd[i];
+    qdd[i] = 0.0;
+  }
+  mass_matrix_lower(M, sqf, cqf, Ml);
+  const bool ok = chol7(Ml);
+#pragma unroll 1
+  for (int pass = 0; pass < 3; ++pass) {
+    rnea_value<double>(M, sq, cq, qdv, qdd, (double)M.g, tau, nullptr);
+    float r[QM];
+#pragma unroll
+    for (int i = 0; i < QM; ++i) r[i] = (float)((double)u[i] - tau[i]);
+    chol7_solve(Ml, r);
+#pragma unroll
+    for (int i = 0; i < QM; ++i) qdd[i] += (double)r[i];
+  }
+  return ok;
 }
 
 }  // namespace gato

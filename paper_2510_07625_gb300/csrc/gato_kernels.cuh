@@ -88,6 +88,7 @@ __device__ void sqp_solve(Ctx& C, const ProbDesc& P, const Params& prm, int iter
     csync(C);  // defect c_k0 comes from the neighbour's last knot
     tstamp(C, T_JAC, tl);
     st_kkt_merit(C, prm.mu, rbuf);
+    if (it == 0) st_line_search(C, prm.mu, prm.beta, prm.n_alpha, rbuf, true);  // FP64 base merit
     tstamp(C, T_KKT, tl);
     kkt = C.scal[S_KKT];
     merit = C.scal[S_MERIT0];
@@ -159,7 +160,7 @@ __global__ void __launch_bounds__(NTHR, REG ? 1 : 2) sqp_fused(FusedLaunch a) {
   for (int i = threadIdx.x; i < (int)(sizeof(DevModel) / sizeof(float)); i += NTHR)
     sm[i] = reinterpret_cast<const float*>(a.models + P.model)[i];
   float* scal = sm + 96;
-  float* red = scal + 64;
+  float* red = scal + SCAL_FLOATS;
   float* xs = red + 2 * RED_SLOTS * RED_W;
   float* vb = xs + 16;
   const int kpc = kpc_for(a.nmax, csize);
@@ -198,7 +199,7 @@ __global__ void __launch_bounds__(NTHR, REG ? 1 : 2) sqp_fused(FusedLaunch a) {
       C.vk0r = C.k1 - 1;
     }
   }
-  if (threadIdx.x < 64) scal[threadIdx.x] = 0.f;
+  if (threadIdx.x < SCAL_FLOATS) scal[threadIdx.x] = 0.f;
   for (int i = threadIdx.x; i < 196; i += NTHR) zblock[i] = 0.f;
   __syncthreads();
   sqp_solve<REG>(C, P, a.prm, a.iters, a.results + b);
@@ -217,7 +218,7 @@ struct PlainArgs {
 };
 
 __global__ void __launch_bounds__(NTHR, 1) sqp_plain_stage(int stage, PlainArgs a) {
-  __shared__ float red[2 * RED_SLOTS * RED_W];
+  __shared__ __align__(16) float red[2 * RED_SLOTS * RED_W];
   __shared__ float zeros196[196];
   for (int i = threadIdx.x; i < 196; i += NTHR) zeros196[i] = 0.f;
   __syncthreads();
@@ -240,14 +241,14 @@ __global__ void __launch_bounds__(NTHR, 1) sqp_plain_stage(int stage, PlainArgs 
   C.vbl = C.vbr = nullptr;
   C.vk0l = C.vk0r = 0;
   C.scal = C.vb + NVEC * C.vstride;
-  C.xs = C.scal + 64;
+  C.xs = C.scal + SCAL_FLOATS;
   C.red = red;
   C.tm = nullptr;
   const Params& prm = a.prm;
   int* rflags = reinterpret_cast<int*>(C.scal + S_RFLAGS);
   int rbuf = 0;
   if (stage == PS_LOAD) {
-    if (rank == 0 && threadIdx.x < 64) C.scal[threadIdx.x] = 0.f;
+    if (rank == 0 && threadIdx.x < SCAL_FLOATS) C.scal[threadIdx.x] = 0.f;
     load_iterate(C, P);
     return;
   }
@@ -273,6 +274,7 @@ __global__ void __launch_bounds__(NTHR, 1) sqp_plain_stage(int stage, PlainArgs 
     case PS_JAC: st_dyn_jacobians(C); break;
     case PS_KKT: {
       st_kkt_merit(C, prm.mu, rbuf);
+      if (a.it == 0) st_line_search(C, prm.mu, prm.beta, prm.n_alpha, rbuf, true);  // FP64 base merit
       const bool bad = *reinterpret_cast<volatile int*>(C.scal + S_FLAGS) != 0;
       if (lead) {
         C.scal[S_MERITF] = C.scal[S_MERIT0];

@@ -30,7 +30,10 @@ EXPORTED = (
     "gato_sync", "gato_get_results", "gato_destroy_batch", "gato_status_string", "gato_last_error",
     "gato_last_transfer_bytes", "gato_debug_plain_stage", "gato_debug_layout", "gato_solve_noalloc",
     "gato_debug_stage_cycles", "gato_set_launch_config", "gato_autotune", "gato_graph_create",
-    "gato_graph_launch", "gato_graph_wait", "gato_graph_destroy",
+    "gato_graph_launch", "gato_graph_wait", "gato_graph_destroy", "gato_server_create",
+    "gato_server_open", "gato_server_submit", "gato_server_poll", "gato_server_read",
+    "gato_server_close", "gato_server_get_stats", "gato_server_last_error", "gato_server_destroy",
+    "gato_server_drive",
 )
 LAYOUT_NAMES = ("X", "U", "dX", "dU", "Fq", "Fv", "Minv", "qdd", "dTau", "Qinv", "Rinv", "q", "r",
                 "c", "Jk", "Linv", "links", "D", "L", "P", "vec", "scal", "Dx", "Du", "nu")
@@ -67,6 +70,27 @@ class LaunchConfig(C.Structure):
 class Result(C.Structure):
     _fields_ = [("flags", C.c_int32), ("sqp_iters", C.c_int32), ("pcg_iters", C.c_int32),
                 ("kkt_residual", C.c_float), ("merit", C.c_float)]
+
+
+class ServerDesc(C.Structure):
+    _fields_ = [("max_sessions", C.c_int32), ("max_horizon", C.c_int32), ("max_batch", C.c_int32),
+                ("max_inflight", C.c_int32), ("sqp_iters", C.c_int32), ("mem_budget_bytes", C.c_int64)]
+
+
+class Reply(C.Structure):
+    _fields_ = [("result", Result), ("u0", C.c_float * 7), ("x1", C.c_float * 14),
+                ("submit_ns", C.c_int64), ("done_ns", C.c_int64)]
+
+
+class DriveStats(C.Structure):
+    _fields_ = [("completed", C.c_int64), ("elapsed_s", C.c_double), ("launches", C.c_int64),
+                ("max_backlog", C.c_int64)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("capacity", C.c_int32), ("sessions_open", C.c_int32), ("max_batch", C.c_int32),
+                ("max_inflight", C.c_int32), ("submitted", C.c_int64), ("completed", C.c_int64),
+                ("launches", C.c_int64), ("pending", C.c_int64), ("reserved_bytes", C.c_int64)]
 
 
 _lib = None
@@ -126,6 +150,27 @@ def load() -> C.CDLL:
     L.gato_graph_wait.restype = C.c_int
     L.gato_graph_destroy.argtypes = [bp]
     L.gato_graph_destroy.restype = None
+    L.gato_server_create.argtypes = [C.POINTER(BatchDesc), C.POINTER(ServerDesc), C.POINTER(C.c_void_p)]
+    L.gato_server_create.restype = C.c_int
+    L.gato_server_open.argtypes = [bp, C.POINTER(Problem), C.POINTER(C.c_int32)]
+    L.gato_server_open.restype = C.c_int
+    L.gato_server_submit.argtypes = [bp, C.c_int32, C.c_void_p, C.c_int32, C.POINTER(C.c_int64)]
+    L.gato_server_submit.restype = C.c_int
+    L.gato_server_poll.argtypes = [bp, C.c_int64, C.c_int64, C.POINTER(Reply)]
+    L.gato_server_poll.restype = C.c_int
+    L.gato_server_read.argtypes = [bp, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
+    L.gato_server_read.restype = C.c_int
+    L.gato_server_close.argtypes = [bp, C.c_int32]
+    L.gato_server_close.restype = C.c_int
+    L.gato_server_get_stats.argtypes = [bp, C.POINTER(ServerStats)]
+    L.gato_server_get_stats.restype = C.c_int
+    L.gato_server_last_error.argtypes = [bp]
+    L.gato_server_last_error.restype = C.c_char_p
+    L.gato_server_destroy.argtypes = [bp]
+    L.gato_server_destroy.restype = None
+    L.gato_server_drive.argtypes = [bp, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_int64, C.c_void_p, C.POINTER(DriveStats)]
+    L.gato_server_drive.restype = C.c_int
     _lib = L
     return L
 
@@ -281,6 +326,88 @@ def gato_graph_wait(graph, results=None):
 
 def gato_graph_destroy(graph):
     load().gato_graph_destroy(C.c_void_p(graph))
+
+
+def _scheck(handle, s, what, ok=(GATO_OK,)):
+    if s not in ok:
+        msg = load().gato_server_last_error(C.c_void_p(handle)).decode()
+        raise GatoError(s, f"{what}: {gato_status_string(s)}: {msg}")
+    return s
+
+
+def gato_server_create(desc: BatchDesc, sdesc: ServerDesc) -> int:
+    h = C.c_void_p()
+    s = load().gato_server_create(C.byref(desc), C.byref(sdesc), C.byref(h))
+    if s != GATO_OK:
+        raise GatoError(s, f"gato_server_create: {gato_status_string(s)}")
+    return h.value
+
+
+def gato_server_open(handle, problem) -> int | None:
+    """Session id, or None when every slot is taken (GATO_E_BUSY)."""
+    sid = C.c_int32()
+    s = load().gato_server_open(C.c_void_p(handle), C.byref(problem), C.byref(sid))
+    if _scheck(handle, s, "gato_server_open", (GATO_OK, GATO_E_BUSY)) == GATO_E_BUSY:
+        return None
+    return sid.value
+
+
+def gato_server_submit(handle, session, x_s, shift=True) -> int | None:
+    """Ticket, or None when the session still has a request (GATO_E_BUSY)."""
+    xs = np.ascontiguousarray(x_s, np.float32)
+    t = C.c_int64()
+    s = load().gato_server_submit(C.c_void_p(handle), session, xs.ctypes.data, 1 if shift else 0, C.byref(t))
+    if _scheck(handle, s, "gato_server_submit", (GATO_OK, GATO_E_BUSY)) == GATO_E_BUSY:
+        return None
+    return t.value
+
+
+def gato_server_poll(handle, ticket, timeout_us=-1):
+    """The Reply, or None if not done within the timeout."""
+    r = Reply()
+    s = load().gato_server_poll(C.c_void_p(handle), ticket, timeout_us, C.byref(r))
+    if _scheck(handle, s, "gato_server_poll", (GATO_OK, GATO_E_TIMEOUT)) == GATO_E_TIMEOUT:
+        return None
+    return r
+
+
+def gato_server_read(handle, session, N, dof):
+    X = np.zeros((N + 1, 2 * dof), np.float32)
+    U = np.zeros((N, dof), np.float32)
+    lam = np.zeros((N + 1, 2 * dof), np.float32)
+    s = load().gato_server_read(C.c_void_p(handle), session, X.ctypes.data, U.ctypes.data, lam.ctypes.data)
+    _scheck(handle, s, "gato_server_read")
+    return X, U, lam
+
+
+def gato_server_close(handle, session):
+    _scheck(handle, load().gato_server_close(C.c_void_p(handle), session), "gato_server_close")
+
+
+def gato_server_get_stats(handle) -> dict:
+    st = ServerStats()
+    _scheck(handle, load().gato_server_get_stats(C.c_void_p(handle), C.byref(st)), "gato_server_get_stats")
+    return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+
+def gato_server_destroy(handle):
+    load().gato_server_destroy(C.c_void_p(handle))
+
+
+def gato_server_drive(handle, sessions, x_init, t_arrival, client, noise):
+    """Replays an arrival schedule; returns (latency_ms array, stats dict)."""
+    sess = np.ascontiguousarray(sessions, np.int32)
+    x0 = np.ascontiguousarray(x_init, np.float32).reshape(len(sess), 14)
+    t = np.ascontiguousarray(t_arrival, np.float64)
+    cl = np.ascontiguousarray(client, np.int32)
+    nz = np.ascontiguousarray(noise, np.float32).reshape(len(t), 14)
+    lat = np.zeros(len(t), np.float32)
+    st = DriveStats()
+    s = load().gato_server_drive(C.c_void_p(handle), sess.ctypes.data, len(sess), x0.ctypes.data,
+                                 t.ctypes.data, cl.ctypes.data, nz.ctypes.data, len(t), lat.ctypes.data,
+                                 C.byref(st))
+    _scheck(handle, s, "gato_server_drive")
+    return lat, {k: getattr(st, k) for k, _ in DriveStats._fields_}
 
 
 # ------------------------------------------------------------- conveniences
