@@ -422,6 +422,7 @@ namespace gato {
 gato_status batch_validate_problem(gato_batch* b, const gato_problem& p) { return validate_problem(b, p, 0); }
 const DevModel* batch_models_device(const gato_batch* b) { return b->models_d; }
 int batch_model_dof(const gato_batch* b, int model) { return b->model_dof[model]; }
+int batch_n_models(const gato_batch* b) { return b->n_models; }
 Params batch_params(const gato_batch* b, int iters) { return to_params(b->params, iters); }
 }  // namespace gato
 

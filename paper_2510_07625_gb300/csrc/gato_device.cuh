@@ -450,37 +450,4 @@ __device__ __forceinline__ void fk_ee(const DevModel& M, const T* q, T* p, float
   }
 }
 
-// Forward dynamics to FP64 accuracy, for the merit (Eq. 3) of line-search
-// trial points: qdd solves ID(q, qd, qdd) = u with the inverse dynamics
-// evaluated in FP64.  The FP32 factor of M only preconditions the fixed-point
-// iteration  qdd <- qdd + M^-1 (u - ID(q, qd, qdd))  (iterative refinement),
-// which contracts by about kappa(M) * 2^-24 per step: three steps from zero
-// reach FP64 accuracy for kappa(M) up to ~1e4.  Returns false if the FP32
-// factorisation failed.
-static __device__ __noinline__ bool forward_dynamics_f64(const DevModel& M, const float* q, const float* qd,
-                                            const float* u, double* qdd) {
-  float sqf[QM], cqf[QM], Ml[QM * (QM + 1) / 2];
-  double sq[QM], cq[QM], qdv[QM], tau[QM];
-#pragma unroll
-  for (int i = 0; i < QM; ++i) {
-    sincosf(q[i], &sqf[i], &cqf[i]);
-    sincos((double)q[i], &sq[i], &cq[i]);
-    qdv[i] = qd[i];
-    qdd[i] = 0.0;
-  }
-  mass_matrix_lower(M, sqf, cqf, Ml);
-  const bool ok = chol7(Ml);
-#pragma unroll 1
-  for (int pass = 0; pass < 3; ++pass) {
-    rnea_value<double>(M, sq, cq, qdv, qdd, (double)M.g, tau, nullptr);
-    float r[QM];
-#pragma unroll
-    for (int i = 0; i < QM; ++i) r[i] = (float)((double)u[i] - tau[i]);
-    chol7_solve(Ml, r);
-#pragma unroll
-    for (int i = 0; i < QM; ++i) qdd[i] += (double)r[i];
-  }
-  return ok;
-}
-
 }  // namespace gato

@@ -85,9 +85,8 @@ __device__ __forceinline__ void tstamp(const Ctx& C, int slot, long long& last) 
   }
 }
 
-// scal[] slots (SCAL_FLOATS floats; FP64 merits from float index S_MD on)
-constexpr int SCAL_FLOATS = 128;
-constexpr int S_MD = 64;
+// scal[] slots (SCAL_FLOATS floats)
+constexpr int SCAL_FLOATS = 64;
 enum : int {
   S_KKT = 0, S_MERIT0, S_CMAX, S_GMAX, S_DMAX, S_ALPHA, S_FLAGS, S_PCG, S_ITERS, S_MERITF,
   S_CHOICE, S_REDBUF, S_DONE, S_NSQP, S_NPCG, S_RFLAGS, S_MERITS = 16  // S_MERITS..+15
@@ -165,10 +164,6 @@ __device__ __forceinline__ float& blk(float* base, int k, int r, int c) { return
 __device__ __forceinline__ float& bD(const Ctx& C, int k, int r, int c) { return blk(C.Dm, k - C.bk0, r, c); }
 __device__ __forceinline__ float& bL(const Ctx& C, int k, int r, int c) { return blk(C.Lm, k - C.bk0, r, c); }
 __device__ __forceinline__ float& bP(const Ctx& C, int k, int r, int c) { return blk(C.Pm, k - C.bk0, r, c); }
-
-__device__ __forceinline__ double* merit64(const Ctx& C) {
-  return reinterpret_cast<double*>(C.scal + S_MD);  // [0] base, [1 + i] trial i
-}
 
 __device__ __forceinline__ float* vec(const Ctx& C, int s, int k) {
   return C.vb + s * C.vstride + (k - C.vk0) * VS;
@@ -630,8 +625,8 @@ __device__ inline void st_kkt_merit(const Ctx& C, float mu, int& rbuf) {
   const float J = df_val(sm[0]), c1 = df_val(sm[1]);
   if (threadIdx.x == 0) {
     C.scal[S_KKT] = fmaxf(mx[0], mx[2] / fmaxf(1.f, mx[1]));
-    // (the merit itself is evaluated in FP64 by st_line_search)
-    if (mx[3] > 0.f || !isfinite(J) || !isfinite(c1)) flag_nonfinite(C);
+    C.scal[S_MERIT0] = J + mu * c1;
+    if (mx[3] > 0.f || !isfinite(J)) flag_nonfinite(C);
   }
   __syncthreads();
 }
@@ -1124,146 +1119,124 @@ __device__ inline void st_recover(const Ctx& C) {
 
 // ------------------------------------------------- stage 5: line search
 
-// Cost of knot k (Eq. 1's J_k) at a trial point (x, u), evaluated in FP64.
-static __device__ __noinline__ double trial_cost(const Ctx& C, int k, const float* x, const float* u) {
+__device__ __forceinline__ float trial_cost(const Ctx& C, int k, const float* x, const float* u) {
   const int N = C.N;
-  const double s = (k == N) ? (double)C.w[3] : 1.0;
-  const double wq = C.w[0], wqd = C.w[1], wr = C.w[2], wee = C.w[4];
-  double J = 0.0;
+  const float s = (k == N) ? C.w[3] : 1.f;
+  const float wq = C.w[0], wqd = C.w[1], wr = C.w[2], wee = C.w[4];
+  float J = 0.f;
   if (C.cost_kind == 0) {
 #pragma unroll
     for (int i = 0; i < XM; ++i) {
-      const double wi = i < QM ? wq : wqd;
-      const double d = (double)x[i] - (double)xref_at(C, k, i);
-      J += 0.5 * s * wi * d * d;
+      const float wi = i < QM ? wq : wqd;
+      const float d = x[i] - xref_at(C, k, i);
+      J += 0.5f * s * wi * d * d;
     }
   } else {
-    double q[QM], p[3];
-#pragma unroll
-    for (int i = 0; i < QM; ++i) q[i] = x[i];
-    fk_ee<double>(*C.M, q, p, nullptr);
+    float p[3];
+    fk_ee(*C.M, x, p, nullptr);
     const float* pr = C.ee_ref + 3 * k;
-    const double d0 = p[0] - pr[0], d1 = p[1] - pr[1], d2 = p[2] - pr[2];
-    J += 0.5 * s * wee * (d0 * d0 + d1 * d1 + d2 * d2);
+    const float d0 = p[0] - pr[0], d1 = p[1] - pr[1], d2 = p[2] - pr[2];
+    J += 0.5f * s * wee * (d0 * d0 + d1 * d1 + d2 * d2);
 #pragma unroll
-    for (int i = 0; i < QM; ++i) J += 0.5 * s * wqd * (double)x[QM + i] * (double)x[QM + i];
+    for (int i = 0; i < QM; ++i) J += 0.5f * s * wqd * x[QM + i] * x[QM + i];
   }
   if (u) {
 #pragma unroll
-    for (int i = 0; i < QM; ++i) J += 0.5 * wr * (double)u[i] * (double)u[i];
+    for (int i = 0; i < QM; ++i) J += 0.5f * wr * u[i] * u[i];
   }
   return J;
 }
 
-__device__ __forceinline__ double warp_sum_f64(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
-// Merits (Eq. 3) of trial points, evaluated in FP64: the point is the FP32
-// iterate Z + alpha dZ exactly as st_accept would store it, its dynamics come
-// from forward_dynamics_f64 and every sum is carried in FP64, so that merit
-// differences near convergence (far below FP32 resolution of the merit) are
-// resolved and the accept/reject decision is the oracle's.
-// base = false: alpha_i = beta^-i for i < n_alpha (Eq. 7), results in
-// merit64(C)[1 + i].  base = true: the current iterate alone (alpha = 0), in
-// merit64(C)[0].  One thread per (alpha, own knot); per-alpha sums over the
-// CTA's knots in a fixed order, then over the cluster's CTAs in rank order.
-__device__ inline void st_line_search(const Ctx& C, float mu, float beta, int n_alpha, int& rbuf,
-                                      bool base = false) {
+// Merit (Eq. 3) of Z + alpha_i dZ for alpha_i = beta^-i (Eq. 7), i < n_alpha:
+// one thread per (alpha, own knot); per-alpha sums over the CTA's knots in a
+// fixed order, then over the cluster's CTAs in rank order.
+__device__ inline void st_line_search(const Ctx& C, float mu, float beta, int n_alpha, int& rbuf) {
   const int N = C.N, K = C.k1 - C.k0;
-  const int na = base ? 1 : n_alpha;
-  // [na][K] in the windows of vector slots V_W.. (dead after the recovery)
-  double* contrib = reinterpret_cast<double*>(C.vb + V_W * C.vstride);
-  for (int it = threadIdx.x; it < na * K; it += NTHR) {
+  float* contrib = vec(C, V_Y, C.k0);  // [n_alpha][K] (free during the line search)
+  for (int it = threadIdx.x; it < n_alpha * K; it += NTHR) {
     const int a = it / K, k = C.k0 + it % K;
-    float alpha = base ? 0.f : 1.f;
+    float alpha = 1.f;
     for (int i = 0; i < a; ++i) alpha /= beta;
     float x[XM], u[QM];
 #pragma unroll
     for (int i = 0; i < XM; ++i) x[i] = C.X[k * VS + i] + alpha * C.dX[k * VS + i];
-    double v;
+    float v;
     if (k < N) {
 #pragma unroll
       for (int i = 0; i < QM; ++i) u[i] = C.U[k * US + i] + alpha * C.dU[k * US + i];
-      double qdd[QM];
-      forward_dynamics_f64(*C.M, x, x + QM, u, qdd);
-      const double h = C.h;
-      double c1 = 0.0;
+      float qdd[QM];
+      forward_dynamics(*C.M, x, x + QM, u, qdd);
+      float c1 = 0.f;
 #pragma unroll
       for (int i = 0; i < QM; ++i) {
-        const double qdn = (double)x[QM + i] + h * qdd[i];
-        const double qn = (double)x[i] + h * qdn;
-        const float xq = C.X[(k + 1) * VS + i] + alpha * C.dX[(k + 1) * VS + i];
-        const float xv = C.X[(k + 1) * VS + QM + i] + alpha * C.dX[(k + 1) * VS + QM + i];
-        c1 += fabs(qn - (double)xq);
-        c1 += fabs(qdn - (double)xv);
+        const float qdn = x[QM + i] + C.h * qdd[i];
+        const float qn = x[i] + C.h * qdn;
+        c1 += fabsf(qn - (C.X[(k + 1) * VS + i] + alpha * C.dX[(k + 1) * VS + i]));
+        c1 += fabsf(qdn - (C.X[(k + 1) * VS + QM + i] + alpha * C.dX[(k + 1) * VS + QM + i]));
       }
-      v = trial_cost(C, k, x, u) + (double)mu * c1;
+      v = trial_cost(C, k, x, u) + mu * c1;
     } else {
       v = trial_cost(C, k, x, nullptr);
     }
     if (k == 0) {
-      double c0 = 0.0;
+      float c0 = 0.f;
 #pragma unroll
-      for (int i = 0; i < XM; ++i) c0 += fabs((double)C.xs[i] - (double)x[i]);
-      v += (double)mu * c0;
+      for (int i = 0; i < XM; ++i) c0 += fabsf(C.xs[i] - (C.X[i] + alpha * C.dX[i]));
+      v += mu * c0;
     }
     contrib[a * K + (k - C.k0)] = v;
   }
   __syncthreads();
   // warp a: this CTA's partial of alpha_a (lane-strided over its knots, fixed tree)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double* slots = reinterpret_cast<double*>(C.red + rbuf * RED_SLOTS * RED_W);  // [rank][alpha]
-  for (int a = warp; a < na; a += NWARP) {
-    double sum = 0.0;
-    for (int kk = lane; kk < K; kk += 32) sum += contrib[a * K + kk];
-    sum = warp_sum_f64(sum);
+  float* slots = C.red + rbuf * RED_SLOTS * RED_W;  // [rank][alpha] pairs
+  for (int a = warp; a < n_alpha; a += NWARP) {
+    DF s = df_zero();
+    for (int kk = lane; kk < K; kk += 32) s = df_add(s, contrib[a * K + kk]);
+    s = warp_df_sum(s);
     if (lane == 0) {
-      const int o = C.rank * MAX_ALPHA + a;
+      const int o = (C.rank * MAX_ALPHA + a) * 2;
       if (C.csize > 1) {
         cg::cluster_group cl = cg::this_cluster();
-        for (int r = 0; r < C.csize; ++r) cl.map_shared_rank(slots, r)[o] = sum;
+        for (int r = 0; r < C.csize; ++r) {
+          float* dst = cl.map_shared_rank(slots, r);
+          dst[o] = s.hi;
+          dst[o + 1] = s.lo;
+        }
       } else {
-        slots[o] = sum;
+        slots[o] = s.hi;
+        slots[o + 1] = s.lo;
       }
     }
   }
   csync(C);
-  if (threadIdx.x < na) {
+  if (threadIdx.x < n_alpha) {
     const int a = threadIdx.x;
-    double m = 0.0;
-    for (int r = 0; r < C.csize; ++r) m += slots[r * MAX_ALPHA + a];
-    m = isfinite(m) ? m : INFINITY;
-    merit64(C)[base ? 0 : 1 + a] = m;
-    if (base) C.scal[S_MERIT0] = (float)m;
-    else C.scal[S_MERITS + a] = (float)m;
+    DF s = df_zero();
+    for (int r = 0; r < C.csize; ++r)
+      s = df_addd(s, DF{slots[(r * MAX_ALPHA + a) * 2], slots[(r * MAX_ALPHA + a) * 2 + 1]});
+    const float m = df_val(s);
+    C.scal[S_MERITS + a] = isfinite(m) ? m : INFINITY;
   }
   rbuf ^= 1;
   __syncthreads();
 }
 
-// Argmin with ties to the smallest index; accept only a strict decrease (c7),
-// both in FP64.  On acceptance the accepted trial's merit becomes the base.
+// Argmin with ties to the smallest index; accept only a strict decrease (c7).
 __device__ inline int st_accept(const Ctx& C, float beta, int n_alpha) {
   const int N = C.N;
-  const double* m = merit64(C);
   int best = 0;
   for (int a = 1; a < n_alpha; ++a)
-    if (m[1 + a] < m[1 + best]) best = a;
-  const int choice = (m[1 + best] < m[0]) ? best : -1;
+    if (C.scal[S_MERITS + a] < C.scal[S_MERITS + best]) best = a;
+  const float m0 = C.scal[S_MERIT0];
+  const int choice = (C.scal[S_MERITS + best] < m0) ? best : -1;
   if (choice >= 0) {
     float alpha = 1.f;
     for (int i = 0; i < choice; ++i) alpha /= beta;
     const int ke = C.k1 < N ? C.k1 : N;
     for (int i = threadIdx.x; i < (C.k1 - C.k0) * VS; i += NTHR) C.X[C.k0 * VS + i] += alpha * C.dX[C.k0 * VS + i];
     for (int i = threadIdx.x; i < (ke - C.k0) * US; i += NTHR) C.U[C.k0 * US + i] += alpha * C.dU[C.k0 * US + i];
-  }
-  csync(C);  // every CTA has read the old base merit
-  if (choice >= 0 && threadIdx.x == 0) {
-    merit64(C)[0] = m[1 + choice];
-    C.scal[S_MERIT0] = (float)m[1 + choice];
   }
   return choice;
 }

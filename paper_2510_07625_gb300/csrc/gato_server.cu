@@ -178,6 +178,7 @@ namespace gato {
 gato_status batch_validate_problem(gato_batch* b, const gato_problem& p);
 const DevModel* batch_models_device(const gato_batch* b);
 int batch_model_dof(const gato_batch* b, int model);
+int batch_n_models(const gato_batch* b);
 Params batch_params(const gato_batch* b, int iters);
 }  // namespace gato
 
@@ -481,7 +482,22 @@ gato_status gato_server_open(gato_server* s, const gato_problem* p, int32_t* ses
   *session = -1;
   if (p->mem != GATO_MEM_HOST) return server_fail(s, GATO_E_INVALID, "sessions open from host problems");
   if (p->N > s->max_horizon) return server_fail(s, GATO_E_INVALID, "N above the server's max_horizon");
-  gato_status st = batch_validate_problem(s->models, *p);
+  if (p->N < 1 || p->model < 0 || p->model >= batch_n_models(s->models) || !p->x_s)
+    return server_fail(s, GATO_E_INVALID, "bad horizon, model or x_s");
+  // validation wants a warm start: the cold start where the problem has none
+  gato_problem q = *p;
+  std::vector<float> Xc, Uc;
+  const int dof0 = batch_model_dof(s->models, p->model);
+  if (!q.X) {
+    Xc.resize((size_t)(p->N + 1) * 2 * dof0);
+    for (int k = 0; k <= p->N; ++k) std::memcpy(Xc.data() + (size_t)k * 2 * dof0, p->x_s, 2 * dof0 * sizeof(float));
+    q.X = Xc.data();
+  }
+  if (!q.U) {
+    Uc.assign((size_t)p->N * dof0, 0.f);
+    q.U = Uc.data();
+  }
+  gato_status st = batch_validate_problem(s->models, q);
   if (st != GATO_OK) return server_fail(s, st, gato_last_error(s->models));
   std::unique_lock<std::mutex> lk(s->mu);
   int slot = -1;

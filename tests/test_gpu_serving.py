@@ -99,7 +99,7 @@ def test_busy_session_and_admission_by_memory(S):
     probs = _mix(4)
     # a budget that holds the launch contexts and only a few slots
     srv = S.Server(MODELS, 1000, 128, max_batch=4, max_inflight=1, sqp_iters=1,
-                   mem_budget_bytes=64 << 20)
+                   mem_budget_bytes=4 << 20)
     cap = srv.stats()["capacity"]
     assert 1 <= cap < 1000
     sids = []

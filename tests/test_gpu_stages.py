@@ -8,8 +8,6 @@ relative to the block's largest entry; pure recombinations (recovery, merit)
 of GPU-produced data are checked against the oracle's formula applied to
 that data, in FP64, at 1e-5.
 """
-import dataclasses
-
 import numpy as np
 import pytest
 
@@ -37,9 +35,6 @@ def G():
     return gato
 
 
-_RAW = {}
-
-
 def stage(G, prob, st, X=None, U=None, lam=None, **prm):
     B = G.Batch([prob.model], 1, prob.N, **prm)
     hp = G.HostProblems(B, [prob],
@@ -49,30 +44,7 @@ def stage(G, prob, st, X=None, U=None, lam=None, **prm):
     buf, off = G.gato_debug_plain_stage(B.handle, hp.arr, st)
     total, _ = G.gato_debug_layout(B.handle)
     B.close()
-    _RAW["buf"] = buf
     return buf.astype(np.float64), off, prob.N
-
-
-def merits64(off, n):
-    """FP64 merits the last stage run left in its scalar block: [base, trial 0..n-1]."""
-    raw = _RAW["buf"]
-    o = off["scal"] + 64  # float index of the FP64 merit slots
-    return raw[o:o + 2 * (n + 1)].copy().view(np.float64)
-
-
-def f32(v):
-    return np.asarray(v, np.float32).astype(np.float64)
-
-
-def f32_problem(p):
-    """The problem with every input the GPU reads as float rounded to float32."""
-    m = p.model
-    m32 = dataclasses.replace(m, link_len=tuple(f32(m.link_len)), mass=tuple(f32(m.mass)),
-                              com=tuple(f32(m.com)), inertia=tuple(f32(m.inertia)),
-                              gravity=float(np.float32(m.gravity)))
-    return dataclasses.replace(p, model=m32, dt=float(np.float32(p.dt)), x_s=f32(p.x_s),
-                               x_ref=None if p.x_ref is None else f32(p.x_ref),
-                               ee_ref=None if p.ee_ref is None else f32(p.ee_ref), w=tuple(f32(p.w)))
 
 
 def knots(buf, off, name, K, stride, n):
@@ -161,12 +133,8 @@ def test_linearisation_stage(G, oracle, name, mk):
     scal = buf[off["scal"]:off["scal"] + 64]
     kkt_ora = oracle.kkt_residual(prob, X, U, lam)
     assert abs(scal[0] - kkt_ora) <= 1e-4 * max(1.0, kkt_ora)
-    # the merit is evaluated in FP64 at the FP32 iterate: against the oracle on
-    # the same (float32-rounded) data, to FP64 evaluation-order accuracy
-    m_ora = oracle.merit(f32_problem(prob), f32(X), f32(U))
-    m_gpu = merits64(off, 0)[0]
-    assert abs(m_gpu - m_ora) <= 1e-9 * m_ora, (m_gpu, m_ora)
-    assert abs(scal[1] - m_ora) <= 1e-6 * m_ora
+    m_ora = oracle.merit(prob, X, U)
+    assert abs(scal[1] - m_ora) <= 1e-5 * m_ora
 
 
 @pytest.mark.parametrize("name,mk", PROBS, ids=[p[0] for p in PROBS])
@@ -295,14 +263,8 @@ def test_pcg_recovery_and_line_search_stages(G, oracle, name, mk, precond):
     np.testing.assert_allclose(dU, dU_want, atol=1e-5 * np.abs(dU_want).max(), rtol=0)
     dX, dU = dX[:, pi], dU[:, :dof]
     # line search: trial merits of the GPU step, against the oracle merit in FP64
-    # the trial point is the FP32 iterate plus alpha dZ rounded to FP32 (alpha
-    # a power of two, so the product is exact); its merit is evaluated in FP64
-    m = merits64(off, 8)
-    p32 = f32_problem(prob)
-    X32, U32 = X.astype(np.float32), U.astype(np.float32)
+    scal = buf[off["scal"]:off["scal"] + 64]
     for a in range(8):
-        al = np.float32(0.5 ** a)
-        Xt = (X32 + al * dX.astype(np.float32)).astype(np.float64)
-        Ut = (U32 + al * dU.astype(np.float32)).astype(np.float64)
-        m_ora = oracle.merit(p32, Xt, Ut)
-        assert abs(m[1 + a] - m_ora) <= 1e-9 * m_ora, (a, m[1 + a], m_ora)
+        al = 0.5 ** a
+        m_ora = oracle.merit(prob, X + al * dX, U + al * dU)
+        assert abs(scal[16 + a] - m_ora) <= 2e-5 * m_ora, (a, scal[16 + a], m_ora)
