@@ -246,6 +246,7 @@ def test_pcg_recovery_and_line_search_stages(G, oracle, name, mk, precond):
     I7 = np.eye(7)
     dX_want = np.zeros((K, XM))
     dU_want = np.zeros((N, 7))
+    cancel = 0.0
     for k in range(K):
         t = Dx[k] + nup[k]
         if k < N:
@@ -253,6 +254,8 @@ def test_pcg_recovery_and_line_search_stages(G, oracle, name, mk, precond):
             Bm = np.vstack([h * h * Mi[k], h * Mi[k]])
             t = t - A.T @ nup[k + 1]
             dU_want[k] = -Ri[k] * (Du[k] - Bm.T @ nup[k + 1])
+            # FP32 rounding of the two terms before R^-1 (= 1e3) scales them up
+            cancel = max(cancel, np.abs(Ri[k]).max() * max(np.abs(Du[k]).max(), np.abs(Bm.T @ nup[k + 1]).max()))
         Qf = np.zeros((14, 14))
         Qf[:7, :7] = Qi[k, :49].reshape(7, 7)
         Qf[7:, 7:] = np.diag(Qi[k, 49:])
@@ -260,7 +263,7 @@ def test_pcg_recovery_and_line_search_stages(G, oracle, name, mk, precond):
     dX = knots(buf, off, "dX", K, VS, XM)
     dU = knots(buf, off, "dU", N, US, 7)
     np.testing.assert_allclose(dX, dX_want, atol=1e-5 * np.abs(dX_want).max(), rtol=0)
-    np.testing.assert_allclose(dU, dU_want, atol=1e-5 * np.abs(dU_want).max(), rtol=0)
+    np.testing.assert_allclose(dU, dU_want, atol=1e-5 * np.abs(dU_want).max() + 8 * 6e-8 * cancel, rtol=0)
     dX, dU = dX[:, pi], dU[:, :dof]
     # line search: trial merits of the GPU step, against the oracle merit in FP64
     scal = buf[off["scal"]:off["scal"] + 64]
