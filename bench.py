@@ -44,6 +44,29 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_seed0(rank, B):
+    """First problem seed of a rank: replicas solve disjoint seeded batches
+    (weak scaling, no data-path collective)."""
+    return rank * B
+
+
+def max_over_ranks(t, device):
+    """The largest of the ranks' timed seconds (barrier implied by the
+    all-reduce); t itself on a single process."""
+    import torch
+
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return t
+    tt = torch.tensor([t], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_rate(ws, solves_per_rank, steps, t_max):
+    """Solves per second of the whole job: every rank's solves over the slowest rank's time."""
+    return ws * solves_per_rank * steps / t_max
+
+
 # --------------------------------------------------------------- FLOP model
 
 def flops_per_solve(N, sqp_iters, pcg_iters, n_alpha=8, ee=True):
@@ -137,7 +160,7 @@ def run_gpu(args):
 
     build.build_library()
     stream = torch.cuda.current_stream()
-    probs = I.config_sweep(B_MAIN, N_MAIN)
+    probs = I.config_sweep(B_MAIN, N_MAIN, seed0=rank_seed0(rank, B_MAIN))
     B = gato.Batch([I.arm7()], B_MAIN, N_MAIN, stream=stream.cuda_stream)
     dp = gato.DeviceProblems(B, probs)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -178,12 +201,8 @@ def run_gpu(args):
     pcg = sum(res[i].pcg_iters for i in range(dp.n))
     sqp = sum(res[i].sqp_iters for i in range(dp.n))
     t_sum = sum(times)
-    t_max = t_sum
-    if ws > 1:
-        tt = torch.tensor([t_sum], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = ws * B_MAIN * args.steps / t_max
+    t_max = max_over_ranks(t_sum, "cuda")
+    value = whole_job_rate(ws, B_MAIN, args.steps, t_max)
     ms_per_step = 1e3 * t_max / args.steps
     flops = sum(flops_per_solve(N_MAIN, res[i].sqp_iters, res[i].pcg_iters) for i in range(dp.n))
     clocks = clk.summary()
@@ -226,9 +245,11 @@ def run_gpu(args):
     return out
 
 
-# DRAM bytes per launch of the dominant kernel on this workload, from the ncu
-# capture summarised in profiles/ (None when the kernel changed since).
-TRAFFIC_BYTES = None
+# DRAM bytes per launch of the dominant kernel on this workload (latency form,
+# 35 knots per CTA), from the ncu capture summarised in
+# profiles/sqp_fused_b256_n64_metrics.md: 17,885,952 read + 14,358,528 written.
+# Set to None when the kernel changes until it is measured again.
+TRAFFIC_BYTES = 32244480
 
 
 def latency_runs(gato, I, torch, stream, flush, n_calls=200, launch_cfg=False):
@@ -411,13 +432,39 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def one_launch(B_n, N):
+    """Profiling case: two warm-up solves and one solve of B_n figure-eight
+    problems (horizon N, 10 SQP iterations) in the latency form with 35 knots
+    per CTA; profile the third launch (ncu -k regex:sqp_fused -s 2 -c 1)."""
+    import torch
+    from paper_2510_07625_gb300 import build, gato, inputs as I
+
+    build.build_library()
+    probs = I.config_sweep(B_n, N)
+    B = gato.Batch([I.arm7()], B_n, N)
+    B.set_launch_config(1, 0, 0)
+    dp = gato.DeviceProblems(B, probs)
+    for _ in range(3):
+        dp.reset()
+        res = B.solve(dp.arr, dp.n, ITERS)
+    torch.cuda.synchronize()
+    print(json.dumps({"one_launch": {"B": B_n, "N": N, "pcg_iters": sum(res[i].pcg_iters for i in range(dp.n)),
+                                     "sqp_iters": sum(res[i].sqp_iters for i in range(dp.n))}}))
+    B.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gato", choices=["gato", "reference"])
+    ap.add_argument("--one-launch", nargs=2, type=int, metavar=("B", "N"),
+                    help="profiling case: 3 launches of B solves of horizon N, no measurement")
     args = ap.parse_args()
+    if args.one_launch:
+        one_launch(*args.one_launch)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

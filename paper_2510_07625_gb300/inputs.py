@@ -197,9 +197,9 @@ def config_fixed_batch(B: int = 32, N: int = 32) -> list[Problem]:
     return [joint_problem(b, arm7(), N, 0.01) for b in range(B)]
 
 
-def config_sweep(B: int, N: int) -> list[Problem]:
-    """B figure-eight solves with seeds 0..B-1, 7-DoF, horizon N, dt=0.01."""
-    return [ee_problem(b, arm7(), N, 0.01) for b in range(B)]
+def config_sweep(B: int, N: int, seed0: int = 0) -> list[Problem]:
+    """B figure-eight solves with seeds seed0..seed0+B-1, 7-DoF, horizon N, dt=0.01."""
+    return [ee_problem(seed0 + b, arm7(), N, 0.01) for b in range(B)]
 
 
 def uneven_horizon(seed: int) -> int:
