@@ -247,9 +247,9 @@ def run_gpu(args):
 
 # DRAM bytes per launch of the dominant kernel on this workload (latency form,
 # 35 knots per CTA), from the ncu capture summarised in
-# profiles/sqp_fused_b256_n64_metrics.md: 17,885,952 read + 14,358,528 written.
+# profiles/sqp_fused_b256_n64_metrics.md: 17,825,024 read + 9,144,320 written.
 # Set to None when the kernel changes until it is measured again.
-TRAFFIC_BYTES = 32244480
+TRAFFIC_BYTES = 26969344
 
 
 def latency_runs(gato, I, torch, stream, flush, n_calls=200, launch_cfg=False):
@@ -453,6 +453,42 @@ def one_launch(B_n, N):
     B.close()
 
 
+def sweep(Bs=(1, 16, 32, 64, 128, 256), Ns=(32, 64, 128), iters=ITERS, reps=5):
+    """The batch/horizon sweep (figure-eight EE, 10 SQP iterations): for every
+    (B, N) the autotuner picks the launch configuration, then the median of
+    `reps` timed calls (CUDA events, cold start each) gives solves/s; the
+    plain form is timed at B = 1 for reference.  One JSON line per point."""
+    import torch
+    from paper_2510_07625_gb300 import build, gato, inputs as I
+
+    build.build_library()
+    stream = torch.cuda.current_stream()
+    for N in Ns:
+        for Bn in Bs:
+            probs = I.config_sweep(Bn, N)
+            B = gato.Batch([I.arm7()], Bn, N, stream=stream.cuda_stream)
+            dp = gato.DeviceProblems(B, probs)
+            cfg, _ = B.autotune(dp.arr, dp.n, iters, reps=1)
+            ts = []
+            for rep in range(reps + 1):
+                dp.reset()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                gato.gato_solve(B.handle, dp.arr, dp.n, iters, None)
+                e1.record(stream)
+                B.sync()
+                if rep:
+                    ts.append(e0.elapsed_time(e1))
+            t = statistics.median(ts)
+            res = gato.gato_get_results(B.handle, dp.n)
+            print(json.dumps({"sweep": {"B": Bn, "N": N, "ms": round(t, 4), "solves_per_s": round(Bn / (t / 1e3), 1),
+                                        "launch": cfg,
+                                        "pcg_per_solve": round(sum(res[i].pcg_iters for i in range(dp.n)) / Bn, 1)}}),
+                  flush=True)
+            B.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -461,7 +497,11 @@ def main():
     ap.add_argument("--impl", default="gato", choices=["gato", "reference"])
     ap.add_argument("--one-launch", nargs=2, type=int, metavar=("B", "N"),
                     help="profiling case: 3 launches of B solves of horizon N, no measurement")
+    ap.add_argument("--sweep", action="store_true", help="batch/horizon sweep with the autotuner (one line per point)")
     args = ap.parse_args()
+    if args.sweep:
+        sweep()
+        return
     if args.one_launch:
         one_launch(*args.one_launch)
         return

@@ -727,68 +727,54 @@ __device__ inline void st_schur(const Ctx& C) {
   }
 }
 
-// D_k^-1 by Cholesky: the 7 lanes of a knot factor D_k in place in Pm, invert
-// the factor column by column into Li, and form L^-T L^-1.
+// D_k^-1 by in-place Gauss-Jordan elimination without pivoting: D_k is
+// symmetric positive definite, so every pivot is a positive diagonal of a
+// Schur complement of D_k.  The 7 lanes of a knot hold rows j and j+7 in
+// registers; at step c the owner of row c broadcasts it by shuffles, every
+// lane eliminates column c from its rows and row c becomes the scaled pivot
+// row, so after 14 steps the registers hold D_k^-1.  A non-positive or
+// non-finite pivot flags the solve.
 __device__ inline void st_block_inverse(const Ctx& C) {
   bool bad = false;
   OWN_KNOT(C);
-  float* Li = C.Li + (act ? k : 0) * LIS;
-  if (act)
-    for (int t = 0; t < 2; ++t) {
-      const int i = j + QM * t;
-      for (int c = 0; c < XM; ++c) bP(C, k, i, c) = bD(C, k, i, c);
-    }
-  __syncwarp();
+  const int lane = threadIdx.x & 31;
+  const int base = lane - j;  // first lane of this knot's group
+  float a0[XM], a1[XM];       // rows j and j+7
+#pragma unroll
   for (int c = 0; c < XM; ++c) {
-    if (act && (c % QM) == j) {
-      const float d2 = bP(C, k, c, c);
-      bad = bad || !(d2 > 0.f);
-      bP(C, k, c, c) = sqrtf(fmaxf(d2, 1e-30f));
-    }
-    __syncwarp();
-    if (act) {
-      const float d = bP(C, k, c, c);
-      for (int t = 0; t < 2; ++t) {
-        const int i = j + QM * t;
-        if (i > c) bP(C, k, i, c) = bP(C, k, i, c) / d;
-      }
-    }
-    __syncwarp();
-    if (act) {
-      for (int t = 0; t < 2; ++t) {
-        const int i = j + QM * t;
-        if (i > c) {
-          const float lic = bP(C, k, i, c);
-          for (int l = c + 1; l <= i; ++l) bP(C, k, i, l) -= lic * bP(C, k, l, c);
-        }
-      }
-    }
-    __syncwarp();
+    a0[c] = act ? bD(C, k, j, c) : (c == j ? 1.f : 0.f);
+    a1[c] = act ? bD(C, k, j + QM, c) : (c == j + QM ? 1.f : 0.f);
   }
-  // columns j and j+7 of L^-1 (lower triangular, column-major in Li)
-  if (act)
-    for (int t = 0; t < 2; ++t) {
-      const int cc = j + QM * t;
-      for (int i = 0; i < cc; ++i) Li[cc * XM + i] = 0.f;
-      Li[cc * XM + cc] = 1.f / bP(C, k, cc, cc);
-      for (int i = cc + 1; i < XM; ++i) {
-        float s = 0.f;
-        for (int l = cc; l < i; ++l) s += bP(C, k, i, l) * Li[cc * XM + l];
-        Li[cc * XM + i] = -s / bP(C, k, i, i);
-      }
+#pragma unroll
+  for (int c = 0; c < XM; ++c) {
+    const int owner = (base + (c % QM)) & 31;
+    float pr[XM];
+#pragma unroll
+    for (int l = 0; l < XM; ++l) pr[l] = __shfl_sync(0xffffffffu, c < QM ? a0[l] : a1[l], owner);
+    const float piv = pr[c];
+    bad = bad || !(piv > 0.f) || !isfinite(piv);
+    const float inv = 1.f / piv;
+    const bool p0 = (j == c), p1 = (j + QM == c);  // this lane holds the pivot row
+    const float f0 = a0[c], f1 = a1[c];
+#pragma unroll
+    for (int l = 0; l < XM; ++l) {
+      if (l == c) continue;
+      const float pl = pr[l] * inv;
+      a0[l] = p0 ? pl : a0[l] - f0 * pl;
+      a1[l] = p1 ? pl : a1[l] - f1 * pl;
     }
-  __syncwarp();
-  if (act)
-    for (int t = 0; t < 2; ++t) {
-      const int i = j + QM * t;
-      for (int c = 0; c < XM; ++c) {
-        float s = 0.f;
-        for (int l = (i > c ? i : c); l < XM; ++l) s += Li[i * XM + l] * Li[c * XM + l];
-        bP(C, k, i, c) = s;
-      }
+    a0[c] = p0 ? inv : -f0 * inv;
+    a1[c] = p1 ? inv : -f1 * inv;
+  }
+  if (act) {
+#pragma unroll
+    for (int c = 0; c < XM; ++c) {
+      bP(C, k, j, c) = a0[c];
+      bP(C, k, j + QM, c) = a1[c];
     }
+    if (bad) flag_nonfinite(C);
+  }
   __syncwarp();
-  if (bad) flag_nonfinite(C);
 }
 
 // ------------------------------------------------------------ stage 3: PCG
