@@ -133,7 +133,7 @@ gato_status gato_create_batch(const gato_batch_desc* desc, void* cuda_stream, ga
 
 /* Runs up to max_sqp_iters SQP iterations (Alg. 1, repeated) for n solves in
  * persistent fused launches: each solve is one thread-block cluster of
- * ceil((N+1)/35) CTAs or more (gato_launch_config), one launch per cluster
+ * ceil((N+1)/33) CTAs or more (gato_launch_config), one launch per cluster
  * size, the launches running concurrently, longest horizon first.  Host
  * problems are staged through pinned memory; device problems are used in place.
  * Asynchronous on the batch stream; if `results` is non-NULL the call waits and
@@ -181,7 +181,7 @@ gato_status gato_solve_noalloc(const gato_model_desc* models, int32_t n_models,
  * How solves map onto the GPU.  variant: 0 automatic, 1 the latency form (the
  * PCG's block rows held in registers, one CTA per SM), 2 the throughput form
  * (off-diagonal rows read from shared memory, two CTAs per SM).
- * knots_per_cta: 0 = 35 (the most one CTA holds), 2..35 spreads each solve
+ * knots_per_cta: 0 = 33 (the most one CTA holds), 2..33 spreads each solve
  * over more CTAs.  cluster: 0 = per solve, 1..8 = every solve uses this many
  * CTAs where its horizon allows (a uniform batch is then a single launch).
  * A cluster never exceeds 8 CTAs nor holds a CTA with fewer than 2 knots
@@ -197,7 +197,7 @@ typedef struct {
 gato_status gato_set_launch_config(gato_batch* b, const gato_launch_config* cfg);
 
 /* Times every candidate configuration (both variants x knots per CTA
- * {35, 24, 17, 12, 9, 6} x uniform clusters, skipping duplicates and
+ * {33, 24, 17, 12, 9, 6} x uniform clusters, skipping duplicates and
  * throughput forms whose shared memory does not fit two CTAs per SM) on these
  * problems for max_sqp_iters iterations, `reps` timed runs each after one
  * warm-up, every run from the problems' current iterate (X, U, lambda are

@@ -628,7 +628,7 @@ int64_t gato_debug_layout(const gato_batch* b, int64_t* o) {
   const WsLayout& L = b->plain_layout;
   const size_t K = b->max_horizon + 1;
   const size_t v[25] = {L.X,  L.U,  L.dX, L.dU, L.Fq, L.Fv, L.Mi, L.qdd, L.dT, L.Qi, L.Ri, L.qg, L.rg,
-                        L.cv, L.Jk, L.Li, L.LV, L.Dm, L.Lm, L.Pm, L.vec, L.vec + NVEC * (K + 2) * VS,
+                        L.cv, L.Jk, L.Li, L.LV, L.Dm, L.Lm, L.Pm, L.vec, L.vec + NVEC * (K + 2) * VW,
                         L.Dx, L.Du, L.nu};
   for (int i = 0; i < 25; ++i) o[i] = (int64_t)v[i];
   return (int64_t)L.total;

@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(NTHR, REG ? 1 : 2) sqp_fused(FusedLaunch a) {
   float* xs = red + 2 * RED_SLOTS * RED_W;
   float* vb = xs + 16;
   const int kpc = kpc_for(a.nmax, csize);
-  const int vstride = (kpc + 2) * VS;
+  const int vstride = (kpc + 2) * VW;
   float* blocks = vb + NVEC * vstride;
   float* zblock = blocks + (3 * kpc + 1) * BS;  // 196 zeros (L_{N+1})
   float* ws = a.ws + (size_t)b * a.ws_stride;
@@ -174,7 +174,11 @@ __global__ void __launch_bounds__(NTHR, REG ? 1 : 2) sqp_fused(FusedLaunch a) {
   C.xs = xs;
   C.red = red;
   C.scal = scal;
-  C.tm = a.timing ? a.timing + (size_t)b * T_COUNT : nullptr;
+  // stage counters accumulate in shared memory (thread 0 of rank 0) and are
+  // added to the solve's global counters once at the end
+  __shared__ long long tm_sh[T_COUNT];
+  if (threadIdx.x < T_COUNT) tm_sh[threadIdx.x] = 0;
+  C.tm = a.timing ? tm_sh : nullptr;
   C.Dm = blocks;
   C.Lm = blocks + kpc * BS;
   C.Pm = blocks + (2 * kpc + 1) * BS;
@@ -202,6 +206,10 @@ __global__ void __launch_bounds__(NTHR, REG ? 1 : 2) sqp_fused(FusedLaunch a) {
   for (int i = threadIdx.x; i < 196; i += NTHR) zblock[i] = 0.f;
   __syncthreads();
   sqp_solve<REG>(C, P, a.prm, a.iters, a.results + b);
+  if (a.timing) {
+    __syncthreads();
+    if (rank == 0 && threadIdx.x < T_COUNT) a.timing[(size_t)b * T_COUNT + threadIdx.x] += tm_sh[threadIdx.x];
+  }
 }
 
 // ----------------------------------------------------------------- plain form
@@ -235,7 +243,7 @@ __global__ void __launch_bounds__(NTHR, 1) sqp_plain_stage(int stage, PlainArgs 
   C.bk0 = 0;
   C.Lz = zeros196;
   C.vb = a.ws + a.layout.vec;
-  C.vstride = (int)((K + 2) * VS);
+  C.vstride = (int)((K + 2) * VW);
   C.vk0 = -1;
   C.vbl = C.vbr = nullptr;
   C.vk0l = C.vk0r = 0;

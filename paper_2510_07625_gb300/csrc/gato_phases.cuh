@@ -30,12 +30,16 @@ namespace cg = cooperative_groups;
 
 constexpr int NWARP = 9;             // warps per CTA
 constexpr int NTHR = 32 * NWARP;     // threads per CTA
-constexpr int KPC_MAX = 4 * NWARP - 1;  // knots per CTA (one slot spare for L_{k1})
+constexpr int KPC_MAX = 4 * (NWARP - 1) + 1;  // knots per CTA: 33 (the PCG runs them on 8 warps)
 constexpr int NVEC = 9;              // vector slots
 constexpr int RED_SLOTS = 8 * NWARP; // per-warp partial slots (up to 8 CTAs)
 constexpr int RED_W = 8;             // floats per slot
 
 enum : int { V_RR = 0, V_P0, V_P1, V_Q, V_Y, V_W, V_Z, V_RHS, V_DNU };
+// Knot stride of the vector windows: 18 floats, so that the four knots a warp
+// reads with one instruction fall in four different shared-memory banks
+// (with 16 the first and third knot collide).
+constexpr int VW = 18;
 
 struct Ctx {
   int N, dof, cost_kind;
@@ -56,7 +60,7 @@ struct Ctx {
   float *Dm, *Lm, *Pm;
   int bk0;
   const float* Lz;  // a 14x14 block of zeros (stands for L_{N+1})
-  // vectors: slot s of knot k at vb + s * vstride + (k - vk0) * VS
+  // vectors: slot s of knot k at vb + s * vstride + (k - vk0) * VW
   float* vb;
   int vstride, vk0;
   float* vbl;  // left neighbour's window (distributed shared memory) or null
@@ -136,7 +140,7 @@ __host__ __device__ inline WsLayout ws_layout(int Nmax, bool global_blocks, bool
     L.Dm = L.Lm = L.Pm = 0;
   }
   if (global_vecs) {
-    L.vec = o; o += align32(NVEC * (K + 2) * VS + SCAL_FLOATS + 16);
+    L.vec = o; o += align32(NVEC * (K + 2) * VW + SCAL_FLOATS + 16);
   } else {
     L.vec = 0;
   }
@@ -147,7 +151,7 @@ __host__ __device__ inline WsLayout ws_layout(int Nmax, bool global_blocks, bool
 // Shared-memory floats of one fused CTA owning at most `kpc` knots.
 __host__ __device__ inline size_t smem_floats(int kpc) {
   size_t f = 96 /*model*/ + SCAL_FLOATS + 2 * RED_SLOTS * RED_W + 16 /*xs*/;
-  f += NVEC * (size_t)(kpc + 2) * VS;
+  f += NVEC * (size_t)(kpc + 2) * VW;
   f += (size_t)(3 * kpc + 1) * BS + 196;  // blocks + a zero block
   return align32(f);
 }
@@ -166,19 +170,19 @@ __device__ __forceinline__ float& bL(const Ctx& C, int k, int r, int c) { return
 __device__ __forceinline__ float& bP(const Ctx& C, int k, int r, int c) { return blk(C.Pm, k - C.bk0, r, c); }
 
 __device__ __forceinline__ float* vec(const Ctx& C, int s, int k) {
-  return C.vb + s * C.vstride + (k - C.vk0) * VS;
+  return C.vb + s * C.vstride + (k - C.vk0) * VW;
 }
 
 // After the owner of knot k wrote rows j, j+7 of slot s, copy them into the
 // halo of the neighbour CTA that reads knot k.
 __device__ __forceinline__ void push_rows(const Ctx& C, int s, int k, int j, float v0, float v1) {
   if (C.vbl && k == C.k0) {
-    float* d = C.vbl + s * C.vstride + (k - C.vk0l) * VS;
+    float* d = C.vbl + s * C.vstride + (k - C.vk0l) * VW;
     d[j] = v0;
     d[j + QM] = v1;
   }
   if (C.vbr && k == C.k1 - 1) {
-    float* d = C.vbr + s * C.vstride + (k - C.vk0r) * VS;
+    float* d = C.vbr + s * C.vstride + (k - C.vk0r) * VW;
     d[j] = v0;
     d[j + QM] = v1;
   }
@@ -862,13 +866,18 @@ __device__ __forceinline__ void cluster_df_sum2(float* red, int rank, int csize,
     __syncthreads();
   a = df_zero();
   b = df_zero();
-  for (int i = lane; i < csize * NWARP; i += 32) {
-    const float4 v = *reinterpret_cast<const float4*>(red + (buf * RED_SLOTS + i) * RED_W);
+  const int ns = csize * NWARP;
+  for (int i0 = 0; i0 < ns; i0 += 32) {
+    const int i = i0 + lane;
+    const float4 v = i < ns ? *reinterpret_cast<const float4*>(red + (buf * RED_SLOTS + i) * RED_W)
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
     a = df_addd(a, DF{v.x, v.y});
     b = df_addd(b, DF{v.z, v.w});
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
+  // a butterfly just wide enough for the ns partials (the same for every warp
+  // and CTA), then every lane copies the total from the first group
+  const int top = ns > 16 ? 16 : (ns > 8 ? 8 : 4);
+  for (int o = top; o > 0; o >>= 1) {
     DF ya, yb;
     ya.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
     ya.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
@@ -876,6 +885,13 @@ __device__ __forceinline__ void cluster_df_sum2(float* red, int rank, int csize,
     yb.lo = __shfl_xor_sync(0xffffffffu, b.lo, o);
     a = df_addd(a, ya);
     b = df_addd(b, yb);
+  }
+  if (top < 16) {
+    const int src = lane & (2 * top - 1);
+    a.hi = __shfl_sync(0xffffffffu, a.hi, src);
+    a.lo = __shfl_sync(0xffffffffu, a.lo, src);
+    b.hi = __shfl_sync(0xffffffffu, b.hi, src);
+    b.lo = __shfl_sync(0xffffffffu, b.lo, src);
   }
   buf ^= 1;
 }
@@ -898,7 +914,19 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
   const bool stair = (precond == 0);
   *hit_max = false;
   long long tlast = C.tm ? clock64() : 0;
-  OWN_KNOT(C);
+  // PCG lane map: warps 0-7 carry 4 knots each on lanes 0-27; knot slot 32
+  // uses the spare lanes 28-31 of warp 0 (rows 0-3) and 28-30 of warp 1
+  // (rows 4-6).  The last warp does no PCG arithmetic, only barriers and
+  // reductions, so no SM sub-partition issues for three working warps.
+  const int lane_ = threadIdx.x & 31, warp_ = threadIdx.x >> 5;
+  const bool pwarp = warp_ < NWARP - 1;
+  const bool spare = lane_ >= 28;
+  const bool lane_ok = pwarp && (!spare || warp_ == 0 || (warp_ == 1 && lane_ < 31));
+  // rows j, j+7 with j in 0..6 for every lane (idle lanes use row 0), so that
+  // all block and vector addresses stay inside their 14x14 blocks and rows
+  const int j = !lane_ok ? 0 : (spare ? lane_ - 28 + (warp_ == 1 ? 4 : 0) : lane_ - 7 * (lane_ / 7));
+  const int k = C.k0 + (spare ? 32 : 4 * warp_ + lane_ / 7);
+  const bool act = lane_ok && k < C.k1;
   RowRegs<REG> R;
   R.load(C, k, j, act);
   // zero every vector slot of the window (halos at the ends stay zero)
@@ -914,8 +942,8 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
 #define SLOT(s) (wb + (s) * vstr)
   // neighbour window of this knot's rows (slot s at pb + s * vstr), boundary knots only
   float* pb = nullptr;
-  if (act && C.vbl && k == C.k0) pb = C.vbl + (k - C.vk0l) * VS;
-  if (act && C.vbr && k == C.k1 - 1) pb = C.vbr + (k - C.vk0r) * VS;
+  if (act && C.vbl && k == C.k0) pb = C.vbl + (k - C.vk0l) * VW;
+  if (act && C.vbr && k == C.k1 - 1) pb = C.vbr + (k - C.vk0r) * VW;
 #define PUSH(s, a, b)                     \
   if (pb) {                               \
     pb[(s) * vstr + J] = (a);             \
@@ -936,11 +964,15 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
     rr[J7] = SLOT(V_RHS)[J7];
   }
   int it = 0;
-  float gamma = 0.f, gamma0 = 0.f, alpha = 0.f;
+  float gamma = 0.f, gamma0 = 0.f, alpha = 0.f, inv_gamma = 0.f, inv_alpha = 0.f;
+  const float eps2 = eps * eps;
   while (true) {
-    // u = Phi r: y = D^-1 r; u = y - D^-1 (O y)
-    __syncwarp();
-    if (act) {
+    // u = Phi r: y = D^-1 r; u = y - D^-1 (O y).  Idle lanes (act false) run
+    // the same straight-line code on a valid knot with zero block rows, so
+    // the warp never branches on act; only their stores are predicated off.
+    // (Block barrier: knot slot 32's rows span warps 0 and 1.)
+    __syncthreads();
+    if (pwarp) {
       float y0 = 0.f, y1 = 0.f;
 #pragma unroll
       for (int c = 0; c < XM; ++c) {
@@ -949,33 +981,32 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
       }
       u0 = y0;
       u1 = y1;
-      if (stair) {
-        yv[J] = y0;
-        yv[J7] = y1;
-        PUSH(V_Y, y0, y1);
-      } else {
-        uv[J] = y0;
-        uv[J7] = y1;
-        PUSH(V_Z, y0, y1);
+      float* const dst = stair ? yv : uv;
+      if (act) {
+        dst[J] = y0;
+        dst[J7] = y1;
       }
+      PUSH(stair ? V_Y : V_Z, y0, y1);
     }
     if (stair) {
       if (csize > 1) cg::this_cluster().sync(); else __syncthreads();
       tstamp(C, T_PCG_Y, tlast);
-      if (act) {
+      if (pwarp) {
         float t0 = 0.f, t1 = 0.f;
 #pragma unroll
         for (int c = 0; c < XM; ++c) {
-          t0 += R.l0(c) * yv[c - VS];
-          t1 += R.l1(c) * yv[c - VS];
-          t0 += R.u0(c) * yv[c + VS];
-          t1 += R.u1(c) * yv[c + VS];
+          t0 += R.l0(c) * yv[c - VW];
+          t1 += R.l1(c) * yv[c - VW];
+          t0 += R.u0(c) * yv[c + VW];
+          t1 += R.u1(c) * yv[c + VW];
         }
-        tv[J] = t0;
-        tv[J7] = t1;
+        if (act) {
+          tv[J] = t0;
+          tv[J7] = t1;
+        }
       }
-      __syncwarp();
-      if (act) {
+      __syncthreads();
+      if (pwarp) {
         float q0 = 0.f, q1 = 0.f;
 #pragma unroll
         for (int c = 0; c < XM; ++c) {
@@ -984,38 +1015,43 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
         }
         u0 -= q0;
         u1 -= q1;
-        uv[J] = u0;
-        uv[J7] = u1;
+        if (act) {
+          uv[J] = u0;
+          uv[J7] = u1;
+        }
         PUSH(V_Z, u0, u1);
       }
     }
     if (csize > 1) cg::this_cluster().sync(); else __syncthreads();
     // w = S u
     DF ru = df_zero(), wu = df_zero();
-    if (act) {
+    if (pwarp) {
       float a0 = 0.f, a1 = 0.f;
 #pragma unroll
       for (int c = 0; c < XM; ++c) {
         const float v0 = uv[c];
         a0 += Drow0[c * XM] * v0;
         a1 += Drow0[c * XM + QM] * v0;
-        const float vm = uv[c - VS];
+        const float vm = uv[c - VW];
         a0 += R.l0(c) * vm;
         a1 += R.l1(c) * vm;
-        const float vp = uv[c + VS];
+        const float vp = uv[c + VW];
         a0 += R.u0(c) * vp;
         a1 += R.u1(c) * vp;
       }
       w0 = a0;
       w1 = a1;
-      ru = df_fma(ru, rr[J], u0);
-      ru = df_fma(ru, rr[J7], u1);
-      wu = df_fma(wu, w0, u0);
-      wu = df_fma(wu, w1, u1);
+      const DF ru1 = df_fma(df_fma(ru, rr[J], u0), rr[J7], u1);
+      const DF wu1 = df_fma(df_fma(wu, w0, u0), w1, u1);
+      ru = act ? ru1 : ru;
+      wu = act ? wu1 : wu;
     }
     tstamp(C, T_PCG_S, tlast);
     cluster_df_sum2(red, rank, csize, ru, wu, rbuf);
     tstamp(C, T_PCG_WZ, tlast);
+    // scalars: one division on the critical path; 1/gamma and 1/alpha for
+    // the next iteration are formed off it, and the stopping rule
+    // sqrt(gamma / gamma_0) <= eps is tested as gamma <= eps^2 gamma_0
     const float gnew = df_val(ru), eps_wu = df_val(wu);
     float beta;
     if (it == 0) {
@@ -1024,25 +1060,31 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
       beta = 0.f;
       alpha = gnew / eps_wu;
     } else {
-      if (!(gnew > 0.f) || sqrtf(gnew / gamma0) <= eps) break;
+      if (!(gnew > 0.f) || gnew <= eps2 * gamma0) break;
       if (it >= maxit) {
         *hit_max = true;
         break;
       }
-      beta = gnew / gamma;
-      alpha = gnew / (eps_wu - beta * gnew / alpha);
+      beta = gnew * inv_gamma;
+      alpha = gnew / (eps_wu - beta * gnew * inv_alpha);
     }
     gamma = gnew;
+    inv_gamma = 1.f / gnew;
+    inv_alpha = 1.f / alpha;
     // p = u + beta p; s = w + beta s; dnu += alpha p; r -= alpha s
-    if (act) {
-      p0 = u0 + beta * p0;
-      p1 = u1 + beta * p1;
-      s0 = w0 + beta * s0;
-      s1 = w1 + beta * s1;
-      dn[J] += alpha * p0;
-      dn[J7] += alpha * p1;
-      rr[J] -= alpha * s0;
-      rr[J7] -= alpha * s1;
+    p0 = u0 + beta * p0;
+    p1 = u1 + beta * p1;
+    s0 = w0 + beta * s0;
+    s1 = w1 + beta * s1;
+    {
+      const float d0 = dn[J] + alpha * p0, d1 = dn[J7] + alpha * p1;
+      const float r0 = rr[J] - alpha * s0, r1 = rr[J7] - alpha * s1;
+      if (act) {
+        dn[J] = d0;
+        dn[J7] = d1;
+        rr[J] = r0;
+        rr[J7] = r1;
+      }
     }
     ++it;
   }

@@ -60,10 +60,13 @@ def block(buf, off, name, K):
 V_RR, V_P0, V_P1, V_Q, V_Y, V_W, V_Z, V_RHS, V_DNU = range(9)
 
 
+VW = 18  # knot stride of the vector windows
+
+
 def vec(buf, off, k_max, idx):
-    VV = (k_max + 3) * VS
-    base = off["vec"] + idx * VV + VS
-    return buf[base:base + (k_max + 1) * VS].reshape(k_max + 1, VS)[:, :XM]
+    VV = (k_max + 3) * VW
+    base = off["vec"] + idx * VV + VW
+    return buf[base:base + (k_max + 1) * VW].reshape(k_max + 1, VW)[:, :XM]
 
 
 PROBS = [
