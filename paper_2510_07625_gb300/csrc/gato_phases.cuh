@@ -40,6 +40,7 @@ enum : int { V_RR = 0, V_P0, V_P1, V_Q, V_Y, V_W, V_Z, V_RHS, V_DNU };
 // reads with one instruction fall in four different shared-memory banks
 // (with 16 the first and third knot collide).
 constexpr int VW = 18;
+static_assert(VW % 2 == 0, "window rows must stay 8-byte aligned for pair loads");
 
 struct Ctx {
   int N, dof, cost_kind;
@@ -168,6 +169,10 @@ __device__ __forceinline__ float& blk(float* base, int k, int r, int c) { return
 __device__ __forceinline__ float& bD(const Ctx& C, int k, int r, int c) { return blk(C.Dm, k - C.bk0, r, c); }
 __device__ __forceinline__ float& bL(const Ctx& C, int k, int r, int c) { return blk(C.Lm, k - C.bk0, r, c); }
 __device__ __forceinline__ float& bP(const Ctx& C, int k, int r, int c) { return blk(C.Pm, k - C.bk0, r, c); }
+
+// Entries 2m, 2m+1 of a window row (8-byte aligned: the window base, its
+// slot stride and VW are even).
+__device__ __forceinline__ float2 ld2(const float* v, int m) { return reinterpret_cast<const float2*>(v)[m]; }
 
 __device__ __forceinline__ float* vec(const Ctx& C, int s, int k) {
   return C.vb + s * C.vstride + (k - C.vk0) * VW;
@@ -975,9 +980,12 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
     if (pwarp) {
       float y0 = 0.f, y1 = 0.f;
 #pragma unroll
-      for (int c = 0; c < XM; ++c) {
-        y0 += R.P0[c] * rr[c];
-        y1 += R.P1[c] * rr[c];
+      for (int m = 0; m < XM / 2; ++m) {
+        const float2 v = ld2(rr, m);
+        y0 += R.P0[2 * m] * v.x;
+        y1 += R.P1[2 * m] * v.x;
+        y0 += R.P0[2 * m + 1] * v.y;
+        y1 += R.P1[2 * m + 1] * v.y;
       }
       u0 = y0;
       u1 = y1;
@@ -994,11 +1002,17 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
       if (pwarp) {
         float t0 = 0.f, t1 = 0.f;
 #pragma unroll
-        for (int c = 0; c < XM; ++c) {
-          t0 += R.l0(c) * yv[c - VW];
-          t1 += R.l1(c) * yv[c - VW];
-          t0 += R.u0(c) * yv[c + VW];
-          t1 += R.u1(c) * yv[c + VW];
+        for (int m = 0; m < XM / 2; ++m) {
+          const float2 vm = ld2(yv - VW, m), vp = ld2(yv + VW, m);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int c = 2 * m + h;
+            const float a = h ? vm.y : vm.x, b = h ? vp.y : vp.x;
+            t0 += R.l0(c) * a;
+            t1 += R.l1(c) * a;
+            t0 += R.u0(c) * b;
+            t1 += R.u1(c) * b;
+          }
         }
         if (act) {
           tv[J] = t0;
@@ -1009,9 +1023,12 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
       if (pwarp) {
         float q0 = 0.f, q1 = 0.f;
 #pragma unroll
-        for (int c = 0; c < XM; ++c) {
-          q0 += R.P0[c] * tv[c];
-          q1 += R.P1[c] * tv[c];
+        for (int m = 0; m < XM / 2; ++m) {
+          const float2 v = ld2(tv, m);
+          q0 += R.P0[2 * m] * v.x;
+          q1 += R.P1[2 * m] * v.x;
+          q0 += R.P0[2 * m + 1] * v.y;
+          q1 += R.P1[2 * m + 1] * v.y;
         }
         u0 -= q0;
         u1 -= q1;
@@ -1028,16 +1045,21 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
     if (pwarp) {
       float a0 = 0.f, a1 = 0.f;
 #pragma unroll
-      for (int c = 0; c < XM; ++c) {
-        const float v0 = uv[c];
-        a0 += Drow0[c * XM] * v0;
-        a1 += Drow0[c * XM + QM] * v0;
-        const float vm = uv[c - VW];
-        a0 += R.l0(c) * vm;
-        a1 += R.l1(c) * vm;
-        const float vp = uv[c + VW];
-        a0 += R.u0(c) * vp;
-        a1 += R.u1(c) * vp;
+      for (int m = 0; m < XM / 2; ++m) {
+        const float2 v2 = ld2(uv, m), vm2 = ld2(uv - VW, m), vp2 = ld2(uv + VW, m);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int c = 2 * m + h;
+          const float v0 = h ? v2.y : v2.x;
+          a0 += Drow0[c * XM] * v0;
+          a1 += Drow0[c * XM + QM] * v0;
+          const float vm = h ? vm2.y : vm2.x;
+          a0 += R.l0(c) * vm;
+          a1 += R.l1(c) * vm;
+          const float vp = h ? vp2.y : vp2.x;
+          a0 += R.u0(c) * vp;
+          a1 += R.u1(c) * vp;
+        }
       }
       w0 = a0;
       w1 = a1;
