@@ -88,6 +88,7 @@ __device__ void sqp_solve(Ctx& C, const ProbDesc& P, const Params& prm, int iter
     csync(C);  // defect c_k0 comes from the neighbour's last knot
     tstamp(C, T_JAC, tl);
     st_kkt_merit(C, prm.mu, rbuf);
+    if (it == 0) st_line_search(C, prm.mu, prm.beta, prm.n_alpha, rbuf, true);  // the iterate's merit
     tstamp(C, T_KKT, tl);
     kkt = C.scal[S_KKT];
     merit = C.scal[S_MERIT0];
@@ -281,6 +282,7 @@ __global__ void __launch_bounds__(NTHR, 1) sqp_plain_stage(int stage, PlainArgs 
     case PS_JAC: st_dyn_jacobians(C); break;
     case PS_KKT: {
       st_kkt_merit(C, prm.mu, rbuf);
+      if (a.it == 0) st_line_search(C, prm.mu, prm.beta, prm.n_alpha, rbuf, true);  // the iterate's merit
       const bool bad = *reinterpret_cast<volatile int*>(C.scal + S_FLAGS) != 0;
       if (lead) {
         C.scal[S_MERITF] = C.scal[S_MERIT0];

@@ -90,8 +90,11 @@ __device__ __forceinline__ void tstamp(const Ctx& C, int slot, long long& last) 
   }
 }
 
-// scal[] slots (SCAL_FLOATS floats)
-constexpr int SCAL_FLOATS = 64;
+// scal[] slots (SCAL_FLOATS floats); from S_MDF on the merits as normalised
+// (hi, lo) pairs: the base merit, then trial i at S_MDF + 2 + 2i
+constexpr int SCAL_FLOATS = 128;  // S_MDF + 2 + 2 * MAX_ALPHA = 98 used
+constexpr int S_MDF = 64;
+static_assert(S_MDF + 2 + 2 * MAX_ALPHA <= SCAL_FLOATS, "merit pairs fit the scalar block");
 enum : int {
   S_KKT = 0, S_MERIT0, S_CMAX, S_GMAX, S_DMAX, S_ALPHA, S_FLAGS, S_PCG, S_ITERS, S_MERITF,
   S_CHOICE, S_REDBUF, S_DONE, S_NSQP, S_NPCG, S_RFLAGS, S_MERITS = 16  // S_MERITS..+15
@@ -634,8 +637,8 @@ __device__ inline void st_kkt_merit(const Ctx& C, float mu, int& rbuf) {
   const float J = df_val(sm[0]), c1 = df_val(sm[1]);
   if (threadIdx.x == 0) {
     C.scal[S_KKT] = fmaxf(mx[0], mx[2] / fmaxf(1.f, mx[1]));
-    C.scal[S_MERIT0] = J + mu * c1;
-    if (mx[3] > 0.f || !isfinite(J)) flag_nonfinite(C);
+    // (the merit itself comes from the line search's evaluation of the iterate)
+    if (mx[3] > 0.f || !isfinite(J) || !isfinite(c1)) flag_nonfinite(C);
   }
   __syncthreads();
 }
@@ -1201,20 +1204,25 @@ __device__ __forceinline__ float trial_cost(const Ctx& C, int k, const float* x,
 // Merit (Eq. 3) of Z + alpha_i dZ for alpha_i = beta^-i (Eq. 7), i < n_alpha:
 // one thread per (alpha, own knot); per-alpha sums over the CTA's knots in a
 // fixed order, then over the cluster's CTAs in rank order.
-__device__ inline void st_line_search(const Ctx& C, float mu, float beta, int n_alpha, int& rbuf) {
+__device__ inline void st_line_search(const Ctx& C, float mu, float beta, int n_alpha, int& rbuf,
+                                      bool base = false) {
   const int N = C.N, K = C.k1 - C.k0;
-  float* contrib = vec(C, V_Y, C.k0);  // [n_alpha][K] (free during the line search)
-  for (int it = threadIdx.x; it < n_alpha * K; it += NTHR) {
+  const int na = base ? 1 : n_alpha;
+  float* contrib = vec(C, V_Y, C.k0);  // [na][K] (free during the line search)
+  for (int it = threadIdx.x; it < na * K; it += NTHR) {
     const int a = it / K, k = C.k0 + it % K;
     float alpha = 1.f;
     for (int i = 0; i < a; ++i) alpha /= beta;
+    // the iterate itself (base) or its trial point Z + alpha dZ
+    auto xat = [&](int idx) { return base ? C.X[idx] : C.X[idx] + alpha * C.dX[idx]; };
+    auto uat = [&](int idx) { return base ? C.U[idx] : C.U[idx] + alpha * C.dU[idx]; };
     float x[XM], u[QM];
 #pragma unroll
-    for (int i = 0; i < XM; ++i) x[i] = C.X[k * VS + i] + alpha * C.dX[k * VS + i];
+    for (int i = 0; i < XM; ++i) x[i] = xat(k * VS + i);
     float v;
     if (k < N) {
 #pragma unroll
-      for (int i = 0; i < QM; ++i) u[i] = C.U[k * US + i] + alpha * C.dU[k * US + i];
+      for (int i = 0; i < QM; ++i) u[i] = uat(k * US + i);
       float qdd[QM];
       forward_dynamics(*C.M, x, x + QM, u, qdd);
       float c1 = 0.f;
@@ -1222,8 +1230,8 @@ __device__ inline void st_line_search(const Ctx& C, float mu, float beta, int n_
       for (int i = 0; i < QM; ++i) {
         const float qdn = x[QM + i] + C.h * qdd[i];
         const float qn = x[i] + C.h * qdn;
-        c1 += fabsf(qn - (C.X[(k + 1) * VS + i] + alpha * C.dX[(k + 1) * VS + i]));
-        c1 += fabsf(qdn - (C.X[(k + 1) * VS + QM + i] + alpha * C.dX[(k + 1) * VS + QM + i]));
+        c1 += fabsf(qn - xat((k + 1) * VS + i));
+        c1 += fabsf(qdn - xat((k + 1) * VS + QM + i));
       }
       v = trial_cost(C, k, x, u) + mu * c1;
     } else {
@@ -1232,7 +1240,7 @@ __device__ inline void st_line_search(const Ctx& C, float mu, float beta, int n_
     if (k == 0) {
       float c0 = 0.f;
 #pragma unroll
-      for (int i = 0; i < XM; ++i) c0 += fabsf(C.xs[i] - (C.X[i] + alpha * C.dX[i]));
+      for (int i = 0; i < XM; ++i) c0 += fabsf(C.xs[i] - xat(i));
       v += mu * c0;
     }
     contrib[a * K + (k - C.k0)] = v;
@@ -1241,7 +1249,7 @@ __device__ inline void st_line_search(const Ctx& C, float mu, float beta, int n_
   // warp a: this CTA's partial of alpha_a (lane-strided over its knots, fixed tree)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float* slots = C.red + rbuf * RED_SLOTS * RED_W;  // [rank][alpha] pairs
-  for (int a = warp; a < n_alpha; a += NWARP) {
+  for (int a = warp; a < na; a += NWARP) {
     DF s = df_zero();
     for (int kk = lane; kk < K; kk += 32) s = df_add(s, contrib[a * K + kk]);
     s = warp_df_sum(s);
@@ -1261,32 +1269,49 @@ __device__ inline void st_line_search(const Ctx& C, float mu, float beta, int n_
     }
   }
   csync(C);
-  if (threadIdx.x < n_alpha) {
+  if (threadIdx.x < na) {
     const int a = threadIdx.x;
     DF s = df_zero();
     for (int r = 0; r < C.csize; ++r)
       s = df_addd(s, DF{slots[(r * MAX_ALPHA + a) * 2], slots[(r * MAX_ALPHA + a) * 2 + 1]});
-    const float m = df_val(s);
-    C.scal[S_MERITS + a] = isfinite(m) ? m : INFINITY;
+    s = df_norm(s);
+    if (!isfinite(s.hi) || !isfinite(s.lo)) s = DF{INFINITY, 0.f};
+    const int o = base ? S_MDF : S_MDF + 2 + 2 * a;
+    C.scal[o] = s.hi;
+    C.scal[o + 1] = s.lo;
+    C.scal[base ? S_MERIT0 : S_MERITS + a] = s.hi;
   }
   rbuf ^= 1;
   __syncthreads();
 }
 
+// a < b for normalised (hi, lo) merits
+__device__ __forceinline__ bool df_less(const float* a, const float* b) {
+  return a[0] < b[0] || (a[0] == b[0] && a[1] < b[1]);
+}
+
 // Argmin with ties to the smallest index; accept only a strict decrease (c7).
+// The base merit is the accepted trial's (the same evaluation of the same
+// point), so trial and base merits always come from the same code.
 __device__ inline int st_accept(const Ctx& C, float beta, int n_alpha) {
   const int N = C.N;
+  const float* md = C.scal + S_MDF;
   int best = 0;
   for (int a = 1; a < n_alpha; ++a)
-    if (C.scal[S_MERITS + a] < C.scal[S_MERITS + best]) best = a;
-  const float m0 = C.scal[S_MERIT0];
-  const int choice = (C.scal[S_MERITS + best] < m0) ? best : -1;
+    if (df_less(md + 2 + 2 * a, md + 2 + 2 * best)) best = a;
+  const int choice = df_less(md + 2 + 2 * best, md) ? best : -1;
   if (choice >= 0) {
     float alpha = 1.f;
     for (int i = 0; i < choice; ++i) alpha /= beta;
     const int ke = C.k1 < N ? C.k1 : N;
     for (int i = threadIdx.x; i < (C.k1 - C.k0) * VS; i += NTHR) C.X[C.k0 * VS + i] += alpha * C.dX[C.k0 * VS + i];
     for (int i = threadIdx.x; i < (ke - C.k0) * US; i += NTHR) C.U[C.k0 * US + i] += alpha * C.dU[C.k0 * US + i];
+  }
+  csync(C);  // every thread (and CTA) has read the old base merit
+  if (choice >= 0 && threadIdx.x == 0) {
+    C.scal[S_MDF] = md[2 + 2 * choice];
+    C.scal[S_MDF + 1] = md[3 + 2 * choice];
+    C.scal[S_MERIT0] = md[2 + 2 * choice];
   }
   return choice;
 }
