@@ -228,8 +228,8 @@ def run_gpu(args):
                        "parallelism": f"replicas x{ws}", "l2": "flushed between timed launches (512 MB write)",
                        "launch": launch},
             "latency_ms": lat, "plain_gpu_form": plain, "uneven_graph": uneven, "serving": serve,
-            "speedup_vs_plain_B32": round(plain["solves_per_s_B32"] and lat["B32_iters10"]["solves_per_s"]
-                                          / plain["solves_per_s_B32"], 2),
+            "speedup_vs_plain_B32": round(lat["B32_iters10"]["solves_per_s"] / plain["solves_per_s_B32"], 2),
+            "speedup_vs_plain_B256": round(value / ws / plain[f"solves_per_s_B{B_MAIN}"], 2),
             "pcg_iters_per_solve": round(pcg / dp.n, 1), "sqp_iters_per_solve": round(sqp / dp.n, 2),
             "wall_s_timed": round(t_wall, 4),
             "roofline": {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 2),
@@ -282,23 +282,27 @@ def latency_runs(gato, I, torch, stream, flush, n_calls=200, launch_cfg=False):
     return out
 
 
-def plain_form(gato, I, torch, reps=3):
-    """The plain one-solve-per-launch form on the B=32 batch (same arithmetic)."""
-    probs = I.config_sweep(B_LAT, N_MAIN)
-    B = gato.Batch([I.arm7()], B_LAT, N_MAIN)
-    dp = gato.DeviceProblems(B, probs)
-    ts = []
-    for _ in range(reps):
-        dp.reset()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        gato.gato_solve_plain(B.handle, dp.arr, dp.n, ITERS, None)
-        B.sync()
-        ts.append(time.perf_counter() - t0)
-    B.close()
-    t = statistics.median(ts)
-    return {"solves_per_s_B32": round(B_LAT / t, 1), "ms_per_call_B32": round(1e3 * t, 2),
-            "launches_per_solve_iter": 12}
+def plain_form(gato, I, torch, reps=3, sizes=(B_LAT, B_MAIN)):
+    """The plain one-solve-per-launch form (same arithmetic, every stage of every
+    SQP iteration of every solve its own launch) at B = 32 and 256."""
+    out = {"launches_per_solve_iter": 12}
+    for Bn in sizes:
+        probs = I.config_sweep(Bn, N_MAIN)
+        B = gato.Batch([I.arm7()], Bn, N_MAIN)
+        dp = gato.DeviceProblems(B, probs)
+        ts = []
+        for _ in range(reps if Bn <= B_LAT else 1):
+            dp.reset()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            gato.gato_solve_plain(B.handle, dp.arr, dp.n, ITERS, None)
+            B.sync()
+            ts.append(time.perf_counter() - t0)
+        B.close()
+        t = statistics.median(ts)
+        out[f"solves_per_s_B{Bn}"] = round(Bn / t, 1)
+        out[f"ms_per_call_B{Bn}"] = round(1e3 * t, 2)
+    return out
 
 
 def uneven_graph(gato, I, torch, reps=10):

@@ -159,7 +159,7 @@ gato_status gato_solve_plain(gato_batch* b, const gato_problem* problems, int32_
  *
  * Same solver and kernel as gato_solve, but it needs no gato_batch: its
  * scratch (per-solve workspace, descriptors, models, launch order) is a set of
- * fixed-size arrays compiled into the library, about 3.3 MiB held on every GPU
+ * fixed-size arrays compiled into the library, about 2.6 MiB held on every GPU
  * that loads it until the process exits.  Limits: n <= 16 solves, N <= 64,
  * n_models <= 8, and every problem must use GATO_MEM_DEVICE pointers; larger
  * or host problems return GATO_E_INVALID and launch nothing.  `results` is a

@@ -31,7 +31,6 @@ __device__ __forceinline__ void bind_workspace(Ctx& C, float* ws, const WsLayout
   C.rg = ws + L.rg;
   C.cv = ws + L.cv;
   C.Jk = ws + L.Jk;
-  C.Li = ws + L.Li;
   C.Dx = ws + L.Dx;
   C.Du = ws + L.Du;
   C.nu = ws + L.nu;

@@ -52,7 +52,7 @@ struct Ctx {
   // cluster partition
   int rank, csize, k0, k1;
   // global workspace
-  float *X, *U, *dX, *dU, *Fq, *Fv, *Mi, *qdd, *dT, *Qi, *Ri, *qg, *rg, *cv, *Jk, *Li;
+  float *X, *U, *dX, *dU, *Fq, *Fv, *Mi, *qdd, *dT, *Qi, *Ri, *qg, *rg, *cv, *Jk;
   float *Dx, *Du;       // dual residual d = g + C^T nu at the current linearisation
   float* nu;            // multiplier (global, all knots)
   LinkRec* LV;
@@ -131,7 +131,7 @@ __host__ __device__ inline WsLayout ws_layout(int Nmax, bool global_blocks, bool
   L.rg = o; o += align32(Nmax * US);
   L.cv = o; o += align32(K * VS);
   L.Jk = o; o += align32(K);
-  L.Li = o; o += align32(K * LIS);
+  L.Li = o;  // (no longer used: the block inverse keeps its rows in registers)
   L.LV = o; o += align32(Nmax * QM * LVS);
   L.Dx = o; o += align32(K * VS);
   L.Du = o; o += align32(Nmax * US);

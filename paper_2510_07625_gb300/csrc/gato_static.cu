@@ -24,7 +24,7 @@ constexpr int kMaxModels = 8;
 constexpr int kMaxDevices = 64;
 // Floats of one solve's workspace at N = 64 (Schur blocks in shared memory);
 // checked against ws_layout() at set-up.
-constexpr size_t kWsStride = 53248;
+constexpr size_t kWsStride = 40960;
 
 static __device__ __align__(256) float g_scratch[kMaxSolves * kWsStride];
 static __device__ __align__(256) ProbDesc g_probs[kMaxSolves];
