@@ -247,9 +247,9 @@ def run_gpu(args):
 
 # DRAM bytes per launch of the dominant kernel on this workload (latency form,
 # 35 knots per CTA), from the ncu capture summarised in
-# profiles/sqp_fused_b256_n64_metrics.md: 17,825,024 read + 9,144,320 written.
+# profiles/sqp_fused_b256_n64_metrics.md: 17,962,240 read + 6,988,032 written.
 # Set to None when the kernel changes until it is measured again.
-TRAFFIC_BYTES = 26969344
+TRAFFIC_BYTES = 24950272
 
 
 def latency_runs(gato, I, torch, stream, flush, n_calls=200, launch_cfg=False):
