@@ -922,9 +922,11 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
   const bool stair = (precond == 0);
   *hit_max = false;
   long long tlast = C.tm ? clock64() : 0;
-  // PCG lane map: warps 0-7 carry 4 knots each on lanes 0-27; knot slot 32
-  // uses the spare lanes 28-31 of warp 0 (rows 0-3) and 28-30 of warp 1
-  // (rows 4-6).  The last warp does no PCG arithmetic, only barriers and
+  // PCG lane map: warps 0-7 carry 4 knots each on lanes 0-27 (slots 0-7,
+  // then 9-32); knot slot 8 uses the spare lanes 28-31 of warp 0 (rows 0-3)
+  // and 28-30 of warp 1 (rows 4-6) -- slot 8, because its window rows fall in
+  // other shared-memory banks than those of slots 0-7 (slots 16 apart share
+  // banks).  The last warp does no PCG arithmetic, only barriers and
   // reductions, so no SM sub-partition issues for three working warps.
   const int lane_ = threadIdx.x & 31, warp_ = threadIdx.x >> 5;
   const bool pwarp = warp_ < NWARP - 1;
@@ -933,7 +935,8 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
   // rows j, j+7 with j in 0..6 for every lane (idle lanes use row 0), so that
   // all block and vector addresses stay inside their 14x14 blocks and rows
   const int j = !lane_ok ? 0 : (spare ? lane_ - 28 + (warp_ == 1 ? 4 : 0) : lane_ - 7 * (lane_ / 7));
-  const int k = C.k0 + (spare ? 32 : 4 * warp_ + lane_ / 7);
+  const int slot = spare ? 8 : 4 * warp_ + lane_ / 7 + (4 * warp_ + lane_ / 7 >= 8 ? 1 : 0);
+  const int k = C.k0 + slot;
   const bool act = lane_ok && k < C.k1;
   RowRegs<REG> R;
   R.load(C, k, j, act);
@@ -978,7 +981,7 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
     // u = Phi r: y = D^-1 r; u = y - D^-1 (O y).  Idle lanes (act false) run
     // the same straight-line code on a valid knot with zero block rows, so
     // the warp never branches on act; only their stores are predicated off.
-    // (Block barrier: knot slot 32's rows span warps 0 and 1.)
+    // (Block barrier: knot slot 8's rows span warps 0 and 1.)
     __syncthreads();
     if (pwarp) {
       float y0 = 0.f, y1 = 0.f;
