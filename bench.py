@@ -486,9 +486,12 @@ def sweep(Bs=(1, 16, 32, 64, 128, 256), Ns=(32, 64, 128), iters=ITERS, reps=5):
                     ts.append(e0.elapsed_time(e1))
             t = statistics.median(ts)
             res = gato.gato_get_results(B.handle, dp.n)
+            pcg = [res[i].pcg_iters for i in range(dp.n)]
+            shape = gato.gato_query_launch(N, Bn, **cfg)
             print(json.dumps({"sweep": {"B": Bn, "N": N, "ms": round(t, 4), "solves_per_s": round(Bn / (t / 1e3), 1),
-                                        "launch": cfg,
-                                        "pcg_per_solve": round(sum(res[i].pcg_iters for i in range(dp.n)) / Bn, 1)}}),
+                                        "launch": cfg, "ctas_per_solve": shape["ctas_per_solve"],
+                                        "resident_solves": shape["max_resident_solves"],
+                                        "pcg_per_solve": round(sum(pcg) / Bn, 1), "pcg_max": max(pcg)}}),
                   flush=True)
             B.close()
 

@@ -196,6 +196,24 @@ typedef struct {
  * autotuned / automatic choice.  GATO_E_INVALID for out-of-range fields. */
 gato_status gato_set_launch_config(gato_batch* b, const gato_launch_config* cfg);
 
+/* What a launch of n_solves solves of horizon N looks like on the current
+ * device under cfg (NULL = the automatic choice): the CTAs per solve, the
+ * kernel form (1 latency, 2 throughput), the dynamic shared memory per CTA,
+ * and how many solves (thread-block clusters) the device holds at once
+ * (cudaOccupancyMaxActiveClusters; clusters are placed within one GPC, so this
+ * can be below SMs / CTAs per solve).  Solves beyond that count wait for a
+ * free cluster slot.  GATO_E_INVALID for N outside 1..256, n_solves < 1 or an
+ * out-of-range cfg; GATO_E_CUDA if the query fails.  No device memory is
+ * allocated. */
+typedef struct {
+  int32_t ctas_per_solve;
+  int32_t variant;
+  int32_t smem_bytes;
+  int32_t max_resident_solves;
+} gato_launch_info;
+gato_status gato_query_launch(int32_t N, int32_t n_solves, const gato_launch_config* cfg,
+                              gato_launch_info* out);
+
 /* Times every candidate configuration (both variants x knots per CTA
  * {33, 24, 17, 12, 9, 6} x uniform clusters, skipping duplicates and
  * throughput forms whose shared memory does not fit two CTAs per SM) on these

@@ -846,6 +846,35 @@ gato_status gato_set_launch_config(gato_batch* b, const gato_launch_config* cfg)
   return GATO_OK;
 }
 
+gato_status gato_query_launch(int32_t N, int32_t n_solves, const gato_launch_config* cfg,
+                              gato_launch_info* out) {
+  if (!out || N < 1 || N > NMAX_LIMIT || n_solves < 1) return GATO_E_INVALID;
+  LaunchPlan p;
+  if (cfg) {
+    if (cfg->variant < 0 || cfg->variant > 2 || cfg->knots_per_cta == 1 || cfg->knots_per_cta < 0 ||
+        cfg->knots_per_cta > KPC_MAX || cfg->cluster < 0 || cfg->cluster > 8)
+      return GATO_E_INVALID;
+    p.variant = cfg->variant;
+    p.knots_per_cta = cfg->knots_per_cta;
+    p.cluster = cfg->cluster;
+  }
+  const int c = cluster_size(N, p.knots_per_cta, p.cluster);
+  const size_t smem = fused_smem_bytes(N, c);
+  if (smem > SMEM_LIMIT_BYTES) return GATO_E_INVALID;
+  const bool reg = !use_throughput_variant(n_solves, c, p.variant, smem);
+  int active = 0;
+  const cudaError_t e = fused_active_clusters(N, c, reg, &active);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return GATO_E_CUDA;
+  }
+  out->ctas_per_solve = c;
+  out->variant = reg ? 1 : 2;
+  out->smem_bytes = (int32_t)smem;
+  out->max_resident_solves = active;
+  return GATO_OK;
+}
+
 gato_status gato_autotune(gato_batch* b, const gato_problem* problems, int32_t n, int32_t max_sqp_iters,
                           int32_t reps, gato_launch_config* best, float* best_ms) {
   if (!b) return GATO_E_INVALID;

@@ -75,6 +75,10 @@ cudaError_t launch_plain(const ProbDesc* probs, const DevModel* models, Result* 
 
 size_t fused_smem_bytes(int nmax, int csize);
 
+// Clusters of csize CTAs of the fused kernel (latency form if reg) that the
+// current device holds at once for a launch whose largest horizon is nmax.
+cudaError_t fused_active_clusters(int nmax, int csize, bool reg, int* out);
+
 enum PlainStage : int {
   PS_LOAD = 0, PS_MASS, PS_FD, PS_VALUE, PS_TANGENT, PS_JAC, PS_KKT, PS_SCHUR, PS_BINV, PS_PCG,
   PS_RECOVER, PS_LS, PS_ACCEPT, PS_STORE, PS_COUNT

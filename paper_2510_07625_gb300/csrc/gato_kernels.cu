@@ -90,6 +90,32 @@ static cudaError_t launch_fused_t(const FusedLaunch& a, size_t smem, cudaStream_
   return cudaLaunchKernelEx(&cfg, sqp_fused<REG>, a);
 }
 
+template <bool REG>
+static cudaError_t active_clusters_t(int csize, size_t smem, int* out) {
+  cudaError_t e = configure_t<REG>(smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(csize * num_sms()));
+  cfg.blockDim = dim3(NTHR);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaOccupancyMaxActiveClusters(out, sqp_fused<REG>, &cfg);
+}
+
+cudaError_t fused_active_clusters(int nmax, int csize, bool reg, int* out) {
+  *out = 0;
+  if (csize < 1 || csize > 8) return cudaErrorInvalidValue;
+  const size_t smem = fused_smem_bytes(nmax, csize);
+  if (smem > SMEM_LIMIT_BYTES) return cudaErrorInvalidValue;
+  return reg ? active_clusters_t<true>(csize, smem, out) : active_clusters_t<false>(csize, smem, out);
+}
+
 bool use_throughput_variant(int n, int csize, int variant, size_t smem) {
   if (variant == 1) return false;
   if (variant == 2) return true;

@@ -845,62 +845,64 @@ struct RowRegs<false> {
   }
 };
 
-// Cluster-wide compensated sums of two values (one reduction for both).
-__device__ __forceinline__ void cluster_df_sum2(float* red, int rank, int csize, DF& a, DF& b, int& buf) {
+__device__ __forceinline__ DF shfl_xor_df(DF v, int o) {
+  return DF{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+}
+__device__ __forceinline__ DF shfl_df(DF v, int src) {
+  return DF{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
+}
+
+// Cluster-wide compensated sums of three values (one reduction for all),
+// summed over the PCG's working warps 0..NWARP-2 of every CTA.  Inside a warp
+// the three sums are reduce-scattered: the first level leaves a and b on the
+// lower half-warp and c on the upper, the second a on lanes 0-7 and b on
+// 8-15, so each level exchanges one value instead of three.  Lanes 0, 8 and
+// 16 write the warp's partials into every CTA of the cluster; then every warp
+// sums them in the same fixed order (lane 8q + i takes partials i, i + 8, ...
+// of value q) and copies the totals from lanes 0, 8 and 16.
+static_assert(NWARP - 1 == 8, "partials are indexed rank * 8 + working warp");
+static_assert(3 * 64 * 2 <= RED_SLOTS * RED_W, "three values x 64 partials x 2 floats per buffer");
+__device__ __forceinline__ void cluster_df_sum3(float* red, int rank, int csize, DF& a, DF& b, DF& c,
+                                                int& buf) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* const base = red + buf * (RED_SLOTS * RED_W);
+  if (warp < NWARP - 1) {
+    const bool lower = lane < 16, hi8 = (lane & 8) != 0;
+    DF k0 = df_addd(lower ? a : c, shfl_xor_df(lower ? c : a, 16));
+    const DF k1 = df_addd(b, shfl_xor_df(b, 16));  // used on the lower half only
+    DF v = lower ? (hi8 ? k1 : k0) : k0;
+    const DF snd = lower ? (hi8 ? k0 : k1) : k0;
+    v = df_addd(v, shfl_xor_df(snd, 8));
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    DF ya, yb;
-    ya.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
-    ya.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
-    yb.hi = __shfl_xor_sync(0xffffffffu, b.hi, o);
-    yb.lo = __shfl_xor_sync(0xffffffffu, b.lo, o);
-    a = df_addd(a, ya);
-    b = df_addd(b, yb);
-  }
-  if (lane == 0) {
-    const int slot = (buf * RED_SLOTS + rank * NWARP + warp) * RED_W;
-    const float4 v = make_float4(a.hi, a.lo, b.hi, b.lo);
-    if (csize > 1) {
-      cg::cluster_group cl = cg::this_cluster();
-      for (int r = 0; r < csize; ++r) *reinterpret_cast<float4*>(cl.map_shared_rank(red, r) + slot) = v;
-    } else {
-      *reinterpret_cast<float4*>(red + slot) = v;
+    for (int o = 4; o > 0; o >>= 1) v = df_addd(v, shfl_xor_df(v, o));
+    if ((lane & 7) == 0 && lane < 24) {
+      const int off = ((lane >> 3) * 64 + rank * 8 + warp) * 2;
+      const float2 val = make_float2(v.hi, v.lo);
+      if (csize > 1) {
+        cg::cluster_group cl = cg::this_cluster();
+        for (int r = 0; r < csize; ++r) *reinterpret_cast<float2*>(cl.map_shared_rank(base, r) + off) = val;
+      } else {
+        *reinterpret_cast<float2*>(base + off) = val;
+      }
     }
   }
   if (csize > 1)
     cg::this_cluster().sync();
   else
     __syncthreads();
-  a = df_zero();
-  b = df_zero();
-  const int ns = csize * NWARP;
-  for (int i0 = 0; i0 < ns; i0 += 32) {
-    const int i = i0 + lane;
-    const float4 v = i < ns ? *reinterpret_cast<const float4*>(red + (buf * RED_SLOTS + i) * RED_W)
-                            : make_float4(0.f, 0.f, 0.f, 0.f);
-    a = df_addd(a, DF{v.x, v.y});
-    b = df_addd(b, DF{v.z, v.w});
+  DF v = df_zero();
+  if (lane < 24) {
+    const float* src = base + (lane >> 3) * 128;
+    for (int j = lane & 7; j < 8 * csize; j += 8) {
+      const float2 t = *reinterpret_cast<const float2*>(src + 2 * j);
+      v = df_addd(v, DF{t.x, t.y});
+    }
   }
-  // a butterfly just wide enough for the ns partials (the same for every warp
-  // and CTA), then every lane copies the total from the first group
-  const int top = ns > 16 ? 16 : (ns > 8 ? 8 : 4);
-  for (int o = top; o > 0; o >>= 1) {
-    DF ya, yb;
-    ya.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
-    ya.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
-    yb.hi = __shfl_xor_sync(0xffffffffu, b.hi, o);
-    yb.lo = __shfl_xor_sync(0xffffffffu, b.lo, o);
-    a = df_addd(a, ya);
-    b = df_addd(b, yb);
-  }
-  if (top < 16) {
-    const int src = lane & (2 * top - 1);
-    a.hi = __shfl_sync(0xffffffffu, a.hi, src);
-    a.lo = __shfl_sync(0xffffffffu, a.lo, src);
-    b.hi = __shfl_sync(0xffffffffu, b.hi, src);
-    b.lo = __shfl_sync(0xffffffffu, b.lo, src);
-  }
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) v = df_addd(v, shfl_xor_df(v, o));
+  a = shfl_df(v, 0);
+  b = shfl_df(v, 8);
+  c = shfl_df(v, 16);
   buf ^= 1;
 }
 
@@ -910,11 +912,15 @@ __device__ __forceinline__ void cluster_df_sum2(float* red, int rank, int csize,
 // D^-1 - D^-1 O D^-1 (reading c4).  Stops when sqrt(eta / eta_0) <= eps with
 // eta = r'u (reading c8).  Returns iterations.
 //
-// Evaluation order: the Chronopoulos-Gear arrangement of PCG, whose iterates
+// Evaluation order: a single-reduction arrangement of PCG whose iterates
 // equal standard PCG's in exact arithmetic.  S is applied to u = Phi r
-// (w = S u) and s = S p is carried by s = w + beta s, so r'u and w'u come from
-// one compensated reduction per iteration; then
-// delta = w'u - beta r'u / alpha_prev, alpha = r'u / delta.  Three barriers
+// (w = S u) and s = S p is carried by s = w + beta s.  One compensated
+// reduction per iteration gives r'u, w'u and p_old'w; the new direction's
+// curvature is expanded exactly, p'Sp = w'u + 2 beta p_old'w + beta^2
+// (p'Sp)_old, and alpha = r'u / p'Sp.  (The Chronopoulos-Gear form instead
+// assumes p_old'w = -r'u / alpha_old, which holds only while the FP32
+// directions stay conjugate; on the end-effector workload it then stalled at
+// the iteration cap where standard PCG takes ~250 iterations.)  Three barriers
 // per iteration: the y halo (stair only), the u halo, the reduction.  Every
 // address and scalar the loop needs is set up before it.
 template <bool REG>
@@ -975,7 +981,7 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
     rr[J7] = SLOT(V_RHS)[J7];
   }
   int it = 0;
-  float gamma = 0.f, gamma0 = 0.f, alpha = 0.f, inv_gamma = 0.f, inv_alpha = 0.f;
+  float gamma = 0.f, gamma0 = 0.f, alpha = 0.f, inv_gamma = 0.f, psp = 0.f;
   const float eps2 = eps * eps;
   while (true) {
     // u = Phi r: y = D^-1 r; u = y - D^-1 (O y).  Idle lanes (act false) run
@@ -1047,7 +1053,7 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
     }
     if (csize > 1) cg::this_cluster().sync(); else __syncthreads();
     // w = S u
-    DF ru = df_zero(), wu = df_zero();
+    DF ru = df_zero(), wu = df_zero(), pw = df_zero();
     if (pwarp) {
       float a0 = 0.f, a1 = 0.f;
 #pragma unroll
@@ -1071,22 +1077,24 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
       w1 = a1;
       const DF ru1 = df_fma(df_fma(ru, rr[J], u0), rr[J7], u1);
       const DF wu1 = df_fma(df_fma(wu, w0, u0), w1, u1);
+      const DF pw1 = df_fma(df_fma(pw, p0, w0), p1, w1);  // p still holds the previous direction
       ru = act ? ru1 : ru;
       wu = act ? wu1 : wu;
+      pw = act ? pw1 : pw;
     }
     tstamp(C, T_PCG_S, tlast);
-    cluster_df_sum2(red, rank, csize, ru, wu, rbuf);
+    cluster_df_sum3(red, rank, csize, ru, wu, pw, rbuf);
     tstamp(C, T_PCG_WZ, tlast);
-    // scalars: one division on the critical path; 1/gamma and 1/alpha for
-    // the next iteration are formed off it, and the stopping rule
+    // scalars: one division on the critical path; 1/gamma for the next
+    // iteration is formed off it, and the stopping rule
     // sqrt(gamma / gamma_0) <= eps is tested as gamma <= eps^2 gamma_0
-    const float gnew = df_val(ru), eps_wu = df_val(wu);
+    const float gnew = df_val(ru), wu_f = df_val(wu), pw_f = df_val(pw);
     float beta;
     if (it == 0) {
       gamma0 = gnew;
       if (!(gamma0 > 1e-30f)) break;
       beta = 0.f;
-      alpha = gnew / eps_wu;
+      psp = wu_f;
     } else {
       if (!(gnew > 0.f) || gnew <= eps2 * gamma0) break;
       if (it >= maxit) {
@@ -1094,11 +1102,11 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
         break;
       }
       beta = gnew * inv_gamma;
-      alpha = gnew / (eps_wu - beta * gnew * inv_alpha);
+      psp = wu_f + beta * (2.f * pw_f + beta * psp);
     }
+    alpha = gnew / psp;
     gamma = gnew;
     inv_gamma = 1.f / gnew;
-    inv_alpha = 1.f / alpha;
     // p = u + beta p; s = w + beta s; dnu += alpha p; r -= alpha s
     p0 = u0 + beta * p0;
     p1 = u1 + beta * p1;

@@ -33,7 +33,7 @@ EXPORTED = (
     "gato_graph_launch", "gato_graph_wait", "gato_graph_destroy", "gato_server_create",
     "gato_server_open", "gato_server_submit", "gato_server_poll", "gato_server_read",
     "gato_server_close", "gato_server_get_stats", "gato_server_last_error", "gato_server_destroy",
-    "gato_server_drive",
+    "gato_server_drive", "gato_query_launch",
 )
 LAYOUT_NAMES = ("X", "U", "dX", "dU", "Fq", "Fv", "Minv", "qdd", "dTau", "Qinv", "Rinv", "q", "r",
                 "c", "Jk", "Linv", "links", "D", "L", "P", "vec", "scal", "Dx", "Du", "nu")
@@ -65,6 +65,11 @@ class Problem(C.Structure):
 
 class LaunchConfig(C.Structure):
     _fields_ = [("variant", C.c_int32), ("knots_per_cta", C.c_int32), ("cluster", C.c_int32)]
+
+
+class LaunchInfo(C.Structure):
+    _fields_ = [("ctas_per_solve", C.c_int32), ("variant", C.c_int32), ("smem_bytes", C.c_int32),
+                ("max_resident_solves", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -139,6 +144,8 @@ def load() -> C.CDLL:
     L.gato_debug_stage_cycles.restype = C.c_int
     L.gato_set_launch_config.argtypes = [bp, C.POINTER(LaunchConfig)]
     L.gato_set_launch_config.restype = C.c_int
+    L.gato_query_launch.argtypes = [C.c_int32, C.c_int32, C.POINTER(LaunchConfig), C.POINTER(LaunchInfo)]
+    L.gato_query_launch.restype = C.c_int
     L.gato_autotune.argtypes = [bp, C.POINTER(Problem), C.c_int32, C.c_int32, C.c_int32,
                                 C.POINTER(LaunchConfig), C.POINTER(C.c_float)]
     L.gato_autotune.restype = C.c_int
@@ -286,6 +293,18 @@ def gato_solve_noalloc(models, n_models, params, problems, n, iters, results_dev
                                   C.c_void_p(results_dev_ptr), C.c_void_p(stream or 0))
     if s != GATO_OK:
         raise GatoError(s, f"gato_solve_noalloc: {gato_status_string(s)}")
+
+
+def gato_query_launch(N, n_solves, variant=None, knots_per_cta=0, cluster=0):
+    """Launch shape of n_solves solves of horizon N on the current device
+    (variant None = the automatic configuration): a dict with ctas_per_solve,
+    variant, smem_bytes and max_resident_solves."""
+    info = LaunchInfo()
+    cfg = None if variant is None else C.byref(LaunchConfig(variant, knots_per_cta, cluster))
+    s = load().gato_query_launch(N, n_solves, cfg, C.byref(info))
+    if s != GATO_OK:
+        raise GatoError(s, f"gato_query_launch: {gato_status_string(s)}")
+    return {f: getattr(info, f) for f, _ in LaunchInfo._fields_}
 
 
 def gato_set_launch_config(handle, variant=None, knots_per_cta=0, cluster=0):

@@ -118,3 +118,26 @@ def test_graph_rejects_host_problems(G):
         B.capture(hp.arr, 1, 2)
     assert e.value.status == G.GATO_E_INVALID
     B.close()
+
+
+def test_query_launch_shapes(G):
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    a = G.gato_query_launch(32, 1)
+    assert (a["ctas_per_solve"], a["variant"]) == (1, 1)
+    assert 1 <= a["max_resident_solves"] <= sms
+    b = G.gato_query_launch(64, 256)
+    assert b["ctas_per_solve"] == 2 and b["variant"] in (1, 2)
+    assert 1 <= b["max_resident_solves"] <= sms * 2 // 2
+    c = G.gato_query_launch(64, 4, variant=1, knots_per_cta=9)
+    assert c["ctas_per_solve"] == 8 and c["variant"] == 1
+    assert c["max_resident_solves"] <= sms // 8
+    d = G.gato_query_launch(64, 4, variant=2)
+    assert d["variant"] == 2 and d["smem_bytes"] == b["smem_bytes"]
+    # two CTAs per SM in the throughput form: at least as many resident solves
+    assert d["max_resident_solves"] >= G.gato_query_launch(64, 4, variant=1)["max_resident_solves"]
+    with pytest.raises(G.GatoError):
+        G.gato_query_launch(0, 1)
+    with pytest.raises(G.GatoError):
+        G.gato_query_launch(300, 1)
