@@ -246,10 +246,10 @@ def run_gpu(args):
 
 
 # DRAM bytes per launch of the dominant kernel on this workload (latency form,
-# 35 knots per CTA), from the ncu capture summarised in
-# profiles/sqp_fused_b256_n64_metrics.md: 17,962,240 read + 6,988,032 written.
+# 33 knots per CTA), from the ncu capture summarised in
+# profiles/sqp_fused_b256_n64_metrics.md: 17,408,768 read + 6,919,936 written.
 # Set to None when the kernel changes until it is measured again.
-TRAFFIC_BYTES = 24950272
+TRAFFIC_BYTES = 24328704
 
 
 def latency_runs(gato, I, torch, stream, flush, n_calls=200, launch_cfg=False):
@@ -438,7 +438,7 @@ def run_reference(args):
 
 def one_launch(B_n, N):
     """Profiling case: two warm-up solves and one solve of B_n figure-eight
-    problems (horizon N, 10 SQP iterations) in the latency form with 35 knots
+    problems (horizon N, 10 SQP iterations) in the latency form with 33 knots
     per CTA; profile the third launch (ncu -k regex:sqp_fused -s 2 -c 1)."""
     import torch
     from paper_2510_07625_gb300 import build, gato, inputs as I
