@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(NTHR, REG ? 1 : 2) sqp_fused(FusedLaunch a) {
   float* xs = red + 2 * RED_SLOTS * RED_W;
   float* vb = xs + 16;
   const int kpc = kpc_for(a.nmax, csize);
-  const int vstride = (kpc + 2) * VW;
+  const int vstride = (kpc + 4) * VW;  // knots k0-2 .. k1+1
   float* blocks = vb + NVEC * vstride;
   float* zblock = blocks + (3 * kpc + 1) * BS;  // 196 zeros (L_{N+1})
   float* ws = a.ws + (size_t)b * a.ws_stride;
@@ -186,20 +186,21 @@ __global__ void __launch_bounds__(NTHR, REG ? 1 : 2) sqp_fused(FusedLaunch a) {
   C.Lz = zblock;
   C.vb = vb;
   C.vstride = vstride;
-  C.vk0 = C.k0 - 1;
+  C.vk0 = C.k0 - 2;
   C.vbl = nullptr;
   C.vbr = nullptr;
   C.vk0l = C.vk0r = 0;
+  C.hrep = REG && csize > 1;
   if (csize > 1) {
     cg::cluster_group cl = cg::this_cluster();
     const int skpc = kpc_for(C.N, csize);
     if (rank > 0 && C.k0 > 0 && C.k0 < C.k1) {
       C.vbl = cl.map_shared_rank(vb, rank - 1);
-      C.vk0l = min((rank - 1) * skpc, C.N + 1) - 1;
+      C.vk0l = min((rank - 1) * skpc, C.N + 1) - 2;
     }
     if (rank < csize - 1 && C.k1 <= C.N && C.k0 < C.k1) {
       C.vbr = cl.map_shared_rank(vb, rank + 1);
-      C.vk0r = C.k1 - 1;
+      C.vk0r = C.k1 - 2;
     }
   }
   if (threadIdx.x < SCAL_FLOATS) scal[threadIdx.x] = 0.f;

@@ -68,6 +68,9 @@ struct Ctx {
   int vk0l;
   float* vbr;  // right neighbour's window or null
   int vk0r;
+  // PCG halo knots recomputed locally (fused latency form, clusters): the
+  // window then spans [k0-2, k1+1] and only w rows cross CTAs
+  bool hrep = false;
   // reductions: red[2][RED_SLOTS][RED_W] in this CTA's shared memory
   float* red;
   float* scal;
@@ -155,7 +158,7 @@ __host__ __device__ inline WsLayout ws_layout(int Nmax, bool global_blocks, bool
 // Shared-memory floats of one fused CTA owning at most `kpc` knots.
 __host__ __device__ inline size_t smem_floats(int kpc) {
   size_t f = 96 /*model*/ + SCAL_FLOATS + 2 * RED_SLOTS * RED_W + 16 /*xs*/;
-  f += NVEC * (size_t)(kpc + 2) * VW;
+  f += NVEC * (size_t)(kpc + 4) * VW;  // windows over knots k0-2 .. k1+1
   f += (size_t)(3 * kpc + 1) * BS + 196;  // blocks + a zero block
   return align32(f);
 }
@@ -810,15 +813,24 @@ struct RowRegs<true> {
   __device__ __forceinline__ float u0(int c) const { return U0[c]; }
   __device__ __forceinline__ float u1(int c) const { return U1[c]; }
   __device__ __forceinline__ void load(const Ctx& C, int k, int j, bool act) {
+    load_from(C.Lm, C.Pm, C.bk0, C.N, k, j, act, true);
+  }
+  // Rows of knot k from block arrays whose first block is knot bk0 (this
+  // CTA's or, through distributed shared memory, a neighbour's); lu = false
+  // leaves the L and L^T rows zero.
+  __device__ __forceinline__ void load_from(const float* Lm, const float* Pm, int bk0, int N, int k, int j,
+                                            bool act, bool lu) {
     const int i0 = j, i1 = j + QM;
+    const float* Lk = Lm + (k - bk0) * BS;
+    const float* Pk = Pm + (k - bk0) * BS;
 #pragma unroll
     for (int c = 0; c < XM; ++c) {
-      L0[c] = (act && k > 0) ? bL(C, k, i0, c) : 0.f;
-      L1[c] = (act && k > 0) ? bL(C, k, i1, c) : 0.f;
-      U0[c] = (act && k < C.N) ? bL(C, k + 1, c, i0) : 0.f;
-      U1[c] = (act && k < C.N) ? bL(C, k + 1, c, i1) : 0.f;
-      P0[c] = act ? bP(C, k, i0, c) : 0.f;
-      P1[c] = act ? bP(C, k, i1, c) : 0.f;
+      L0[c] = (act && lu && k > 0) ? Lk[c * XM + i0] : 0.f;
+      L1[c] = (act && lu && k > 0) ? Lk[c * XM + i1] : 0.f;
+      U0[c] = (act && lu && k < N) ? Lk[BS + i0 * XM + c] : 0.f;
+      U1[c] = (act && lu && k < N) ? Lk[BS + i1 * XM + c] : 0.f;
+      P0[c] = act ? Pk[c * XM + i0] : 0.f;
+      P1[c] = act ? Pk[c * XM + i1] : 0.f;
     }
   }
 };
@@ -923,8 +935,8 @@ __device__ __forceinline__ void cluster_df_sum3(float* red, int rank, int csize,
 // the iteration cap where standard PCG takes ~250 iterations.)  Three barriers
 // per iteration: the y halo (stair only), the u halo, the reduction.  Every
 // address and scalar the loop needs is set up before it.
-template <bool REG>
-__device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bool* hit_max, int& rbuf) {
+template <bool REG, bool HREP>
+__device__ inline int st_pcg_t(const Ctx& C, float eps, int maxit, int precond, bool* hit_max, int& rbuf) {
   const bool stair = (precond == 0);
   *hit_max = false;
   long long tlast = C.tm ? clock64() : 0;
@@ -935,15 +947,30 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
   // banks).  The last warp does no PCG arithmetic, only barriers and
   // reductions, so no SM sub-partition issues for three working warps.
   const int lane_ = threadIdx.x & 31, warp_ = threadIdx.x >> 5;
+  const int rank = C.rank, csize = C.csize;
   const bool pwarp = warp_ < NWARP - 1;
   const bool spare = lane_ >= 28;
   const bool lane_ok = pwarp && (!spare || warp_ == 0 || (warp_ == 1 && lane_ < 31));
+  // Halo knots (clusters, latency form): the last warp recomputes y for the
+  // neighbours' knots k0-2, k0-1, k1, k1+1 (lanes 7h..7h+6, h = 0..3) and t, u
+  // for k0-1 and k1, from the neighbours' block rows and their pushed w rows,
+  // with the same arithmetic as the owners, so the values are bitwise the
+  // owners'.  Then no y or u rows cross CTAs and the reduction's cluster
+  // barrier is the only one per iteration.
+  constexpr bool hrep = REG && HREP;
+  const bool hw = hrep && warp_ == NWARP - 1;
+  const int hs = lane_ / 7;
+  const int khalo = hs == 0 ? C.k0 - 2 : (hs == 1 ? C.k0 - 1 : (hs == 2 ? C.k1 : C.k1 + 1));
+  const bool hact = hw && lane_ < 28 && (hs < 2 ? rank > 0 : (rank < csize - 1 && khalo <= C.N));
+  const bool htu = hs == 1 || hs == 2;  // halo knots whose t and u are needed
   // rows j, j+7 with j in 0..6 for every lane (idle lanes use row 0), so that
   // all block and vector addresses stay inside their 14x14 blocks and rows
-  const int j = !lane_ok ? 0 : (spare ? lane_ - 28 + (warp_ == 1 ? 4 : 0) : lane_ - 7 * (lane_ / 7));
+  const int j = (lane_ok || (hw && lane_ < 28)) ? (spare ? lane_ - 28 + (warp_ == 1 ? 4 : 0) : lane_ - 7 * (lane_ / 7)) : 0;
   const int slot = spare ? 8 : 4 * warp_ + lane_ / 7 + (4 * warp_ + lane_ / 7 >= 8 ? 1 : 0);
-  const int k = C.k0 + slot;
-  const bool act = lane_ok && k < C.k1;
+  const int k = hw ? khalo : C.k0 + slot;
+  const bool act = lane_ok && k < C.k1;  // own knot
+  const bool acty = act || hact;         // y of this lane's knot is stored
+  const bool acttu = act || (hact && htu);
   RowRegs<REG> R;
   R.load(C, k, j, act);
   // zero every vector slot of the window (halos at the ends stay zero)
@@ -952,21 +979,26 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
     if (s != V_RHS) C.vb[i] = 0.f;
   }
   float* const red = C.red;
-  const int rank = C.rank, csize = C.csize;
-  const int ka = act ? k : C.k0;  // a valid knot for the address set-up of idle lanes
+  const int ka = acty ? k : C.k0;  // a valid knot for the address set-up of idle lanes
+  const int kd = act ? k : C.k0;
   const int vstr = C.vstride;
   float* const wb = vec(C, 0, ka);  // slot s of this knot at wb + s * vstr
 #define SLOT(s) (wb + (s) * vstr)
   // neighbour window of this knot's rows (slot s at pb + s * vstr), boundary knots only
-  float* pb = nullptr;
-  if (act && C.vbl && k == C.k0) pb = C.vbl + (k - C.vk0l) * VW;
-  if (act && C.vbr && k == C.k1 - 1) pb = C.vbr + (k - C.vk0r) * VW;
+  float* pbd = nullptr;
+  if (act && C.vbl && k == C.k0) pbd = C.vbl + (k - C.vk0l) * VW;
+  if (act && C.vbr && k == C.k1 - 1) pbd = C.vbr + (k - C.vk0r) * VW;
+  float* const pb = hrep ? nullptr : pbd;  // y and u rows cross CTAs only without halo knots
+  // with halo knots: w rows of the first two and last two knots go to the
+  // neighbours' halo slots (V_P0 + iteration parity)
+  float* const pwl = (hrep && act && C.vbl && k <= C.k0 + 1) ? C.vbl + (k - C.vk0l) * VW : nullptr;
+  float* const pwr = (hrep && act && C.vbr && k >= C.k1 - 2) ? C.vbr + (k - C.vk0r) * VW : nullptr;
 #define PUSH(s, a, b)                     \
   if (pb) {                               \
     pb[(s) * vstr + J] = (a);             \
     pb[(s) * vstr + J7] = (b);            \
   }
-  const float* const Drow0 = &bD(C, ka, j, 0);  // D_k row j: element c at Drow0[c * XM]
+  const float* const Drow0 = &bD(C, kd, j, 0);  // D_k row j: element c at Drow0[c * XM]
   float* const rr = SLOT(V_RR);
   float* const yv = SLOT(V_Y);
   float* const uv = SLOT(V_Z);
@@ -980,6 +1012,22 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
     rr[J] = SLOT(V_RHS)[J];
     rr[J7] = SLOT(V_RHS)[J7];
   }
+  if constexpr (REG) {
+    if (hw) {
+      // the halo knot's rows and right-hand side, from the neighbour that owns it
+      // (its blocks and window are final: the barrier above)
+      cg::cluster_group cl = cg::this_cluster();
+      const int nb = hs < 2 ? rank - 1 : rank + 1;
+      const int nk0 = hs < 2 ? C.k0 - kpc_for(C.N, csize) : C.k1;  // the neighbour's first knot
+      const int nbs = hact ? nb : rank;
+      R.load_from(cl.map_shared_rank(C.Lm, nbs), cl.map_shared_rank(C.Pm, nbs), nk0, C.N, k, j, hact, htu);
+      if (hact) {
+        const float* rhs = cl.map_shared_rank(C.vb, nb) + V_RHS * vstr + (k - (nk0 - 2)) * VW;
+        rr[J] = rhs[J];
+        rr[J7] = rhs[J7];
+      }
+    }
+  }
   int it = 0;
   float gamma = 0.f, gamma0 = 0.f, alpha = 0.f, inv_gamma = 0.f, psp = 0.f;
   const float eps2 = eps * eps;
@@ -989,7 +1037,7 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
     // the warp never branches on act; only their stores are predicated off.
     // (Block barrier: knot slot 8's rows span warps 0 and 1.)
     __syncthreads();
-    if (pwarp) {
+    if (pwarp || hw) {
       float y0 = 0.f, y1 = 0.f;
 #pragma unroll
       for (int m = 0; m < XM / 2; ++m) {
@@ -1002,16 +1050,16 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
       u0 = y0;
       u1 = y1;
       float* const dst = stair ? yv : uv;
-      if (act) {
+      if (acty) {
         dst[J] = y0;
         dst[J7] = y1;
       }
       PUSH(stair ? V_Y : V_Z, y0, y1);
     }
     if (stair) {
-      if (csize > 1) cg::this_cluster().sync(); else __syncthreads();
+      if (csize > 1 && !hrep) cg::this_cluster().sync(); else __syncthreads();
       tstamp(C, T_PCG_Y, tlast);
-      if (pwarp) {
+      if (pwarp || hw) {
         float t0 = 0.f, t1 = 0.f;
 #pragma unroll
         for (int m = 0; m < XM / 2; ++m) {
@@ -1026,13 +1074,13 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
             t1 += R.u1(c) * b;
           }
         }
-        if (act) {
+        if (acttu) {
           tv[J] = t0;
           tv[J7] = t1;
         }
       }
       __syncthreads();
-      if (pwarp) {
+      if (pwarp || hw) {
         float q0 = 0.f, q1 = 0.f;
 #pragma unroll
         for (int m = 0; m < XM / 2; ++m) {
@@ -1044,14 +1092,14 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
         }
         u0 -= q0;
         u1 -= q1;
-        if (act) {
+        if (acttu) {
           uv[J] = u0;
           uv[J7] = u1;
         }
         PUSH(V_Z, u0, u1);
       }
     }
-    if (csize > 1) cg::this_cluster().sync(); else __syncthreads();
+    if (csize > 1 && !hrep) cg::this_cluster().sync(); else __syncthreads();
     // w = S u
     DF ru = df_zero(), wu = df_zero(), pw = df_zero();
     if (pwarp) {
@@ -1075,6 +1123,15 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
       }
       w0 = a0;
       w1 = a1;
+      const int wsl = (V_P0 + (it & 1)) * vstr;  // the neighbours' halo w slot of this iteration
+      if (pwl) {
+        pwl[wsl + J] = w0;
+        pwl[wsl + J7] = w1;
+      }
+      if (pwr) {
+        pwr[wsl + J] = w0;
+        pwr[wsl + J7] = w1;
+      }
       const DF ru1 = df_fma(df_fma(ru, rr[J], u0), rr[J7], u1);
       const DF wu1 = df_fma(df_fma(wu, w0, u0), w1, u1);
       const DF pw1 = df_fma(df_fma(pw, p0, w0), p1, w1);  // p still holds the previous direction
@@ -1107,7 +1164,13 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
     alpha = gnew / psp;
     gamma = gnew;
     inv_gamma = 1.f / gnew;
-    // p = u + beta p; s = w + beta s; dnu += alpha p; r -= alpha s
+    if (hw) {  // the owner's w rows of this halo knot, pushed before the reduction
+      const float* wh = SLOT(V_P0 + (it & 1));
+      w0 = wh[J];
+      w1 = wh[J7];
+    }
+    // p = u + beta p; s = w + beta s; dnu += alpha p; r -= alpha s (halo
+    // knots: s and r only, the same expressions as their owners')
     p0 = u0 + beta * p0;
     p1 = u1 + beta * p1;
     s0 = w0 + beta * s0;
@@ -1118,6 +1181,8 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
       if (act) {
         dn[J] = d0;
         dn[J7] = d1;
+      }
+      if (acty) {
         rr[J] = r0;
         rr[J7] = r1;
       }
@@ -1125,13 +1190,25 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
     ++it;
   }
   // the correction's boundary rows go to the neighbours for the recovery
-  if (act) {
-    PUSH(V_DNU, dn[J], dn[J7]);
+  if (act && pbd) {
+    pbd[V_DNU * vstr + J] = dn[J];
+    pbd[V_DNU * vstr + J7] = dn[J7];
   }
   if (csize > 1) cg::this_cluster().sync(); else __syncthreads();
   return it;
 #undef PUSH
 #undef SLOT
+}
+
+// The loop with halo knots (C.hrep: fused latency form in a cluster) and
+// without are separate instantiations, so the one-CTA loop carries none of
+// the halo logic.
+template <bool REG>
+__device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bool* hit_max, int& rbuf) {
+  if constexpr (REG) {
+    if (C.hrep) return st_pcg_t<true, true>(C, eps, maxit, precond, hit_max, rbuf);
+  }
+  return st_pcg_t<REG, false>(C, eps, maxit, precond, hit_max, rbuf);
 }
 
 // ------------------------------------------------- stage 4: step recovery
