@@ -141,3 +141,25 @@ def test_query_launch_shapes(G):
         G.gato_query_launch(0, 1)
     with pytest.raises(G.GatoError):
         G.gato_query_launch(300, 1)
+
+
+# (N, uniform cluster) -> CTA knot counts: (9, 4) -> 3,3,3,1; (7, 4) -> 2,2,2,2;
+# (6, 3) -> 3,3,1; (24, 8) -> 4 x 6, 1; (64, 8) -> 9 x 7, 2; (64, 2) -> 33, 32
+HALO_CASES = [(9, 4), (7, 4), (6, 3), (24, 8), (64, 8), (64, 2)]
+
+
+@pytest.mark.parametrize("precond", [0, 1], ids=["stair", "jacobi"])
+@pytest.mark.parametrize("N,cl", HALO_CASES, ids=[f"N{n}-C{c}" for n, c in HALO_CASES])
+def test_halo_recompute_equals_pushed_halos_bitwise(G, N, cl, precond):
+    # The latency form recomputes the neighbours' halo knots inside each CTA;
+    # the throughput form exchanges y and u rows through distributed shared
+    # memory.  Both must give the same bits, including CTAs with one or two
+    # knots (whose halo knots reach the neighbour's first or last knot).
+    probs = [I.ee_problem(7, I.arm7(), N), I.joint_problem(8, I.arm7(), N, 0.01),
+             I.joint_problem(9, I.arm6(), N, 0.01)]
+    a = gpu_solve(G, probs, 3, launch=(1, 0, cl), precond=precond)
+    b = gpu_solve(G, probs, 3, launch=(2, 0, cl), precond=precond)
+    for x, y in zip(a, b):
+        for k in ("X", "U", "lam"):
+            np.testing.assert_array_equal(x[k], y[k])
+        assert (x["flags"], x["sqp_iters"], x["pcg_iters"]) == (y["flags"], y["sqp_iters"], y["pcg_iters"])
