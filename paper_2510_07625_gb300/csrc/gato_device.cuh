@@ -399,7 +399,8 @@ __device__ __forceinline__ void mass_matrix_crba(const DevModel& M, const float*
     mc += m;
     const int ai = M.axis[i];
     const V3 e = unitv(ai);
-    V3 n = V3{J[3 * 0 + ai], J[3 * 1 + ai], J[3 * 2 + ai]};  // J e_i
+    // J e_i, column picked by selects (a runtime index would move J to local memory)
+    V3 n = ai == 0 ? V3{J[0], J[3], J[6]} : (ai == 1 ? V3{J[1], J[4], J[7]} : V3{J[2], J[5], J[8]});
     V3 f = cross(e, h);
     Ml[i * (i + 1) / 2 + i] = comp(ai, n);
 #pragma unroll
