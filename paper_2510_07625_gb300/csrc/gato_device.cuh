@@ -321,26 +321,6 @@ __device__ __forceinline__ void rnea_tangent(const DevModel& M, const LinkRec* R
   }
 }
 
-// Lower-triangular mass matrix by unit-acceleration RNEA columns (gravity and
-// velocity off); padded joints get a unit diagonal.  Ml[i*(i+1)/2 + j], j <= i.
-__device__ __forceinline__ void mass_matrix_lower(const DevModel& M, const float* sq,
-                                                  const float* cq, float* Ml) {
-  float z[QM], e[QM], col[QM];
-#pragma unroll
-  for (int i = 0; i < QM; ++i) z[i] = 0.f;
-#pragma unroll
-  for (int j = 0; j < QM; ++j) {
-#pragma unroll
-    for (int i = 0; i < QM; ++i) e[i] = (i == j) ? 1.f : 0.f;
-    rnea_value(M, sq, cq, z, e, 0.f, col, nullptr);
-#pragma unroll
-    for (int i = j; i < QM; ++i) Ml[i * (i + 1) / 2 + j] = col[i];
-  }
-#pragma unroll
-  for (int j = 0; j < QM; ++j)
-    if (j >= M.dof) Ml[j * (j + 1) / 2 + j] = 1.f;
-}
-
 // Lower-triangular mass matrix by composite rigid bodies, for the per-thread
 // forward dynamics of the line search.  From the tip, the composite of links
 // i..n (rotational inertia J about joint i's origin, first moment h about it,

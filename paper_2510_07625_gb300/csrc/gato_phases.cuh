@@ -184,21 +184,6 @@ __device__ __forceinline__ float* vec(const Ctx& C, int s, int k) {
   return C.vb + s * C.vstride + (k - C.vk0) * VW;
 }
 
-// After the owner of knot k wrote rows j, j+7 of slot s, copy them into the
-// halo of the neighbour CTA that reads knot k.
-__device__ __forceinline__ void push_rows(const Ctx& C, int s, int k, int j, float v0, float v1) {
-  if (C.vbl && k == C.k0) {
-    float* d = C.vbl + s * C.vstride + (k - C.vk0l) * VW;
-    d[j] = v0;
-    d[j + QM] = v1;
-  }
-  if (C.vbr && k == C.k1 - 1) {
-    float* d = C.vbr + s * C.vstride + (k - C.vk0r) * VW;
-    d[j] = v0;
-    d[j + QM] = v1;
-  }
-}
-
 __device__ __forceinline__ void csync(const Ctx& C) {
   if (C.csize > 1)
     cg::this_cluster().sync();
@@ -1029,7 +1014,7 @@ __device__ inline int st_pcg_t(const Ctx& C, float eps, int maxit, int precond, 
     }
   }
   int it = 0;
-  float gamma = 0.f, gamma0 = 0.f, alpha = 0.f, inv_gamma = 0.f, psp = 0.f;
+  float gamma0 = 0.f, alpha = 0.f, inv_gamma = 0.f, psp = 0.f;
   const float eps2 = eps * eps;
   while (true) {
     // u = Phi r: y = D^-1 r; u = y - D^-1 (O y).  Idle lanes (act false) run
@@ -1162,7 +1147,6 @@ __device__ inline int st_pcg_t(const Ctx& C, float eps, int maxit, int precond, 
       psp = wu_f + beta * (2.f * pw_f + beta * psp);
     }
     alpha = gnew / psp;
-    gamma = gnew;
     inv_gamma = 1.f / gnew;
     if (hw) {  // the owner's w rows of this halo knot, pushed before the reduction
       const float* wh = SLOT(V_P0 + (it & 1));
