@@ -391,19 +391,20 @@ __device__ inline void st_mass_bias(const Ctx& C) {
 }
 
 // Cholesky of M, explicit M^-1, qdd = M^-1 (u - bias), dynamics defects.
+// One (knot, right-hand side) per thread: column c < 7 of M^-1 or, for c = 7,
+// qdd and the defects; every thread of a knot factors M_k itself (the same
+// bits), so the eight triangular solves run side by side.
 __device__ inline void st_forward_dynamics(const Ctx& C) {
   const int N = C.N;
   const int ke = C.k1 < N ? C.k1 : N;
   const float h = C.h;
-  const int items = (ke - C.k0) + (C.k0 == 0 ? 1 : 0);
-  for (int it = threadIdx.x; it < items; it += NTHR) {
-    if (it == ke - C.k0) {  // c_0 = x_s - x_0, by the CTA owning knot 0
-#pragma unroll
-      for (int i = 0; i < XM; ++i) C.cv[i] = C.xs[i] - C.X[i];
-      continue;
-    }
-    const int k = C.k0 + it;
-    float Ml[28];
+  const int nk = ke - C.k0;  // 8 * nk + 1 <= 8 * KPC_MAX + 1 < NTHR: one round
+  static_assert(8 * KPC_MAX + 1 <= NTHR, "one (knot, column) per thread");
+  const int it = threadIdx.x;
+  const int k = C.k0 + (it >> 3), col = it & 7;
+  const bool act = it < 8 * nk;
+  float Ml[28];
+  if (act) {
 #pragma unroll
     for (int i = 0; i < QM; ++i)
 #pragma unroll
@@ -412,30 +413,38 @@ __device__ inline void st_forward_dynamics(const Ctx& C) {
 #pragma unroll
     for (int i = 0; i < QM; ++i)
       if (i >= C.dof) Ml[i * (i + 1) / 2 + i] = 1.f;
-    if (!chol7(Ml)) flag_nonfinite(C);
-    float b[QM];
+  }
+  __syncthreads();  // every M_k is read before a column of M_k^-1 overwrites it
+  if (act) {
+    const bool ok = chol7(Ml);
+    if (col == 7) {
+      if (!ok) flag_nonfinite(C);
+      float b[QM];
 #pragma unroll
-    for (int i = 0; i < QM; ++i) b[i] = C.U[k * US + i] - C.qdd[k * US + i];
-    chol7_solve(Ml, b);
-    const float* x = C.X + k * VS;
-    const float* xn = C.X + (k + 1) * VS;
+      for (int i = 0; i < QM; ++i) b[i] = C.U[k * US + i] - C.qdd[k * US + i];
+      chol7_solve(Ml, b);
+      const float* x = C.X + k * VS;
+      const float* xn = C.X + (k + 1) * VS;
 #pragma unroll
-    for (int i = 0; i < QM; ++i) {
-      C.qdd[k * US + i] = b[i];
-      const float qdn = x[QM + i] + h * b[i];
-      const float qn = x[i] + h * qdn;
-      C.cv[(k + 1) * VS + i] = qn - xn[i];
-      C.cv[(k + 1) * VS + QM + i] = qdn - xn[QM + i];
-    }
-#pragma unroll
-    for (int j2 = 0; j2 < QM; ++j2) {
+      for (int i = 0; i < QM; ++i) {
+        C.qdd[k * US + i] = b[i];
+        const float qdn = x[QM + i] + h * b[i];
+        const float qn = x[i] + h * qdn;
+        C.cv[(k + 1) * VS + i] = qn - xn[i];
+        C.cv[(k + 1) * VS + QM + i] = qdn - xn[QM + i];
+      }
+    } else {
       float e[QM];
 #pragma unroll
-      for (int i = 0; i < QM; ++i) e[i] = (i == j2) ? 1.f : 0.f;
+      for (int i = 0; i < QM; ++i) e[i] = (i == col) ? 1.f : 0.f;
       chol7_solve(Ml, e);
 #pragma unroll
-      for (int i = 0; i < QM; ++i) C.Mi[k * FQS + i * QM + j2] = e[i];
+      for (int i = 0; i < QM; ++i) C.Mi[k * FQS + i * QM + col] = e[i];
     }
+  }
+  if (it == 8 * nk && C.k0 == 0) {  // c_0 = x_s - x_0, by the CTA owning knot 0
+#pragma unroll
+    for (int i = 0; i < XM; ++i) C.cv[i] = C.xs[i] - C.X[i];
   }
 }
 
@@ -540,18 +549,25 @@ __device__ inline void st_tangents(const Ctx& C) {
   }
 }
 
-// dqdd/dq = -M^-1 dID/dq, dqdd/dqd = -M^-1 dID/dqd.
+// dqdd/dq = -M^-1 dID/dq, dqdd/dqd = -M^-1 dID/dqd: one (knot, which, row r)
+// per thread, the seven entries of row r from one read of M^-1's row.
 __device__ inline void st_dyn_jacobians(const Ctx& C) {
   const int ke = C.k1 < C.N ? C.k1 : C.N;
-  for (int it = threadIdx.x; it < (ke - C.k0) * 98; it += NTHR) {
-    const int k = C.k0 + it / 98, e = it % 98;
-    const int which = e / 49, r = (e % 49) / QM, c = e % QM;
-    const float* Mi = C.Mi + k * FQS + r * QM;
-    const float* col = C.dT + k * DTS + (which * QM + c) * 8;
-    float a = 0.f;
+  for (int it = threadIdx.x; it < (ke - C.k0) * 14; it += NTHR) {
+    const int k = C.k0 + it / 14, e = it % 14;
+    const int which = e / QM, r = e % QM;
+    float mrow[QM];
 #pragma unroll
-    for (int l = 0; l < QM; ++l) a += Mi[l] * col[l];
-    (which ? C.Fv : C.Fq)[k * FQS + r * QM + c] = -a;
+    for (int l = 0; l < QM; ++l) mrow[l] = C.Mi[k * FQS + r * QM + l];
+    float* out = (which ? C.Fv : C.Fq) + k * FQS + r * QM;
+#pragma unroll
+    for (int c = 0; c < QM; ++c) {
+      const float* col = C.dT + k * DTS + (which * QM + c) * 8;
+      float a = 0.f;
+#pragma unroll
+      for (int l = 0; l < QM; ++l) a += mrow[l] * col[l];
+      out[c] = -a;
+    }
   }
 }
 
