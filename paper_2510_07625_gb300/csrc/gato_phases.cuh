@@ -952,23 +952,35 @@ __device__ inline int st_pcg_t(const Ctx& C, float eps, int maxit, int precond, 
   const bool pwarp = warp_ < NWARP - 1;
   const bool spare = lane_ >= 28;
   const bool lane_ok = pwarp && (!spare || warp_ == 0 || (warp_ == 1 && lane_ < 31));
-  // Halo knots (clusters, latency form): the last warp recomputes y for the
-  // neighbours' knots k0-2, k0-1, k1, k1+1 (lanes 7h..7h+6, h = 0..3) and t, u
-  // for k0-1 and k1, from the neighbours' block rows and their pushed w rows,
-  // with the same arithmetic as the owners, so the values are bitwise the
-  // owners'.  Then no y or u rows cross CTAs and the reduction's cluster
-  // barrier is the only one per iteration.
+  // Halo knots (clusters, latency form): y of the neighbours' knots k0-2,
+  // k0-1, k1, k1+1 and t, u of k0-1 and k1 are recomputed here from the
+  // neighbours' block rows and their pushed w rows, with the same arithmetic
+  // as the owners, so the values are bitwise the owners'.  Then no y or u
+  // rows cross CTAs and the reduction's cluster barrier is the only one per
+  // iteration.  The CTA's halo knots, in the order k0-2, k0-1, k1, k1+1 (the
+  // ones that exist), take halo slots 0..3: slot h < 3 on the spare lanes
+  // 28-31 of warp 2h+2 (rows 0-3) and 28-30 of warp 2h+3 (rows 4-6), slot 3
+  // on lanes 0-6 of the last warp.  A CTA with one neighbour (both CTAs of a
+  // two-CTA cluster) has two halo knots on spare lanes of warps that issue
+  // their own knots' instructions anyway, and its last warp stays idle.
   constexpr bool hrep = REG && HREP;
-  const bool hw = hrep && warp_ == NWARP - 1;
-  const int hs = lane_ / 7;
+  const bool hasL = rank > 0, hasR1 = rank < csize - 1 && C.k1 <= C.N, hasR2 = hasR1 && C.k1 + 1 <= C.N;
+  const int hslot = !hrep ? -1
+                    : (warp_ >= 2 && warp_ < NWARP - 1 && lane_ >= 28 && !((warp_ & 1) && lane_ == 31))
+                          ? (warp_ - 2) / 2
+                          : (warp_ == NWARP - 1 && lane_ < 7 ? 3 : -1);
+  const int hs = hasL ? hslot : hslot + 2;  // 0: k0-2, 1: k0-1, 2: k1, 3: k1+1
+  const bool hact = hslot >= 0 && hs <= 3 && (hs < 2 ? hasL : (hs == 2 ? hasR1 : hasR2));
   const int khalo = hs == 0 ? C.k0 - 2 : (hs == 1 ? C.k0 - 1 : (hs == 2 ? C.k1 : C.k1 + 1));
-  const bool hact = hw && lane_ < 28 && (hs < 2 ? rank > 0 : (rank < csize - 1 && khalo <= C.N));
   const bool htu = hs == 1 || hs == 2;  // halo knots whose t and u are needed
+  const bool hw = hrep && warp_ == NWARP - 1 && hasL && hasR2;  // the last warp carries slot 3
   // rows j, j+7 with j in 0..6 for every lane (idle lanes use row 0), so that
   // all block and vector addresses stay inside their 14x14 blocks and rows
-  const int j = (lane_ok || (hw && lane_ < 28)) ? (spare ? lane_ - 28 + (warp_ == 1 ? 4 : 0) : lane_ - 7 * (lane_ / 7)) : 0;
+  const int hrow = warp_ == NWARP - 1 ? lane_ : lane_ - 28 + ((warp_ & 1) ? 4 : 0);
+  const int j = lane_ok ? (spare ? lane_ - 28 + (warp_ == 1 ? 4 : 0) : lane_ - 7 * (lane_ / 7))
+                        : (hslot >= 0 ? hrow : 0);
   const int slot = spare ? 8 : 4 * warp_ + lane_ / 7 + (4 * warp_ + lane_ / 7 >= 8 ? 1 : 0);
-  const int k = hw ? khalo : C.k0 + slot;
+  const int k = hslot >= 0 ? khalo : C.k0 + slot;
   const bool act = lane_ok && k < C.k1;  // own knot
   const bool acty = act || hact;         // y of this lane's knot is stored
   const bool acttu = act || (hact && htu);
@@ -1014,7 +1026,7 @@ __device__ inline int st_pcg_t(const Ctx& C, float eps, int maxit, int precond, 
     rr[J7] = SLOT(V_RHS)[J7];
   }
   if constexpr (REG) {
-    if (hw) {
+    if (hslot >= 0) {
       // the halo knot's rows and right-hand side, from the neighbour that owns it
       // (its blocks and window are final: the barrier above)
       cg::cluster_group cl = cg::this_cluster();
@@ -1164,7 +1176,7 @@ __device__ inline int st_pcg_t(const Ctx& C, float eps, int maxit, int precond, 
     }
     alpha = gnew / psp;
     inv_gamma = 1.f / gnew;
-    if (hw) {  // the owner's w rows of this halo knot, pushed before the reduction
+    if (hslot >= 0) {  // the owner's w rows of this halo knot, pushed before the reduction
       const float* wh = SLOT(V_P0 + (it & 1));
       w0 = wh[J];
       w1 = wh[J7];
