@@ -949,7 +949,11 @@ __device__ inline int st_pcg_t(const Ctx& C, float eps, int maxit, int precond, 
   // reductions, so no SM sub-partition issues for three working warps.
   const int lane_ = threadIdx.x & 31, warp_ = threadIdx.x >> 5;
   const int rank = C.rank, csize = C.csize;
-  const bool pwarp = warp_ < NWARP - 1;
+  // warps 0..wown-1 hold own knots (slots 0-7 on warps 0-1, slot 8 on their
+  // spare lanes, slot s > 8 on warp (s-1)/4); the others skip the arithmetic
+  const int nown = C.k1 - C.k0;
+  const int wown = nown <= 8 ? (nown + 3) / 4 : (nown == 9 ? 2 : (nown - 2) / 4 + 1);
+  const bool pwarp = warp_ < wown;
   const bool spare = lane_ >= 28;
   const bool lane_ok = pwarp && (!spare || warp_ == 0 || (warp_ == 1 && lane_ < 31));
   // Halo knots (clusters, latency form): y of the neighbours' knots k0-2,
@@ -958,14 +962,19 @@ __device__ inline int st_pcg_t(const Ctx& C, float eps, int maxit, int precond, 
   // as the owners, so the values are bitwise the owners'.  Then no y or u
   // rows cross CTAs and the reduction's cluster barrier is the only one per
   // iteration.  The CTA's halo knots, in the order k0-2, k0-1, k1, k1+1 (the
-  // ones that exist), take halo slots 0..3: slot h < 3 on the spare lanes
-  // 28-31 of warp 2h+2 (rows 0-3) and 28-30 of warp 2h+3 (rows 4-6), slot 3
-  // on lanes 0-6 of the last warp.  A CTA with one neighbour (both CTAs of a
-  // two-CTA cluster) has two halo knots on spare lanes of warps that issue
-  // their own knots' instructions anyway, and its last warp stays idle.
+  // ones that exist), take halo slots 0..3.  If a warp below the last has no
+  // own knots (compact: at most 29 own knots), slot h sits on its lanes
+  // 7h..7h+6.  Otherwise slot h < 3 sits on the spare lanes 28-31 of warp
+  // 2h+2 (rows 0-3) and 28-30 of warp 2h+3 (rows 4-6), slot 3 on lanes 0-6 of
+  // the last warp: a CTA with one neighbour (both CTAs of a two-CTA cluster)
+  // has two halo knots on spare lanes of warps that issue their own knots'
+  // instructions anyway.  Either way no SM sub-partition issues for three
+  // warps unless a middle CTA holds 30 or more knots.
   constexpr bool hrep = REG && HREP;
   const bool hasL = rank > 0, hasR1 = rank < csize - 1 && C.k1 <= C.N, hasR2 = hasR1 && C.k1 + 1 <= C.N;
+  const bool compact = wown < NWARP - 1;
   const int hslot = !hrep ? -1
+                    : compact ? (warp_ == wown && lane_ < 28 ? lane_ / 7 : -1)
                     : (warp_ >= 2 && warp_ < NWARP - 1 && lane_ >= 28 && !((warp_ & 1) && lane_ == 31))
                           ? (warp_ - 2) / 2
                           : (warp_ == NWARP - 1 && lane_ < 7 ? 3 : -1);
@@ -973,10 +982,12 @@ __device__ inline int st_pcg_t(const Ctx& C, float eps, int maxit, int precond, 
   const bool hact = hslot >= 0 && hs <= 3 && (hs < 2 ? hasL : (hs == 2 ? hasR1 : hasR2));
   const int khalo = hs == 0 ? C.k0 - 2 : (hs == 1 ? C.k0 - 1 : (hs == 2 ? C.k1 : C.k1 + 1));
   const bool htu = hs == 1 || hs == 2;  // halo knots whose t and u are needed
-  const bool hw = hrep && warp_ == NWARP - 1 && hasL && hasR2;  // the last warp carries slot 3
+  // a warp whose lanes carry halo knots only
+  const bool hw = hrep && (compact ? warp_ == wown : (warp_ == NWARP - 1 && hasL && hasR2));
   // rows j, j+7 with j in 0..6 for every lane (idle lanes use row 0), so that
   // all block and vector addresses stay inside their 14x14 blocks and rows
-  const int hrow = warp_ == NWARP - 1 ? lane_ : lane_ - 28 + ((warp_ & 1) ? 4 : 0);
+  const int hrow = compact ? lane_ - 7 * (lane_ / 7)
+                            : (warp_ == NWARP - 1 ? lane_ : lane_ - 28 + ((warp_ & 1) ? 4 : 0));
   const int j = lane_ok ? (spare ? lane_ - 28 + (warp_ == 1 ? 4 : 0) : lane_ - 7 * (lane_ / 7))
                         : (hslot >= 0 ? hrow : 0);
   const int slot = spare ? 8 : 4 * warp_ + lane_ / 7 + (4 * warp_ + lane_ / 7 >= 8 ? 1 : 0);
