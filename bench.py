@@ -247,9 +247,9 @@ def run_gpu(args):
 
 # DRAM bytes per launch of the dominant kernel on this workload (latency form,
 # 33 knots per CTA), from the ncu capture summarised in
-# profiles/sqp_fused_b256_n64_metrics.md: 17,231,872 read + 6,626,048 written.
+# profiles/sqp_fused_b256_n64_metrics.md: 17,303,296 read + 6,251,264 written.
 # Set to None when the kernel changes until it is measured again.
-TRAFFIC_BYTES = 23857920
+TRAFFIC_BYTES = 23554560
 
 
 def latency_runs(gato, I, torch, stream, flush, n_calls=200, launch_cfg=False):

@@ -178,9 +178,10 @@ gato_status gato_solve_noalloc(const gato_model_desc* models, int32_t n_models,
                                gato_result* results, void* cuda_stream);
 
 /* ---- launch configuration and autotuning (Sec. III's M-block mapping made tunable) ----
- * How solves map onto the GPU.  variant: 0 automatic, 1 the latency form (the
- * PCG's block rows held in registers, one CTA per SM), 2 the throughput form
- * (off-diagonal rows read from shared memory, two CTAs per SM).
+ * How solves map onto the GPU.  variant: 0 automatic (the latency form), 1 the
+ * latency form (the PCG's block rows held in registers, one CTA per SM), 2 the
+ * throughput form (off-diagonal rows read from shared memory, two CTAs per SM
+ * when the shared memory fits).
  * knots_per_cta: 0 = 33 (the most one CTA holds), 2..33 spreads each solve
  * over more CTAs.  cluster: 0 = per solve, 1..8 = every solve uses this many
  * CTAs where its horizon allows (a uniform batch is then a single launch).

@@ -117,11 +117,13 @@ cudaError_t fused_active_clusters(int nmax, int csize, bool reg, int* out) {
 }
 
 bool use_throughput_variant(int n, int csize, int variant, size_t smem) {
-  if (variant == 1) return false;
-  if (variant == 2) return true;
-  // more CTAs than one per SM, and two of them fit an SM's shared memory
-  // (228 KB, 1 KB reserved per CTA): two CTAs per SM halve the waves
-  return (long long)n * csize > num_sms() && 2 * (smem + 1024) <= 233472;
+  (void)n;
+  (void)csize;
+  (void)smem;
+  // automatic = the latency form: with the halo knots recomputed in the
+  // cluster it is faster than two CTAs per SM at every batch size and horizon
+  // measured (B 1..256, N 32..128); the throughput form is kept on request
+  return variant == 2;
 }
 
 cudaError_t launch_fused(const FusedLaunch& a, cudaStream_t s) {
