@@ -5,10 +5,11 @@ B=256 end-effector tracking solves, N=64 knots, dt=0.01 s, 10 SQP iterations
 per solve call, FP32 with compensated PCG dots and merit sums.  A "step" is one
 gato_solve call over the whole batch from the cold start.  Extra keys report
 the p50/p99 latency of the B=32 call (10 and 3 SQP iterations), the plain
-one-solve-per-launch GPU form at B=32, the uneven mix (128 solves, N in
-16..128, two arms, per-solve stop at KKT 1e-5 or 20 iterations) replayed from a
-CUDA graph, and the serving loop under Poisson arrivals (1k-20k ticks/s over
-128 resident sessions of that mix, 3 SQP iterations per tick).
+one-solve-per-launch GPU form at B=32 and B=256, the uneven mix (128 solves, N
+in 16..128, two arms, per-solve stop at KKT 1e-5 or 20 iterations) replayed
+from a CUDA graph, and the serving loop under Poisson arrivals (1k, 2k, 5k, 10k
+and 20k ticks/s over 128 resident sessions of that mix, 3 SQP iterations per
+tick, each rate for 10 s or 50k requests, whichever comes first).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -70,7 +71,7 @@ def whole_job_rate(ws, solves_per_rank, steps, t_max):
 # --------------------------------------------------------------- FLOP model
 
 def flops_per_solve(N, sqp_iters, pcg_iters, n_alpha=8, ee=True):
-    """Algorithmic FP32 FLOPs of one solve (counts of the stage formulas).
+    """Algorithmic FP32 FLOPs of one solve (operation counts of the stage formulas).
 
     Per knot and SQP iteration: dynamics + Jacobians 45.0 kFLOP, cost 0.1 kFLOP
     (joint) / 1.6 kFLOP (end effector), KKT residual 0.6, Schur blocks 14.5,
@@ -334,8 +335,10 @@ def uneven_graph(gato, I, torch, reps=10):
             "converged": conv, "sqp_iters_mean": round(sum(iters) / len(iters), 2), "sqp_iters_max": max(iters)}
 
 
-def serving_runs(gato, I, rates=(1000.0, 5000.0, 20000.0), duration_s=1.0):
-    """Serving loop: Poisson ticks over 128 resident sessions of the uneven mix."""
+def serving_runs(gato, I, rates=(1000.0, 2000.0, 5000.0, 10000.0, 20000.0), duration_s=10.0,
+                 max_requests=50000):
+    """Serving loop: Poisson ticks over 128 resident sessions of the uneven mix,
+    each rate for 10 s or 50k requests, whichever comes first."""
     from paper_2510_07625_gb300 import serving
 
     probs = I.config_uneven(128)
@@ -349,7 +352,8 @@ def serving_runs(gato, I, rates=(1000.0, 5000.0, 20000.0), duration_s=1.0):
            "capacity": srv.stats()["capacity"]}
     runs = []
     for rate in rates:
-        r, _ = serving.poisson_load(srv, sids, probs, rate, duration_s, seed=int(rate))
+        r, _ = serving.poisson_load(srv, sids, probs, rate, duration_s, seed=int(rate),
+                                    max_requests=max_requests)
         runs.append(r)
     out["runs"] = runs
     srv.close()

@@ -106,14 +106,16 @@ class _HostProblem:
         self.arr = a
 
 
-def poisson_load(server: Server, sids, probs, rate, duration_s, seed=12345, sigma_q=0.05, sigma_qd=0.1):
-    """Poisson ticks at `rate` requests/s over the open sessions `sids`.
+def poisson_load(server: Server, sids, probs, rate, duration_s, seed=12345, sigma_q=0.05, sigma_qd=0.1,
+                 max_requests=None):
+    """Poisson ticks at `rate` requests/s over the open sessions `sids`, for
+    `duration_s` seconds or `max_requests` arrivals, whichever comes first.
 
     Each arrival is a tick of a uniformly drawn session: its last predicted
     state plus Gaussian disturbance (sigma_q rad, sigma_qd rad/s), warm start
     shifted one knot.  Latency runs from the scheduled arrival to completion.
     """
-    t, clients = I.poisson_arrivals(rate, duration_s, len(sids), seed=seed)
+    t, clients = I.poisson_arrivals(rate, duration_s, len(sids), seed=seed, max_requests=max_requests)
     rng = np.random.default_rng(seed + 1)
     noise = np.zeros((len(t), 14), np.float32)
     for i, c in enumerate(clients):

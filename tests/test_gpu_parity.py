@@ -1,13 +1,15 @@
 """End-to-end parity of the fused CUDA SQP against the FP64 oracle, via the C ABI.
 
-Tolerances (the derivation is written out in DESIGN.md, "Parity"):
+Tolerances, derived from the arithmetic:
 
 * Converged solves: X, U within 1e-4 relative (||.||_inf / max(1, ||.||_inf)).
   A converged iterate is a fixed point of the SQP map, so it does not depend on
   the rounding of the path that reached it.  The residual the GPU reports must
   equal the oracle's FP64 KKT residual of the GPU iterate within 1e-5 plus the
   measured FP32 evaluation error, and that residual must be under the FP32
-  floor of this model (1e-4; measured 2e-6 .. 7.8e-5, causes in the design doc)
+  floor of this model (1e-4; measured 2e-6 .. 7.8e-5: near convergence the
+  FP32 line search can no longer resolve the merit decrease of a step, and
+  the FP32 defects carry ~2e-6 per component from the mass-matrix solve)
   instead of 1e-5.
 * Single SQP steps from the same iterate: the step computed in FP32 differs
   from the FP64 one by the QP's sensitivity to FP32 rounding of its own data.
