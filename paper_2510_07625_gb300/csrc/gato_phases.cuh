@@ -1029,12 +1029,16 @@ __device__ inline int st_pcg_t(const Ctx& C, float eps, int maxit, int precond, 
   float* const tv = SLOT(V_W);
   float* const dn = SLOT(V_DNU);
   const int J = j, J7 = j + QM;
-  // p, s and the own rows of u, w stay in registers
+  // p, s and the own rows of u, w, r and dnu stay in registers (r and dnu
+  // also in the window: y reads all rows of the knot's r, the recovery dnu)
   float p0 = 0.f, p1 = 0.f, s0 = 0.f, s1 = 0.f, u0 = 0.f, u1 = 0.f, w0 = 0.f, w1 = 0.f;
+  float rv0 = 0.f, rv1 = 0.f, dv0 = 0.f, dv1 = 0.f;
   if (csize > 1) cg::this_cluster().sync(); else __syncthreads();
   if (act) {
-    rr[J] = SLOT(V_RHS)[J];
-    rr[J7] = SLOT(V_RHS)[J7];
+    rv0 = SLOT(V_RHS)[J];
+    rv1 = SLOT(V_RHS)[J7];
+    rr[J] = rv0;
+    rr[J7] = rv1;
   }
   if constexpr (REG) {
     if (hslot >= 0) {
@@ -1047,8 +1051,10 @@ __device__ inline int st_pcg_t(const Ctx& C, float eps, int maxit, int precond, 
       R.load_from(cl.map_shared_rank(C.Lm, nbs), cl.map_shared_rank(C.Pm, nbs), nk0, C.N, k, j, hact, htu);
       if (hact) {
         const float* rhs = cl.map_shared_rank(C.vb, nb) + V_RHS * vstr + (k - (nk0 - 2)) * VW;
-        rr[J] = rhs[J];
-        rr[J7] = rhs[J7];
+        rv0 = rhs[J];
+        rv1 = rhs[J7];
+        rr[J] = rv0;
+        rr[J7] = rv1;
       }
     }
   }
@@ -1156,7 +1162,7 @@ __device__ inline int st_pcg_t(const Ctx& C, float eps, int maxit, int precond, 
         pwr[wsl + J] = w0;
         pwr[wsl + J7] = w1;
       }
-      const DF ru1 = df_fma(df_fma(ru, rr[J], u0), rr[J7], u1);
+      const DF ru1 = df_fma(df_fma(ru, rv0, u0), rv1, u1);
       const DF wu1 = df_fma(df_fma(wu, w0, u0), w1, u1);
       const DF pw1 = df_fma(df_fma(pw, p0, w0), p1, w1);  // p still holds the previous direction
       ru = act ? ru1 : ru;
@@ -1199,12 +1205,12 @@ __device__ inline int st_pcg_t(const Ctx& C, float eps, int maxit, int precond, 
     s0 = w0 + beta * s0;
     s1 = w1 + beta * s1;
     {
-      const float d0 = dn[J] + alpha * p0, d1 = dn[J7] + alpha * p1;
-      const float r0 = rr[J] - alpha * s0, r1 = rr[J7] - alpha * s1;
-      if (act) {
-        dn[J] = d0;
-        dn[J7] = d1;
-      }
+      const float d0 = dv0 + alpha * p0, d1 = dv1 + alpha * p1;
+      const float r0 = rv0 - alpha * s0, r1 = rv1 - alpha * s1;
+      dv0 = d0;
+      dv1 = d1;
+      rv0 = r0;
+      rv1 = r1;
       if (acty) {
         rr[J] = r0;
         rr[J7] = r1;
@@ -1212,10 +1218,15 @@ __device__ inline int st_pcg_t(const Ctx& C, float eps, int maxit, int precond, 
     }
     ++it;
   }
-  // the correction's boundary rows go to the neighbours for the recovery
+  // the correction into the window (once, after the loop) and its boundary
+  // rows to the neighbours for the recovery
+  if (act) {
+    dn[J] = dv0;
+    dn[J7] = dv1;
+  }
   if (act && pbd) {
-    pbd[V_DNU * vstr + J] = dn[J];
-    pbd[V_DNU * vstr + J7] = dn[J7];
+    pbd[V_DNU * vstr + J] = dv0;
+    pbd[V_DNU * vstr + J7] = dv1;
   }
   if (csize > 1) cg::this_cluster().sync(); else __syncthreads();
   return it;
