@@ -495,16 +495,9 @@ __device__ __forceinline__ void knot_cost(const Ctx& C, int k) {
       qg[QM + i] = s * wqd * v;
       Qi[49 + i] = 1.f / (s * wqd + rho);
     }
-    if (!chol7(Hl)) atomicOr(reinterpret_cast<int*>(C.scal + S_FLAGS), F_NONFINITE);
+    // the packed Q_qq, inverted column by column in the next phase
 #pragma unroll
-    for (int j2 = 0; j2 < QM; ++j2) {
-      float e[QM];
-#pragma unroll
-      for (int i = 0; i < QM; ++i) e[i] = (i == j2) ? 1.f : 0.f;
-      chol7_solve(Hl, e);
-#pragma unroll
-      for (int i = 0; i < QM; ++i) Qi[i * QM + j2] = e[i];
-    }
+    for (int i = 0; i < 28; ++i) Qi[i] = Hl[i];
   }
   if (k < N) {
     const float* u = C.U + k * US;
@@ -520,6 +513,8 @@ __device__ __forceinline__ void knot_cost(const Ctx& C, int k) {
 
 
 // Value RNEA at the dynamics solution (stored for the tangent pass) + costs.
+// End-effector cost: Q_qq^-1 by one (knot, column) per thread, each thread
+// factoring its knot's packed Q_qq (the same bits), seven solves side by side.
 __device__ inline void st_value_and_cost(const Ctx& C) {
   const int ke = C.k1 < C.N ? C.k1 : C.N;
   const int nd = ke - C.k0, nc = C.k1 - C.k0;
@@ -533,6 +528,30 @@ __device__ inline void st_value_and_cost(const Ctx& C) {
       rnea_value(*C.M, sq, cq, x + QM, C.qdd + k * US, C.M->g, tau, C.LV + k * QM);
     } else {
       knot_cost(C, C.k0 + it - nd);
+    }
+  }
+  if (C.cost_kind != 0) {
+    static_assert(QM * KPC_MAX <= NTHR, "one (knot, column) per thread");
+    __syncthreads();  // every packed Q_qq is stored
+    const int it = threadIdx.x;
+    const int k = C.k0 + it / QM, col = it % QM;
+    const bool act = it < QM * nc;
+    float Hl[28];
+    float* Qi = C.Qi + k * QIS;
+    if (act) {
+#pragma unroll
+      for (int i = 0; i < 28; ++i) Hl[i] = Qi[i];
+    }
+    __syncthreads();  // every Q_qq is read before a column of its inverse overwrites it
+    if (act) {
+      const bool ok = chol7(Hl);
+      if (!ok && col == 0) atomicOr(reinterpret_cast<int*>(C.scal + S_FLAGS), F_NONFINITE);
+      float e[QM];
+#pragma unroll
+      for (int i = 0; i < QM; ++i) e[i] = (i == col) ? 1.f : 0.f;
+      chol7_solve(Hl, e);
+#pragma unroll
+      for (int i = 0; i < QM; ++i) Qi[i * QM + col] = e[i];
     }
   }
 }
