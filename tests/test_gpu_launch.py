@@ -145,10 +145,11 @@ def test_query_launch_shapes(G):
 
 # (N, uniform cluster) -> CTA knot counts: (9, 4) -> 3,3,3,1; (7, 4) -> 2,2,2,2;
 # (6, 3) -> 3,3,1; (24, 8) -> 4 x 6, 1; (64, 8) -> 9 x 7, 2; (64, 2) -> 33, 32;
-# (98, 3) -> 33 x 3 and (128, 4) -> 33, 33, 33, 30: middle CTAs of 30 or more
-# knots, whose fourth halo knot sits on the last warp (the others on spare
-# lanes); CTAs of at most 29 knots keep all halo knots on one free warp
-HALO_CASES = [(9, 4), (7, 4), (6, 3), (24, 8), (64, 8), (64, 2), (98, 3), (128, 4)]
+# (98, 3) -> 33 x 3, (128, 4) -> 33, 33, 33, 30 and (256, 8) -> 33 x 7, 26: middle
+# CTAs of 30 or more knots, whose fourth halo knot sits on the last warp (the
+# others on spare lanes); CTAs of at most 29 knots keep all halo knots on one
+# free warp
+HALO_CASES = [(9, 4), (7, 4), (6, 3), (24, 8), (64, 8), (64, 2), (98, 3), (128, 4), (256, 8)]
 
 
 @pytest.mark.parametrize("precond", [0, 1], ids=["stair", "jacobi"])

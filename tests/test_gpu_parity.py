@@ -123,6 +123,39 @@ def _per_step_parity(G, oracle, prob, iters, factor=30.0, launch=None):
     return worst
 
 
+def test_full_size_batch(G, oracle):
+    """The benchmark's workload in the launch configuration it times: 256
+    figure-eight solves at N = 64 in one gato_solve (latency form, two-CTA
+    clusters), every solve from its cold start.
+
+    One SQP step: sampled solves (first, last and two between) against the
+    oracle's FP64 step from the same cold start, with the per-step bound of
+    _per_step_parity.  Ten SQP steps (the benchmark's count): every solve
+    finite, ten iterations, no PCG stopped at its cap, and its merit below the
+    cold-start merit (the line search only accepts decreases).
+    """
+    probs = I.config_sweep(256, 64)
+    g1 = gpu_solve(G, probs, 1, launch=(1, 0, 0))
+    for i in (0, 85, 170, 255):
+        p = probs[i]
+        X, U, lam = oracle.cold_start(p)
+        o = oracle.solve(p, max_iter=1, X=X, U=U, lam=lam)
+        sens, dmax = qp_sensitivity(oracle, p, X, U, lam)
+        g = g1[i]
+        assert g["sqp_iters"] == 1 and not (g["flags"] & 16), g["flags"]
+        if len(o["alpha_idx"]) == 1 and o["alpha_idx"][0] >= 0 and o["merit_gap"][0] > 1e-5:
+            a = 0.5 ** o["alpha_idx"][0]
+            tol = 1e-4 * max(1.0, np.abs(o["X"]).max()) + 30.0 * a * sens * dmax
+            assert np.abs(g["X"] - o["X"]).max() <= tol, (i, np.abs(g["X"] - o["X"]).max(), tol)
+            assert np.abs(g["U"] - o["U"]).max() <= tol * max(1.0, np.abs(o["U"]).max()), i
+    g10 = gpu_solve(G, probs, 10, launch=(1, 0, 0))
+    for p, g in zip(probs, g10):
+        assert g["sqp_iters"] == 10 and not (g["flags"] & (8 | 16)), (p.seed, g["flags"])
+        assert np.isfinite(g["X"]).all() and np.isfinite(g["U"]).all(), p.seed
+        X0, U0, _ = oracle.cold_start(p)
+        assert g["merit"] < oracle.merit(p, X0, U0), (p.seed, g["merit"])
+
+
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_single_solve_per_step_parity(G, oracle, seed):
     """The single-solve workload (7-DoF, N=32, dt=0.01), 5 SQP iterations."""
