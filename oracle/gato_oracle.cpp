@@ -24,7 +24,9 @@
  *              the previous multiplier; stops when the preconditioned residual
  *              relative to the warm start's, sqrt(eta/eta_0), is <= eps (c8),
  *              so the correction to the multiplier is accurate relative to its
- *              own size; no iterations when eta_0 < 1e-30.
+ *              own size; no iterations when eta_0 < 1e-30.  Optionally (the
+ *              direct alternative Sec. II-B sets against iterative methods) the
+ *              same system S nu = rhs by block elimination (ora_blocktri_solve).
  *   recovery   dZ = -G^-1 (g + C^T nu)  (Eq. 4, sign of reading c1).
  *   merit      Eq. 3: J + mu * ||c||_1 (reading c5).
  *   line srch  Eq. 7: alpha_i = beta^-i, i = 0..A-1, argmin with ties to the
@@ -68,6 +70,7 @@ typedef struct {
   int32_t precond;        /* 0 = stair (Eq. 6), 1 = block Jacobi */
   double kkt_tol;         /* <= 0: run the fixed iteration count */
   int32_t max_iter;
+  int32_t linsolve;       /* 0 = PCG (Sec. II-B), 1 = direct block elimination */
 } ora_params;
 
 typedef struct {
@@ -815,6 +818,9 @@ double ora_kkt_residual(const ora_model* m, const ora_problem* p, const double* 
    Per-iteration logs (each [max_iter] or NULL): chosen alpha index (-1 reject),
    PCG iterations, merit before the step, merit after, KKT residual, the gap
    between the two best trial merits relative to the best. */
+int32_t ora_blocktri_solve(int32_t N, int32_t nx, const double* Sd, const double* Ss,
+                           const double* rhs, double* x);
+
 int32_t ora_solve(const ora_model* m, const ora_problem* p, const ora_params* prm,
                   double* X, double* U, double* nu, const int32_t* replay,
                   int32_t* log_alpha, int32_t* log_pcg, double* log_m0, double* log_m1,
@@ -839,7 +845,15 @@ int32_t ora_solve(const ora_model* m, const ora_problem* p, const ora_params* pr
     Schur S = form_schur(L, prm->precond);
     if (!S.ok) { R.flags |= 16; break; }
     bool hit = false;
-    int pit = pcg(S, prm->pcg_eps, prm->pcg_max, nu, &hit);
+    int pit = 0;
+    if (prm->linsolve == 1) {
+      if (ora_blocktri_solve(N, nx, S.Sd.data(), S.Ss.data(), S.rhs.data(), nu) != 0) {
+        R.flags |= 16;
+        break;
+      }
+    } else {
+      pit = pcg(S, prm->pcg_eps, prm->pcg_max, nu, &hit);
+    }
     if (hit) R.flags |= 8;
     R.pcg_total += pit;
     recover(L, S, nu, dX.data(), dU.data());

@@ -129,3 +129,17 @@ def test_oracle_regression_fixture(oracle):
         np.testing.assert_allclose(r["X"], np.array(g["X"]), atol=1e-9)
         np.testing.assert_allclose(r["U"], np.array(g["U"]), atol=1e-8)
         np.testing.assert_allclose(r["kkt_log"], g["kkt_log"], rtol=1e-8)
+
+
+def test_direct_linear_solve_equals_converged_pcg(oracle):
+    # The direct alternative to PCG (block elimination of S nu = rhs) and PCG
+    # run to a tolerance far below FP64 noise solve the same QP each iteration,
+    # so the SQP paths agree to rounding; the direct path takes no PCG steps.
+    for p in (I.joint_problem(0, I.arm7(), 16, 0.01), I.ee_problem(2, I.arm7(), 12, 0.01)):
+        a = oracle.solve(p, 3, pcg_eps=1e-12, pcg_max=5000)
+        b = oracle.solve(p, 3, linsolve=1)
+        assert b["pcg_total"] == 0 and b["flags"] == a["flags"]
+        assert list(a["alpha_idx"]) == list(b["alpha_idx"])
+        assert np.abs(a["X"] - b["X"]).max() <= 1e-9 * max(1.0, np.abs(a["X"]).max())
+        assert np.abs(a["U"] - b["U"]).max() <= 1e-9 * max(1.0, np.abs(a["U"]).max())
+        assert np.abs(a["lam"] - b["lam"]).max() <= 1e-7 * max(1.0, np.abs(a["lam"]).max())
