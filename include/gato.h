@@ -57,6 +57,8 @@ enum {
 
 enum { GATO_COST_JOINT = 0, GATO_COST_EE = 1 };
 enum { GATO_PRECOND_STAIR = 0, GATO_PRECOND_JACOBI = 1 };
+/* Linear solver of the Schur system (gato_solver_params.linsolve). */
+enum { GATO_LINSOLVE_PCG = 0, GATO_LINSOLVE_DIRECT = 1 };
 enum { GATO_MEM_HOST = 0, GATO_MEM_DEVICE = 1 };
 
 /* Serial revolute chain (Sec. II-A "discrete-time dynamical system"; the
@@ -86,6 +88,10 @@ typedef struct {
   int32_t pcg_max_iter;    /* PCG iteration cap, default 1000 */
   int32_t precond;         /* GATO_PRECOND_STAIR (Eq. 6) or GATO_PRECOND_JACOBI */
   float kkt_tol;           /* > 0: a solve stops once its KKT residual <= kkt_tol */
+  int32_t linsolve;        /* GATO_LINSOLVE_PCG (the method, default) or
+                              GATO_LINSOLVE_DIRECT: S dnu = rhs by block elimination
+                              along the horizon (sequential over knots; precond,
+                              pcg_eps and pcg_max_iter unused; pcg_iters reads 0) */
 } gato_solver_params;
 
 typedef struct {

@@ -154,6 +154,8 @@ gato_status validate_params(gato_batch* b, const gato_solver_params& p) {
   if (p.pcg_max_iter < 1) return fail(b, GATO_E_INVALID, "pcg_max_iter must be >= 1");
   if (p.precond != GATO_PRECOND_STAIR && p.precond != GATO_PRECOND_JACOBI)
     return fail(b, GATO_E_INVALID, "unknown preconditioner");
+  if (p.linsolve != GATO_LINSOLVE_PCG && p.linsolve != GATO_LINSOLVE_DIRECT)
+    return fail(b, GATO_E_INVALID, "unknown linear solver");
   if (!std::isfinite(p.kkt_tol)) return fail(b, GATO_E_INVALID, "kkt_tol must be finite");
   return GATO_OK;
 }
@@ -207,6 +209,7 @@ Params to_params(const gato_solver_params& p, int iters) {
   o.precond = p.precond;
   o.kkt_tol = p.kkt_tol;
   o.max_iter = iters;
+  o.linsolve = p.linsolve;
   return o;
 }
 
@@ -437,6 +440,7 @@ void gato_default_params(gato_solver_params* o) {
   o->pcg_max_iter = 1000;
   o->precond = GATO_PRECOND_STAIR;
   o->kkt_tol = 0.f;
+  o->linsolve = GATO_LINSOLVE_PCG;
 }
 
 const char* gato_status_string(gato_status s) {

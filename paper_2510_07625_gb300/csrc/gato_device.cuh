@@ -57,6 +57,7 @@ struct Params {
   int precond;
   float kkt_tol;
   int max_iter;
+  int linsolve;  // 0 PCG, 1 direct block elimination
 };
 
 struct Result {

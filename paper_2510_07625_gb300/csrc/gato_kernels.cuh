@@ -107,15 +107,24 @@ __device__ void sqp_solve(Ctx& C, const ProbDesc& P, const Params& prm, int iter
     st_schur(C);
     __syncthreads();
     tstamp(C, T_SCHUR, tl);
-    st_block_inverse(C);
-    if (cluster_flag(C, rbuf)) {
-      flags |= F_NONFINITE;
-      break;
+    if (prm.linsolve == 1) {  // direct block elimination instead of PCG
+      st_direct(C);
+      if (cluster_flag(C, rbuf)) {
+        flags |= F_NONFINITE;
+        break;
+      }
+      tstamp(C, T_BINV, tl);
+    } else {
+      st_block_inverse(C);
+      if (cluster_flag(C, rbuf)) {
+        flags |= F_NONFINITE;
+        break;
+      }
+      tstamp(C, T_BINV, tl);
+      bool hit = false;
+      pcg_total += st_pcg<REG>(C, prm.pcg_eps, prm.pcg_max, prm.precond, &hit, rbuf);
+      if (hit) flags |= F_PCGMAX;
     }
-    tstamp(C, T_BINV, tl);
-    bool hit = false;
-    pcg_total += st_pcg<REG>(C, prm.pcg_eps, prm.pcg_max, prm.precond, &hit, rbuf);
-    if (hit) flags |= F_PCGMAX;
     if (C.tm && C.rank == 0 && threadIdx.x == 0) tl = clock64();
     st_recover(C);
     if (cluster_flag(C, rbuf)) {
@@ -313,6 +322,15 @@ __global__ void __launch_bounds__(NTHR, 1) sqp_plain_stage(int stage, PlainArgs 
       }
       break;
     case PS_PCG: {
+      if (prm.linsolve == 1) {
+        st_direct(C);
+        csync(C);
+        if (lead && *reinterpret_cast<volatile int*>(C.scal + S_FLAGS)) {
+          *rflags |= F_NONFINITE;
+          C.scal[S_DONE] = 1.f;
+        }
+        break;
+      }
       bool hit = false;
       const int n = st_pcg<true>(C, prm.pcg_eps, prm.pcg_max, prm.precond, &hit, rbuf);
       if (lead) {

@@ -1266,6 +1266,137 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
 
 // ------------------------------------------------- stage 4: step recovery
 
+// --------------------------------------- stage 3b: direct linear solve
+//
+// The direct alternative to PCG that Sec. II-B sets against iterative
+// methods, for the same system S dnu = rhs, by block elimination along the
+// horizon:
+//   D~_0 = D_0, y~_0 = rhs_0;  W_k = L_k D~_{k-1}^-1,
+//   D~_k = D_k - W_k L_k^T,    y~_k = rhs_k - W_k y~_{k-1};
+//   dnu_N = D~_N^-1 y~_N,      dnu_k = D~_k^-1 (y~_k - L_{k+1}^T dnu_{k+1}).
+// Sequential over knots and parallel inside a 14x14 block (one element per
+// thread, block barriers between the products).  The CTAs of a cluster take
+// the forward sweep in rank order and the backward sweep in reverse, each
+// handing its last D~^-1 and y~ (forward) or its first dnu (backward) to the
+// next CTA through distributed shared memory, with a cluster barrier per
+// hand-over.  D~_k^-1 (Gauss-Jordan without pivoting: D~_k is SPD, a Schur
+// complement of the SPD S; a pivot that is not positive flags the solve)
+// goes to the preconditioner's block slot, y~ to the y window; the
+// reduction slots serve as scratch.
+__device__ inline void st_direct(const Ctx& C) {
+  constexpr int BB = XM * XM;
+  static_assert(4 * BB + 2 * XM <= 2 * RED_SLOTS * RED_W, "scratch in the reduction slots");
+  static_assert(BB + XM <= NTHR, "one block element per thread");
+  const int t = threadIdx.x;
+  const int i = t % XM, j = t / XM;  // element (i, j) of a column-major block, t < BB
+  const bool el = t < BB;
+  float* const W = C.red;
+  float* const G0 = W + BB;
+  float* const G1 = G0 + BB;
+  float* const carry = G1 + BB;  // [BB] D~^-1, [XM] y~, [XM] dnu
+  csync(C);  // every CTA has finished reading the reduction slots of earlier stages
+  // forward sweep
+  for (int s = 0; s < C.csize; ++s) {
+    if (C.rank == s) {
+      for (int k = C.k0; k < C.k1; ++k) {
+        const float* Dk = &bD(C, k, 0, 0);
+        const float* Lk = &bL(C, k, 0, 0);
+        const float* rk = vec(C, V_RHS, k);
+        float* yk = vec(C, V_Y, k);
+        if (k == 0) {
+          if (el) G0[t] = Dk[t];
+          else if (t < BB + XM) yk[t - BB] = rk[t - BB];
+        } else {
+          const float* Pp = (k == C.k0) ? carry : &bP(C, k - 1, 0, 0);
+          const float* yp = (k == C.k0) ? carry + BB : vec(C, V_Y, k - 1);
+          if (el) {
+            float a = 0.f;
+#pragma unroll
+            for (int l = 0; l < XM; ++l) a += Lk[l * XM + i] * Pp[j * XM + l];
+            W[t] = a;
+          }
+          __syncthreads();
+          if (el) {
+            float a = Dk[t];
+#pragma unroll
+            for (int l = 0; l < XM; ++l) a -= W[l * XM + i] * Lk[l * XM + j];
+            G0[t] = a;
+          } else if (t < BB + XM) {
+            const int r = t - BB;
+            float a = rk[r];
+#pragma unroll
+            for (int l = 0; l < XM; ++l) a -= W[l * XM + r] * yp[l];
+            yk[r] = a;
+          }
+        }
+        __syncthreads();
+        float* A = G0;
+        float* B = G1;
+        float* const Pk = &bP(C, k, 0, 0);
+        for (int p = 0; p < XM; ++p) {
+          if (el) {
+            const float piv = A[p * XM + p];
+            const float inv = 1.f / piv;
+            const float aip = A[p * XM + i], apj = A[j * XM + p], aij = A[t];
+            float out;
+            if (i == p)
+              out = (j == p) ? inv : apj * inv;
+            else
+              out = (j == p) ? -aip * inv : aij - aip * (apj * inv);
+            (p == XM - 1 ? Pk : B)[t] = out;
+            if (t == 0 && !(piv > 0.f && piv < INFINITY)) flag_nonfinite(C);
+          }
+          __syncthreads();
+          float* const tmp = A;
+          A = B;
+          B = tmp;
+        }
+      }
+      if (C.rank + 1 < C.csize) {  // D~^-1 and y~ of the last knot to the next CTA
+        float* dst = cg::this_cluster().map_shared_rank(carry, C.rank + 1);
+        if (el)
+          dst[t] = bP(C, C.k1 - 1, i, j);
+        else if (t < BB + XM)
+          dst[t] = vec(C, V_Y, C.k1 - 1)[t - BB];
+      }
+    }
+    csync(C);
+  }
+  // backward sweep
+  for (int s = C.csize - 1; s >= 0; --s) {
+    if (C.rank == s) {
+      for (int k = C.k1 - 1; k >= C.k0; --k) {
+        if (t < XM) {
+          float b = vec(C, V_Y, k)[t];
+          if (k < C.N) {
+            const float* xn = (k == C.k1 - 1) ? carry + BB + XM : vec(C, V_DNU, k + 1);
+            const float* Ln = &bL(C, k + 1, 0, 0);  // (L_{k+1}^T)(t, l) = L_{k+1}(l, t)
+#pragma unroll
+            for (int l = 0; l < XM; ++l) b -= Ln[t * XM + l] * xn[l];
+          }
+          W[t] = b;
+        }
+        __syncthreads();
+        if (t < XM) {
+          const float* Pk = &bP(C, k, 0, 0);
+          float x = 0.f;
+#pragma unroll
+          for (int l = 0; l < XM; ++l) x += Pk[l * XM + t] * W[l];
+          vec(C, V_DNU, k)[t] = x;
+        }
+        __syncthreads();
+      }
+      if (t < XM) {
+        // the right neighbour's first dnu is this CTA's halo for the recovery
+        if (C.rank + 1 < C.csize && C.k1 <= C.N) vec(C, V_DNU, C.k1)[t] = carry[BB + XM + t];
+        if (C.rank > 0)  // this CTA's first dnu to the previous CTA
+          cg::this_cluster().map_shared_rank(carry, C.rank - 1)[BB + XM + t] = vec(C, V_DNU, C.k0)[t];
+      }
+    }
+    csync(C);
+  }
+}
+
 // dx_k = -Q_k^-1 (q_k + nu_k - A_k^T nu_{k+1}), du_k = -R_k^-1 (r_k - B_k^T nu_{k+1})
 // (Eq. 4, reading c1), evaluated as -G^-1 (d + C^T dnu); then nu += dnu.
 __device__ inline void st_recover(const Ctx& C) {

@@ -122,6 +122,7 @@ extern "C" gato_status gato_solve_noalloc(const gato_model_desc* models, int32_t
   if (!(sp.mu >= 0.f) || !std::isfinite(sp.mu) || !(sp.beta > 1.f) || !std::isfinite(sp.beta) ||
       sp.n_alpha < 1 || sp.n_alpha > MAX_ALPHA || !(sp.pcg_eps > 0.f) || sp.pcg_max_iter < 1 ||
       (sp.precond != GATO_PRECOND_STAIR && sp.precond != GATO_PRECOND_JACOBI) ||
+      (sp.linsolve != GATO_LINSOLVE_PCG && sp.linsolve != GATO_LINSOLVE_DIRECT) ||
       !std::isfinite(sp.kkt_tol))
     return GATO_E_INVALID;
   DevModel dm[kMaxModels];
@@ -185,6 +186,7 @@ extern "C" gato_status gato_solve_noalloc(const gato_model_desc* models, int32_t
   a.prm.precond = sp.precond;
   a.prm.kkt_tol = sp.kkt_tol;
   a.prm.max_iter = max_sqp_iters;
+  a.prm.linsolve = sp.linsolve;
   a.timing = nullptr;
   a.variant = 0;
   if (launch_fused_grouped(a, order, P->order, Ns, n, stream, LaunchPlan()) != cudaSuccess) {

@@ -23,6 +23,7 @@ GATO_OK, GATO_E_INVALID, GATO_E_NOMEM, GATO_E_CUDA, GATO_E_TIMEOUT, GATO_E_BUSY 
 SOLVE_CONVERGED, SOLVE_MAXITER, SOLVE_LSFAIL, SOLVE_PCG_MAXIT, SOLVE_NONFINITE = 1, 2, 4, 8, 16
 COST_JOINT, COST_EE = 0, 1
 PRECOND_STAIR, PRECOND_JACOBI = 0, 1
+LINSOLVE_PCG, LINSOLVE_DIRECT = 0, 1
 MEM_HOST, MEM_DEVICE = 0, 1
 
 EXPORTED = (
@@ -48,7 +49,7 @@ class ModelDesc(C.Structure):
 class SolverParams(C.Structure):
     _fields_ = [("mu", C.c_float), ("beta", C.c_float), ("n_alpha", C.c_int32),
                 ("pcg_eps", C.c_float), ("pcg_max_iter", C.c_int32), ("precond", C.c_int32),
-                ("kkt_tol", C.c_float)]
+                ("kkt_tol", C.c_float), ("linsolve", C.c_int32)]
 
 
 class BatchDesc(C.Structure):

@@ -100,13 +100,14 @@ def test_batch_invariance_bitwise(G):
         np.testing.assert_array_equal(alone["U"], together[i]["U"])
 
 
-def _per_step_parity(G, oracle, prob, iters, factor=30.0, launch=None):
-    """Each GPU SQP step against the oracle step from the same iterate."""
+def _per_step_parity(G, oracle, prob, iters, factor=30.0, launch=None, linsolve=0):
+    """Each GPU SQP step against the oracle step from the same iterate (both
+    with the same linear solver: PCG, or direct block elimination)."""
     X, U, lam = oracle.cold_start(prob)
     worst = 0.0
     for it in range(iters):
-        g = gpu_solve(G, [prob], 1, X=[X], U=[U], lam=[lam], launch=launch)[0]
-        o = oracle.solve(prob, max_iter=1, X=X, U=U, lam=lam)
+        g = gpu_solve(G, [prob], 1, X=[X], U=[U], lam=[lam], launch=launch, linsolve=linsolve)[0]
+        o = oracle.solve(prob, max_iter=1, X=X, U=U, lam=lam, linsolve=linsolve)
         sens, dmax = qp_sensitivity(oracle, prob, X, U, lam)
         if g["sqp_iters"] == 1 and len(o["alpha_idx"]) == 1 and o["alpha_idx"][0] >= 0:
             a = 0.5 ** o["alpha_idx"][0]
