@@ -7,9 +7,11 @@ gato_solve call over the whole batch from the cold start.  Extra keys report
 the p50/p99 latency of the B=32 call (10 and 3 SQP iterations), the plain
 one-solve-per-launch GPU form at B=32 and B=256, the uneven mix (128 solves, N
 in 16..128, two arms, per-solve stop at KKT 1e-5 or 20 iterations) replayed
-from a CUDA graph, and the serving loop under Poisson arrivals (1k, 2k, 5k, 10k
+from a CUDA graph, the serving loop under Poisson arrivals (1k, 2k, 5k, 10k
 and 20k ticks/s over 128 resident sessions of that mix, 3 SQP iterations per
-tick, each rate for 10 s or 50k requests, whichever comes first).
+tick, each rate for 10 s or 50k requests, whichever comes first), and the same
+B=32 latencies and B=256 throughput with the optional direct linear solve
+(block elimination along the horizon in place of PCG).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -213,6 +215,7 @@ def run_gpu(args):
     out = {}
     if rank == 0:
         lat = latency_runs(gato, I, torch, stream, flush, launch_cfg=True)
+        direct = direct_solver_runs(gato, I, torch, stream, flush)
         plain = plain_form(gato, I, torch)
         uneven = uneven_graph(gato, I, torch)
         serve = serving_runs(gato, I)
@@ -228,7 +231,8 @@ def run_gpu(args):
                        "B": B_MAIN, "N": N_MAIN, "sqp_iters": ITERS, "dof": 7,
                        "parallelism": f"replicas x{ws}", "l2": "flushed between timed launches (512 MB write)",
                        "launch": launch},
-            "latency_ms": lat, "plain_gpu_form": plain, "uneven_graph": uneven, "serving": serve,
+            "latency_ms": lat, "direct_linear_solve": direct, "plain_gpu_form": plain,
+            "uneven_graph": uneven, "serving": serve,
             "speedup_vs_plain_B32": round(lat["B32_iters10"]["solves_per_s"] / plain["solves_per_s_B32"], 2),
             "speedup_vs_plain_B256": round(value / ws / plain[f"solves_per_s_B{B_MAIN}"], 2),
             "pcg_iters_per_solve": round(pcg / dp.n, 1), "sqp_iters_per_solve": round(sqp / dp.n, 2),
@@ -253,11 +257,11 @@ def run_gpu(args):
 TRAFFIC_BYTES = 23554560
 
 
-def latency_runs(gato, I, torch, stream, flush, n_calls=200, launch_cfg=False):
+def latency_runs(gato, I, torch, stream, flush, n_calls=200, launch_cfg=False, **prm):
     """p50/p99 of one B=32 call (device events), 10 and 3 SQP iterations."""
     out = {}
     probs = I.config_sweep(B_LAT, N_MAIN)
-    B = gato.Batch([I.arm7()], B_LAT, N_MAIN, stream=stream.cuda_stream)
+    B = gato.Batch([I.arm7()], B_LAT, N_MAIN, stream=stream.cuda_stream, **prm)
     dp = gato.DeviceProblems(B, probs)
     if launch_cfg:
         out["launch"], _ = B.autotune(dp.arr, dp.n, 3, reps=3)
@@ -279,6 +283,38 @@ def latency_runs(gato, I, torch, stream, flush, n_calls=200, launch_cfg=False):
         p99 = ts[min(len(ts) - 1, int(0.99 * len(ts)))]
         out[f"B32_iters{iters}"] = {"p50_ms": round(p50, 4), "p99_ms": round(p99, 4),
                                     "solves_per_s": round(B_LAT / (p50 / 1e3), 1), "calls": n_calls}
+    B.close()
+    return out
+
+
+def direct_solver_runs(gato, I, torch, stream, flush, steps=10):
+    """The direct linear solve (block elimination along the horizon instead of
+    PCG; an option, not the paper's method): B = 32 p50/p99 latency at 10 and
+    3 SQP iterations and the B = 256 throughput of the headline workload, each
+    with its own autotuned launch configuration and the L2 flushed between
+    timed throughput launches."""
+    out = {"linsolve": "direct", "latency_ms": latency_runs(gato, I, torch, stream, flush, launch_cfg=True,
+                                                            linsolve=gato.LINSOLVE_DIRECT)}
+    probs = I.config_sweep(B_MAIN, N_MAIN)
+    B = gato.Batch([I.arm7()], B_MAIN, N_MAIN, stream=stream.cuda_stream, linsolve=gato.LINSOLVE_DIRECT)
+    dp = gato.DeviceProblems(B, probs)
+    out["launch"], _ = B.autotune(dp.arr, dp.n, ITERS, reps=1)
+    ts = []
+    for rep in range(steps + 3):
+        dp.reset()
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        gato.gato_solve(B.handle, dp.arr, dp.n, ITERS, None)
+        e1.record(stream)
+        B.sync()
+        if rep >= 3:
+            ts.append(e0.elapsed_time(e1))
+    res = gato.gato_get_results(B.handle, dp.n)
+    t = statistics.median(ts)
+    out["B256_iters10"] = {"ms_per_call": round(t, 4), "solves_per_s": round(B_MAIN / (t / 1e3), 1),
+                           "kkt_max": round(max(res[i].kkt_residual for i in range(dp.n)), 6)}
     B.close()
     return out
 
