@@ -1283,7 +1283,7 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
 // complement of the SPD S; a pivot that is not positive flags the solve)
 // goes to the preconditioner's block slot, y~ to the y window; the
 // reduction slots serve as scratch.
-__device__ inline void st_direct(const Ctx& C) {
+__device__ __forceinline__ void st_direct_body(const Ctx& C) {
   constexpr int BB = XM * XM;
   static_assert(4 * BB + 2 * XM <= 2 * RED_SLOTS * RED_W, "scratch in the reduction slots");
   static_assert(BB + XM <= NTHR, "one block element per thread");
@@ -1395,6 +1395,38 @@ __device__ inline void st_direct(const Ctx& C) {
     }
     csync(C);
   }
+}
+
+// The direct solve as a call of its own (kept out of the kernel body so that
+// the PCG's register allocation does not change with it), with the fields it
+// reads passed by value rather than through the caller's Ctx in memory.
+struct DirectView {
+  float *Dm, *Lm, *Pm, *vb, *red, *scal;
+  int bk0, vstride, vk0, k0, k1, N, rank, csize;
+};
+
+static __device__ __noinline__ void st_direct_call(DirectView v) {
+  Ctx C;
+  C.Dm = v.Dm;
+  C.Lm = v.Lm;
+  C.Pm = v.Pm;
+  C.vb = v.vb;
+  C.red = v.red;
+  C.scal = v.scal;
+  C.bk0 = v.bk0;
+  C.vstride = v.vstride;
+  C.vk0 = v.vk0;
+  C.k0 = v.k0;
+  C.k1 = v.k1;
+  C.N = v.N;
+  C.rank = v.rank;
+  C.csize = v.csize;
+  st_direct_body(C);
+}
+
+__device__ __forceinline__ void st_direct(const Ctx& C) {
+  st_direct_call(DirectView{C.Dm, C.Lm, C.Pm, C.vb, C.red, C.scal, C.bk0, C.vstride, C.vk0, C.k0, C.k1, C.N,
+                            C.rank, C.csize});
 }
 
 // dx_k = -Q_k^-1 (q_k + nu_k - A_k^T nu_{k+1}), du_k = -R_k^-1 (r_k - B_k^T nu_{k+1})
