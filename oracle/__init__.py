@@ -46,7 +46,8 @@ class OraProblem(C.Structure):
 class OraParams(C.Structure):
     _fields_ = [("mu", C.c_double), ("beta", C.c_double), ("n_alpha", C.c_int32),
                 ("pcg_eps", C.c_double), ("pcg_max", C.c_int32), ("precond", C.c_int32),
-                ("kkt_tol", C.c_double), ("max_iter", C.c_int32), ("linsolve", C.c_int32)]
+                ("kkt_tol", C.c_double), ("max_iter", C.c_int32), ("linsolve", C.c_int32),
+                ("rho_adapt", C.c_int32)]
 
 
 class OraResult(C.Structure):
@@ -298,7 +299,7 @@ def kkt_residual(prob, X, U, nu):
 
 
 DEFAULTS = dict(mu=10.0, beta=2.0, n_alpha=8, pcg_eps=1e-6, pcg_max=200, precond=0,
-                kkt_tol=0.0, max_iter=10, linsolve=0)
+                kkt_tol=0.0, max_iter=10, linsolve=0, rho_adapt=0)
 
 
 def solve(prob, max_iter=10, X=None, U=None, lam=None, replay=None, **kw):

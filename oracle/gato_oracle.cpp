@@ -71,6 +71,8 @@ typedef struct {
   double kkt_tol;         /* <= 0: run the fixed iteration count */
   int32_t max_iter;
   int32_t linsolve;       /* 0 = PCG (Sec. II-B), 1 = direct block elimination */
+  int32_t rho_adapt;      /* 1: rho /= 3 after an accepted step, *= 2 after a rejected
+                             one, within [1e-8, 1e8] (Sec. IV-C, reading c25) */
 } ora_params;
 
 typedef struct {
@@ -830,9 +832,10 @@ int32_t ora_solve(const ora_model* m, const ora_problem* p, const ora_params* pr
   Vec dX(nX), dU(nU), Xt(nX), Ut(nU), mer(std::max(1, (int)prm->n_alpha));
   ora_result R;
   R.iters = 0; R.flags = 0; R.pcg_total = 0; R.kkt = 0.0; R.merit = 0.0;
+  ora_problem pr = *p;  /* its rho (w[5]) follows the adaptation when that is on */
   for (int it = 0;; ++it) {
     if (it == prm->max_iter && prm->kkt_tol <= 0.0) break;
-    Lin L = linearize(*m, *p, X, U);
+    Lin L = linearize(*m, pr, X, U);
     if (!L.ok || !all_finite(L.c.data(), L.c.size())) { R.flags |= 16; break; }
     double rk = kkt_residual(L, nu);
     R.kkt = rk;
@@ -865,7 +868,7 @@ int32_t ora_solve(const ora_model* m, const ora_problem* p, const ora_params* pr
       for (size_t l = 0; l < nX; ++l) Xt[l] = X[l] + alpha * dX[l];
       for (size_t l = 0; l < nU; ++l) Ut[l] = U[l] + alpha * dU[l];
       bool ok = true;
-      double mi = merit(*m, *p, Xt.data(), Ut.data(), prm->mu, &ok);
+      double mi = merit(*m, pr, Xt.data(), Ut.data(), prm->mu, &ok);
       if (!ok || !std::isfinite(mi)) mi = INFINITY;
       mer[i] = mi;
       alpha /= prm->beta;
@@ -887,6 +890,8 @@ int32_t ora_solve(const ora_model* m, const ora_problem* p, const ora_params* pr
     } else {
       R.flags |= 4;
     }
+    if (prm->rho_adapt)
+      pr.w[5] = choice >= 0 ? std::max(pr.w[5] / 3.0, 1e-8) : std::min(pr.w[5] * 2.0, 1e8);
     if (log_alpha && it < prm->max_iter) log_alpha[it] = choice;
     if (log_pcg && it < prm->max_iter) log_pcg[it] = pit;
     if (log_m1 && it < prm->max_iter) log_m1[it] = R.merit;

@@ -143,3 +143,27 @@ def test_direct_linear_solve_equals_converged_pcg(oracle):
         assert np.abs(a["X"] - b["X"]).max() <= 1e-9 * max(1.0, np.abs(a["X"]).max())
         assert np.abs(a["U"] - b["U"]).max() <= 1e-9 * max(1.0, np.abs(a["U"]).max())
         assert np.abs(a["lam"] - b["lam"]).max() <= 1e-7 * max(1.0, np.abs(a["lam"]).max())
+
+
+def test_rho_adaptation_rule(oracle):
+    # Sec. IV-C adjusts rho after each SQP iteration from the line search's
+    # outcome; reading c25: rho / 3 after an accepted step, rho * 2 after a
+    # rejected one, within [1e-8, 1e8].  The adapted run equals single
+    # iterations with rho set by that rule between them.
+    import dataclasses
+
+    p0 = I.ee_problem(1, I.arm7(), 16, 0.05)
+    p = dataclasses.replace(p0, w=tuple(p0.w[:5]) + (0.1,))
+    full = oracle.solve(p, 8, rho_adapt=1)
+    plain = oracle.solve(p, 8)
+    assert np.abs(full["X"] - plain["X"]).max() > 1e-6  # the adaptation changes the path
+    X, U, lam = oracle.cold_start(p)
+    rho = 0.1
+    for it in range(8):
+        q = dataclasses.replace(p, w=tuple(p.w[:5]) + (rho,))
+        r = oracle.solve(q, 1, X=X, U=U, lam=lam)
+        assert r["alpha_idx"][0] == full["alpha_idx"][it]
+        X, U, lam = r["X"], r["U"], r["lam"]
+        rho = max(rho / 3.0, 1e-8) if r["alpha_idx"][0] >= 0 else min(rho * 2.0, 1e8)
+    np.testing.assert_allclose(full["X"], X, rtol=0, atol=1e-12 * max(1.0, np.abs(X).max()))
+    np.testing.assert_allclose(full["U"], U, rtol=0, atol=1e-12 * max(1.0, np.abs(U).max()))
