@@ -92,6 +92,11 @@ typedef struct {
                               GATO_LINSOLVE_DIRECT: S dnu = rhs by block elimination
                               along the horizon (sequential over knots; precond,
                               pcg_eps and pcg_max_iter unused; pcg_iters reads 0) */
+  int32_t rho_adapt;       /* 1: each solve's rho (w[5]) is adjusted after every SQP
+                              iteration from its line search (Sec. IV-C): / 3 after an
+                              accepted step, * 2 after a rejected one, within
+                              [1e-8, 1e8]; it starts from w[5] at every call.
+                              0 (default): rho fixed */
 } gato_solver_params;
 
 typedef struct {

@@ -156,6 +156,7 @@ gato_status validate_params(gato_batch* b, const gato_solver_params& p) {
     return fail(b, GATO_E_INVALID, "unknown preconditioner");
   if (p.linsolve != GATO_LINSOLVE_PCG && p.linsolve != GATO_LINSOLVE_DIRECT)
     return fail(b, GATO_E_INVALID, "unknown linear solver");
+  if (p.rho_adapt != 0 && p.rho_adapt != 1) return fail(b, GATO_E_INVALID, "rho_adapt must be 0 or 1");
   if (!std::isfinite(p.kkt_tol)) return fail(b, GATO_E_INVALID, "kkt_tol must be finite");
   return GATO_OK;
 }
@@ -210,6 +211,7 @@ Params to_params(const gato_solver_params& p, int iters) {
   o.kkt_tol = p.kkt_tol;
   o.max_iter = iters;
   o.linsolve = p.linsolve;
+  o.rho_adapt = p.rho_adapt;
   return o;
 }
 
@@ -441,6 +443,7 @@ void gato_default_params(gato_solver_params* o) {
   o->precond = GATO_PRECOND_STAIR;
   o->kkt_tol = 0.f;
   o->linsolve = GATO_LINSOLVE_PCG;
+  o->rho_adapt = 0;
 }
 
 const char* gato_status_string(gato_status s) {

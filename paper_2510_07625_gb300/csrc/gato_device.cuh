@@ -58,6 +58,7 @@ struct Params {
   float kkt_tol;
   int max_iter;
   int linsolve;  // 0 PCG, 1 direct block elimination
+  int rho_adapt; // 1: rho / 3 after an accepted step, * 2 after a rejected one
 };
 
 struct Result {

@@ -136,6 +136,7 @@ __device__ void sqp_solve(Ctx& C, const ProbDesc& P, const Params& prm, int iter
     tstamp(C, T_LS, tl);
     const int choice = st_accept(C, prm.beta, prm.n_alpha);
     csync(C);
+    if (prm.rho_adapt) C.w[5] = rho_next(C.w[5], choice);  // every thread, the same choice
     tstamp(C, T_ACCEPT, tl);
     if (choice >= 0)
       merit = C.scal[S_MERITS + choice];
@@ -265,10 +266,11 @@ __global__ void __launch_bounds__(NTHR, 1) sqp_plain_stage(int stage, PlainArgs 
   int* rflags = reinterpret_cast<int*>(C.scal + S_RFLAGS);
   int rbuf = 0;
   if (stage == PS_LOAD) {
-    if (rank == 0 && threadIdx.x < SCAL_FLOATS) C.scal[threadIdx.x] = 0.f;
+    if (rank == 0 && threadIdx.x < SCAL_FLOATS) C.scal[threadIdx.x] = threadIdx.x == S_RHO ? P.w[5] : 0.f;
     load_iterate(C, P);
     return;
   }
+  if (a.prm.rho_adapt) C.w[5] = C.scal[S_RHO];  // the adapted rho of this SQP iteration
   if (stage == PS_STORE) {
     store_iterate(C, P);
     if (rank == 0 && threadIdx.x == 0) {
@@ -350,6 +352,7 @@ __global__ void __launch_bounds__(NTHR, 1) sqp_plain_stage(int stage, PlainArgs 
     case PS_LS: st_line_search(C, prm.mu, prm.beta, prm.n_alpha, rbuf); break;
     case PS_ACCEPT: {
       const int choice = st_accept(C, prm.beta, prm.n_alpha);
+      if (lead && prm.rho_adapt) C.scal[S_RHO] = rho_next(C.w[5], choice);
       if (lead) {
         if (choice >= 0)
           C.scal[S_MERITF] = C.scal[S_MERITS + choice];

@@ -100,8 +100,16 @@ constexpr int S_MDF = 64;
 static_assert(S_MDF + 2 + 2 * MAX_ALPHA <= SCAL_FLOATS, "merit pairs fit the scalar block");
 enum : int {
   S_KKT = 0, S_MERIT0, S_CMAX, S_GMAX, S_DMAX, S_ALPHA, S_FLAGS, S_PCG, S_ITERS, S_MERITF,
-  S_CHOICE, S_REDBUF, S_DONE, S_NSQP, S_NPCG, S_RFLAGS, S_MERITS = 16  // S_MERITS..+15
+  S_CHOICE, S_REDBUF, S_DONE, S_NSQP, S_NPCG, S_RFLAGS, S_MERITS = 16,  // S_MERITS..+15
+  S_RHO = 32  // the adapted rho between the plain form's launches
 };
+
+// rho after an SQP iteration (Sec. IV-C adjusts it from the line search's
+// outcome): / 3 after an accepted step, * 2 after a rejected one, within
+// [1e-8, 1e8].
+__device__ __forceinline__ float rho_next(float rho, int choice) {
+  return choice >= 0 ? fmaxf(rho / 3.f, 1e-8f) : fminf(rho * 2.f, 1e8f);
+}
 
 // Per-knot strides of the global workspace arrays.
 constexpr int FQS = 49, QIS = 56, DTS = 14 * 8, LIS = 196;
@@ -467,10 +475,12 @@ __device__ __forceinline__ void knot_cost(const Ctx& C, int k) {
     }
 #pragma unroll
     for (int i = 0; i < 49; ++i) Qi[i] = 0.f;
+    // products and sums rounded explicitly: a multiply-add contracted in one
+    // kernel and not in another would round these differently at small rho
 #pragma unroll
     for (int i = 0; i < QM; ++i) {
-      Qi[i * QM + i] = 1.f / (s * wq + rho);
-      Qi[49 + i] = 1.f / (s * wqd + rho);
+      Qi[i * QM + i] = 1.f / __fadd_rn(__fmul_rn(s, wq), rho);
+      Qi[49 + i] = 1.f / __fadd_rn(__fmul_rn(s, wqd), rho);
     }
   } else {
     float p[3], Jp[3 * QM];
@@ -484,16 +494,16 @@ __device__ __forceinline__ void knot_cost(const Ctx& C, int k) {
       qg[i] = s * wee * (Jp[i] * d0 + Jp[QM + i] * d1 + Jp[2 * QM + i] * d2);
 #pragma unroll
       for (int j2 = 0; j2 <= i; ++j2)
-        Hl[i * (i + 1) / 2 + j2] = s * wee * (Jp[i] * Jp[j2] + Jp[QM + i] * Jp[QM + j2] +
-                                              Jp[2 * QM + i] * Jp[2 * QM + j2]) +
-                                   (i == j2 ? rho : 0.f);
+        Hl[i * (i + 1) / 2 + j2] = __fadd_rn(__fmul_rn(s * wee, Jp[i] * Jp[j2] + Jp[QM + i] * Jp[QM + j2] +
+                                                                  Jp[2 * QM + i] * Jp[2 * QM + j2]),
+                                             i == j2 ? rho : 0.f);
     }
 #pragma unroll
     for (int i = 0; i < QM; ++i) {
       const float v = x[QM + i];
       J += 0.5f * s * wqd * v * v;
       qg[QM + i] = s * wqd * v;
-      Qi[49 + i] = 1.f / (s * wqd + rho);
+      Qi[49 + i] = 1.f / __fadd_rn(__fmul_rn(s, wqd), rho);
     }
     // the packed Q_qq, inverted column by column in the next phase
 #pragma unroll

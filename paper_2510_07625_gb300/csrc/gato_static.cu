@@ -123,6 +123,7 @@ extern "C" gato_status gato_solve_noalloc(const gato_model_desc* models, int32_t
       sp.n_alpha < 1 || sp.n_alpha > MAX_ALPHA || !(sp.pcg_eps > 0.f) || sp.pcg_max_iter < 1 ||
       (sp.precond != GATO_PRECOND_STAIR && sp.precond != GATO_PRECOND_JACOBI) ||
       (sp.linsolve != GATO_LINSOLVE_PCG && sp.linsolve != GATO_LINSOLVE_DIRECT) ||
+      (sp.rho_adapt != 0 && sp.rho_adapt != 1) ||
       !std::isfinite(sp.kkt_tol))
     return GATO_E_INVALID;
   DevModel dm[kMaxModels];
@@ -187,6 +188,7 @@ extern "C" gato_status gato_solve_noalloc(const gato_model_desc* models, int32_t
   a.prm.kkt_tol = sp.kkt_tol;
   a.prm.max_iter = max_sqp_iters;
   a.prm.linsolve = sp.linsolve;
+  a.prm.rho_adapt = sp.rho_adapt;
   a.timing = nullptr;
   a.variant = 0;
   if (launch_fused_grouped(a, order, P->order, Ns, n, stream, LaunchPlan()) != cudaSuccess) {

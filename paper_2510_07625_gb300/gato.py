@@ -49,7 +49,7 @@ class ModelDesc(C.Structure):
 class SolverParams(C.Structure):
     _fields_ = [("mu", C.c_float), ("beta", C.c_float), ("n_alpha", C.c_int32),
                 ("pcg_eps", C.c_float), ("pcg_max_iter", C.c_int32), ("precond", C.c_int32),
-                ("kkt_tol", C.c_float), ("linsolve", C.c_int32)]
+                ("kkt_tol", C.c_float), ("linsolve", C.c_int32), ("rho_adapt", C.c_int32)]
 
 
 class BatchDesc(C.Structure):
