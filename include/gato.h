@@ -95,7 +95,7 @@ typedef struct {
   int32_t rho_adapt;       /* 1: each solve's rho (w[5]) is adjusted after every SQP
                               iteration from its line search (Sec. IV-C): / 3 after an
                               accepted step, * 2 after a rejected one, within
-                              [1e-8, 1e8]; it starts from w[5] at every call.
+                              [1e-8, 1e1]; it starts from w[5] at every call.
                               0 (default): rho fixed */
 } gato_solver_params;
 

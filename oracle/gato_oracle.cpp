@@ -11,27 +11,30 @@
  *
  *   dynamics   RNEA in spatial-vector form (Featherstone); M(q) column j is
  *              ID(q, 0, e_j) without gravity; qdd = M^-1 (tau - ID(q, qd, 0));
- *              semi-implicit Euler (Sec. II-A leaves f open; reading c11).
+ *              semi-implicit Euler (Sec. II-A leaves the integrator open).
  *   gradients  A_k, B_k by forward-mode dual numbers through the whole step.
  *   QP         Eq. 1 (Sec. II-A Step 1), second-order cost, first-order dynamics.
  *   KKT        Eq. 2 with the sign convention of Eq. 1:
- *              [G C^T; C 0][dZ; nu] = [-g; c]   (reading c1).
- *   Schur      Eq. 4-5: S = C G^-1 C^T (the SPD sign, reading c3), blocks
+ *              [G C^T; C 0][dZ; nu] = [-g; c]   (Eq. 2's sign of c is garbled).
+ *   Schur      Eq. 4-5: S = C G^-1 C^T (the SPD sign; the printed minus signs
+ *              on S and Phi^-1 cancel), blocks
  *              Q_0^-1, theta_k, phi_k; rhs = -c - C G^-1 g built from zeta_k.
  *   precond    Eq. 6 stair preconditioner assembled block by block from
  *              theta_k^-1 and phi_k; or block-Jacobi (diagonal only).
  *   PCG        Sec. II-B / III-B, standard preconditioned CG warm-started from
  *              the previous multiplier; stops when the preconditioned residual
- *              relative to the warm start's, sqrt(eta/eta_0), is <= eps (c8),
+ *              relative to the warm start's, sqrt(eta/eta_0), is <= eps,
  *              so the correction to the multiplier is accurate relative to its
  *              own size; no iterations when eta_0 < 1e-30.  Optionally (the
  *              direct alternative Sec. II-B sets against iterative methods) the
  *              same system S nu = rhs by block elimination (ora_blocktri_solve).
- *   recovery   dZ = -G^-1 (g + C^T nu)  (Eq. 4, sign of reading c1).
- *   merit      Eq. 3: J + mu * ||c||_1 (reading c5).
+ *   recovery   dZ = -G^-1 (g + C^T nu)  (Eq. 4, with Eq. 1's sign of c).
+ *   merit      Eq. 3: J + mu * ||c||_1 (mu = 10 by default).
  *   line srch  Eq. 7: alpha_i = beta^-i, i = 0..A-1, argmin with ties to the
- *              smallest i; rejected when no alpha lowers the merit (c6, c7).
- *   KKT resid  max(||c||_inf, ||g + C^T nu||_inf / max(1, ||g||_inf)) (c17).
+ *              smallest i; rejected when no alpha lowers the merit (the paper leaves
+ *              that case open: the iterate is kept).
+ *   KKT resid  max(||c||_inf, ||g + C^T nu||_inf / max(1, ||g||_inf)) (the paper names no
+ *              formula).
  */
 #include <cmath>
 #include <cstdint>
@@ -72,7 +75,8 @@ typedef struct {
   int32_t max_iter;
   int32_t linsolve;       /* 0 = PCG (Sec. II-B), 1 = direct block elimination */
   int32_t rho_adapt;      /* 1: rho /= 3 after an accepted step, *= 2 after a rejected
-                             one, within [1e-8, 1e8] (Sec. IV-C, reading c25) */
+                             one, within [1e-8, 1e1], the range Sec. IV-C samples
+                             rho over (Fig. 4); no factors are given there */
 } ora_params;
 
 typedef struct {
@@ -535,7 +539,7 @@ struct Schur {
 };
 
 Schur form_schur(const Lin& L, int precond) {
-  /* Eq. 5-6 blocks with the SPD sign (readings c1, c3). */
+  /* Eq. 5-6 blocks with the SPD sign S = C G^-1 C^T. */
   Schur S;
   int N = L.N, nx = L.nx, nu = L.nu;
   S.N = N; S.nx = nx; S.ok = true;
@@ -891,7 +895,7 @@ int32_t ora_solve(const ora_model* m, const ora_problem* p, const ora_params* pr
       R.flags |= 4;
     }
     if (prm->rho_adapt)
-      pr.w[5] = choice >= 0 ? std::max(pr.w[5] / 3.0, 1e-8) : std::min(pr.w[5] * 2.0, 1e8);
+      pr.w[5] = choice >= 0 ? std::max(pr.w[5] / 3.0, 1e-8) : std::min(pr.w[5] * 2.0, 1e1);
     if (log_alpha && it < prm->max_iter) log_alpha[it] = choice;
     if (log_pcg && it < prm->max_iter) log_pcg[it] = pit;
     if (log_m1 && it < prm->max_iter) log_m1[it] = R.merit;

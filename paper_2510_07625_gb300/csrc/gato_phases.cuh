@@ -106,9 +106,9 @@ enum : int {
 
 // rho after an SQP iteration (Sec. IV-C adjusts it from the line search's
 // outcome): / 3 after an accepted step, * 2 after a rejected one, within
-// [1e-8, 1e8].
+// [1e-8, 1e1].
 __device__ __forceinline__ float rho_next(float rho, int choice) {
-  return choice >= 0 ? fmaxf(rho / 3.f, 1e-8f) : fminf(rho * 2.f, 1e8f);
+  return choice >= 0 ? fmaxf(rho / 3.f, 1e-8f) : fminf(rho * 2.f, 1e1f);
 }
 
 // Per-knot strides of the global workspace arrays.
@@ -600,7 +600,8 @@ __device__ inline void st_dyn_jacobians(const Ctx& C) {
   }
 }
 
-// KKT residual (reading c17) and the merit of the current iterate (Eq. 3).
+// KKT residual max(||c||_inf, ||g + C^T nu||_inf / max(1, ||g||_inf)) at this
+// linearisation with the last multiplier, and the merit of the current iterate (Eq. 3).
 // Also stores the dual residual d = g + C^T nu, accumulated with compensated
 // sums: near convergence d is a small difference of O(|nu|) terms, and the
 // step is recovered from it through G^-1 (R^-1 = 1/w_u amplifies its error).
@@ -678,7 +679,8 @@ __device__ inline void st_kkt_merit(const Ctx& C, float mu, int& rbuf) {
 
 // ------------------------------------------------------ stage 2: Schur form
 
-// Eq. 5-6 blocks (reading c1/c3 signs):  L_k = phi_{k-1} = -A_{k-1} Q_{k-1}^-1,
+// Eq. 5-6 blocks (S = C G^-1 C^T, the SPD sign; the overall minus signs
+// printed on S and Phi^-1 cancel):  L_k = phi_{k-1} = -A_{k-1} Q_{k-1}^-1,
 // D_k = theta_{k-1} = A Q^-1 A^T + B R^-1 B^T + Q_k^-1 (D_0 = Q_0^-1).
 // Right-hand side for the multiplier correction dnu = nu - nu_0: zeta_k and
 // gamma of Eq. 5 with the gradient g replaced by the dual residual
@@ -951,8 +953,9 @@ __device__ __forceinline__ void cluster_df_sum3(float* red, int rank, int csize,
 // Preconditioned CG (Sec. II-B, III-B) for the multiplier correction
 // S dnu = rhs, started from dnu = 0; nu_0 + dnu equals the warm-started PCG
 // iterate on S nu = gamma.  Stair preconditioner (Eq. 6) applied as
-// D^-1 - D^-1 O D^-1 (reading c4).  Stops when sqrt(eta / eta_0) <= eps with
-// eta = r'u (reading c8).  Returns iterations.
+// D^-1 - D^-1 O D^-1 (Eq. 6 written exactly in factored form).  Stops when
+// sqrt(eta / eta_0) <= eps with eta = r'u and eta_0 from the warm start, none
+// when eta_0 < 1e-30.  Returns iterations.
 //
 // Evaluation order: a single-reduction arrangement of PCG whose iterates
 // equal standard PCG's in exact arithmetic.  S is applied to u = Phi r
@@ -1440,7 +1443,7 @@ __device__ __forceinline__ void st_direct(const Ctx& C) {
 }
 
 // dx_k = -Q_k^-1 (q_k + nu_k - A_k^T nu_{k+1}), du_k = -R_k^-1 (r_k - B_k^T nu_{k+1})
-// (Eq. 4, reading c1), evaluated as -G^-1 (d + C^T dnu); then nu += dnu.
+// (Eq. 4 with Eq. 1's sign convention C dZ = c), evaluated as -G^-1 (d + C^T dnu); then nu += dnu.
 __device__ inline void st_recover(const Ctx& C) {
   const int N = C.N;
   const float h = C.h;
@@ -1604,7 +1607,8 @@ __device__ __forceinline__ bool df_less(const float* a, const float* b) {
   return a[0] < b[0] || (a[0] == b[0] && a[1] < b[1]);
 }
 
-// Argmin with ties to the smallest index; accept only a strict decrease (c7).
+// Argmin with ties to the smallest index; accept only a strict decrease
+// (the paper does not say what happens when no step size lowers the merit).
 // The base merit is the accepted trial's (the same evaluation of the same
 // point), so trial and base merits always come from the same code.
 __device__ inline int st_accept(const Ctx& C, float beta, int n_alpha) {

@@ -543,7 +543,7 @@ class Graph:
 
 
 def cold_start_arrays(prob):
-    """Initial guess of reading c14: X_k = x_s, U = 0, lambda = 0 (float32)."""
+    """Cold-start initial guess (the paper gives none): X_k = x_s, U = 0, lambda = 0 (float32)."""
     nx, nu = 2 * prob.model.dof, prob.model.dof
     X = np.tile(np.asarray(prob.x_s, np.float32), (prob.N + 1, 1))
     U = np.zeros((prob.N, nu), np.float32)

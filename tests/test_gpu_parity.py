@@ -206,7 +206,7 @@ def fp32_eval_error(lin, r32, r64):
 
 
 def kkt_correction(lin, c, dx, du):
-    """delta Z solving [G C^T; C 0][dZ; dnu] = [-d; c] (Eq. 2, reading c1) densely."""
+    """delta Z solving [G C^T; C 0][dZ; dnu] = [-d; c] (Eq. 2 with Eq. 1's sign of c) densely."""
     from tests.test_oracle_kkt import dense_kkt
     Gm, g, Cm, _, xi, ui = dense_kkt(lin)
     N, nx, nu = lin["B"].shape

@@ -1,7 +1,7 @@
 """Per-solve rho adaptation (gato_solver_params.rho_adapt; Sec. IV-C adjusts
-rho after each SQP iteration from the line search's outcome; reading c25:
-rho / 3 after an accepted step, rho * 2 after a rejected one, within
-[1e-8, 1e8]) on the GPU.
+rho after each SQP iteration from the line search's outcome; here rho / 3
+after an accepted step, rho * 2 after a rejected one, within Fig. 4's range
+[1e-8, 1e1]) on the GPU.
 
 * fused kernel and plain form agree with the adaptation on (bit for bit for
   the first five iterations of these runs, to FP32 accuracy after);
@@ -65,7 +65,7 @@ def test_rho_adapt_replays_the_rule(G, oracle, seed, rho0):
         outcomes.append(accepted)
         X, U, lam = (g[k].astype(np.float32) for k in ("X", "U", "lam"))
         rho = (np.maximum(rho / np.float32(3.0), np.float32(1e-8)) if accepted
-               else np.minimum(rho * np.float32(2.0), np.float32(1e8)))
+               else np.minimum(rho * np.float32(2.0), np.float32(1e1)))
     assert any(outcomes)
     np.testing.assert_array_equal(full["X"], X)
     np.testing.assert_array_equal(full["U"], U)

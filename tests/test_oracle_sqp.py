@@ -147,8 +147,8 @@ def test_direct_linear_solve_equals_converged_pcg(oracle):
 
 def test_rho_adaptation_rule(oracle):
     # Sec. IV-C adjusts rho after each SQP iteration from the line search's
-    # outcome; reading c25: rho / 3 after an accepted step, rho * 2 after a
-    # rejected one, within [1e-8, 1e8].  The adapted run equals single
+    # outcome (no factors given); here rho / 3 after an accepted step, rho * 2
+    # after a rejected one, within the range [1e-8, 1e1] of Fig. 4.  The adapted run equals single
     # iterations with rho set by that rule between them.
     import dataclasses
 
@@ -164,6 +164,6 @@ def test_rho_adaptation_rule(oracle):
         r = oracle.solve(q, 1, X=X, U=U, lam=lam)
         assert r["alpha_idx"][0] == full["alpha_idx"][it]
         X, U, lam = r["X"], r["U"], r["lam"]
-        rho = max(rho / 3.0, 1e-8) if r["alpha_idx"][0] >= 0 else min(rho * 2.0, 1e8)
+        rho = max(rho / 3.0, 1e-8) if r["alpha_idx"][0] >= 0 else min(rho * 2.0, 1e1)
     np.testing.assert_allclose(full["X"], X, rtol=0, atol=1e-12 * max(1.0, np.abs(X).max()))
     np.testing.assert_allclose(full["U"], U, rtol=0, atol=1e-12 * max(1.0, np.abs(U).max()))
