@@ -216,6 +216,7 @@ def run_gpu(args):
     if rank == 0:
         lat = latency_runs(gato, I, torch, stream, flush, launch_cfg=True)
         direct = direct_solver_runs(gato, I, torch, stream, flush)
+        rho = rho_sampling(gato, I, torch, stream)
         plain = plain_form(gato, I, torch)
         uneven = uneven_graph(gato, I, torch)
         serve = serving_runs(gato, I)
@@ -231,7 +232,7 @@ def run_gpu(args):
                        "B": B_MAIN, "N": N_MAIN, "sqp_iters": ITERS, "dof": 7,
                        "parallelism": f"replicas x{ws}", "l2": "flushed between timed launches (512 MB write)",
                        "launch": launch},
-            "latency_ms": lat, "direct_linear_solve": direct, "plain_gpu_form": plain,
+            "latency_ms": lat, "direct_linear_solve": direct, "rho_sampling": rho, "plain_gpu_form": plain,
             "uneven_graph": uneven, "serving": serve,
             "speedup_vs_plain_B32": round(lat["B32_iters10"]["solves_per_s"] / plain["solves_per_s_B32"], 2),
             "speedup_vs_plain_B256": round(value / ws / plain[f"solves_per_s_B{B_MAIN}"], 2),
@@ -252,9 +253,9 @@ def run_gpu(args):
 
 # DRAM bytes per launch of the dominant kernel on this workload (latency form,
 # 33 knots per CTA), from the ncu capture summarised in
-# profiles/sqp_fused_b256_n64_metrics.md: 17,303,296 read + 6,251,264 written.
+# profiles/sqp_fused_b256_n64_metrics.md: 18,278,400 read + 6,587,136 written.
 # Set to None when the kernel changes until it is measured again.
-TRAFFIC_BYTES = 23554560
+TRAFFIC_BYTES = 24865536
 
 
 def latency_runs(gato, I, torch, stream, flush, n_calls=200, launch_cfg=False, **prm):
@@ -316,6 +317,42 @@ def direct_solver_runs(gato, I, torch, stream, flush, steps=10):
     out["B256_iters10"] = {"ms_per_call": round(t, 4), "solves_per_s": round(B_MAIN / (t / 1e3), 1),
                            "kkt_max": round(max(res[i].kkt_residual for i in range(dp.n)), 6)}
     B.close()
+    return out
+
+
+def rho_sampling(gato, I, torch, stream, M=32, iters=(1, 5, 20, 100)):
+    """Sampling the damping rho over a batch (Sec. IV-C's case study on the
+    synthetic arm): one start (7-DoF, joint cost, N = 64, h = 0.05), M solves
+    with rho log-spaced over [1e-8, 1e1] against one solve with rho = 0.1,
+    both adapting rho after every iteration, from the cold start.  For each
+    iteration count: the best merit reached (over the solves without the
+    non-finite flag), how many ended non-finite, and the time per call."""
+    import dataclasses
+
+    import numpy as np
+
+    base = I.joint_problem(0, I.arm7(), N_MAIN, 0.05)
+    out = {"M": M, "by_iters": []}
+    for it in iters:
+        row = {"sqp_iters": it}
+        for name, rhos in (("batch", np.logspace(-8, 1, M)), ("single", [0.1])):
+            probs = [dataclasses.replace(base, w=tuple(base.w[:5]) + (float(r),)) for r in rhos]
+            B = gato.Batch([I.arm7()], len(probs), N_MAIN, stream=stream.cuda_stream, rho_adapt=1)
+            dp = gato.DeviceProblems(B, probs)
+            dp.reset()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            gato.gato_solve(B.handle, dp.arr, dp.n, it, None)
+            e1.record(stream)
+            B.sync()
+            res = gato.gato_get_results(B.handle, dp.n)
+            merits = [res[i].merit for i in range(dp.n) if not (res[i].flags & gato.SOLVE_NONFINITE)]
+            row[name] = {"ms_per_call": round(e0.elapsed_time(e1), 3),
+                         "best_merit": round(float(min(merits)), 6) if merits else None,
+                         "nonfinite": dp.n - len(merits)}
+            B.close()
+        out["by_iters"].append(row)
     return out
 
 
