@@ -40,7 +40,8 @@ class OraModel(C.Structure):
 class OraProblem(C.Structure):
     _fields_ = [("N", C.c_int32), ("cost_kind", C.c_int32), ("dt", C.c_double),
                 ("x_s", C.POINTER(C.c_double)), ("x_ref", C.POINTER(C.c_double)),
-                ("ee_ref", C.POINTER(C.c_double)), ("w", C.c_double * 6)]
+                ("ee_ref", C.POINTER(C.c_double)), ("w", C.c_double * 6),
+                ("f_ext", C.c_double * 3)]
 
 
 class OraParams(C.Structure):
@@ -79,11 +80,12 @@ def lib():
         pp = C.POINTER(OraProblem)
         L.ora_rnea.argtypes = [mp, dp, dp, dp, C.c_int32, dp]
         L.ora_mass_matrix.argtypes = [mp, dp, dp]
-        L.ora_forward_dynamics.argtypes = [mp, dp, dp, dp, dp]
+        L.ora_forward_dynamics.argtypes = [mp, dp, dp, dp, dp, dp]
         L.ora_forward_dynamics.restype = C.c_int32
-        L.ora_step.argtypes = [mp, dp, dp, C.c_double, dp]
+        L.ora_step.argtypes = [mp, dp, dp, C.c_double, dp, dp]
         L.ora_step.restype = C.c_int32
-        L.ora_step_jacobians.argtypes = [mp, dp, dp, C.c_double, dp, dp]
+        L.ora_step_jacobians.argtypes = [mp, dp, dp, C.c_double, dp, dp, dp]
+        L.ora_ee_joint_torque.argtypes = [mp, dp, dp, dp]
         L.ora_fk.argtypes = [mp, dp, dp, dp]
         L.ora_merit.argtypes = [mp, pp, dp, dp, C.c_double]
         L.ora_merit.restype = C.c_double
@@ -153,6 +155,8 @@ class _Prob:
         p.ee_ref = _d(self.ee_ref) if self.ee_ref is not None else C.POINTER(C.c_double)()
         for i in range(6):
             p.w[i] = prob.w[i]
+        for i, f in enumerate(getattr(prob, "f_ext", (0.0, 0.0, 0.0))):
+            p.f_ext[i] = f
         self.p = p
         self.N = prob.N
         self.nx = 2 * prob.model.dof
@@ -178,30 +182,47 @@ def mass_matrix(model, q):
     return M
 
 
-def forward_dynamics(model, q, qd, tau):
+def _fext(f_ext):
+    return C.POINTER(C.c_double)() if f_ext is None else _d(_arr(f_ext))
+
+
+def forward_dynamics(model, q, qd, tau, f_ext=None):
+    """qdd from M(q) qdd = tau + J_p(q)^T f_ext - ID(q, qd, 0)."""
     n = model.dof
     out = np.zeros(n)
     m = make_model(model)
-    rc = lib().ora_forward_dynamics(C.byref(m), _d(_arr(q)), _d(_arr(qd)), _d(_arr(tau)), _d(out))
+    fe = None if f_ext is None else _arr(f_ext)
+    rc = lib().ora_forward_dynamics(C.byref(m), _d(_arr(q)), _d(_arr(qd)), _d(_arr(tau)),
+                                    _fext(fe), _d(out))
     if rc != 0:
         raise FloatingPointError("mass matrix not positive definite")
     return out
 
 
-def step(model, x, u, h):
+def step(model, x, u, h, f_ext=None):
     out = np.zeros(2 * model.dof)
     m = make_model(model)
-    lib().ora_step(C.byref(m), _d(_arr(x)), _d(_arr(u)), h, _d(out))
+    fe = None if f_ext is None else _arr(f_ext)
+    lib().ora_step(C.byref(m), _d(_arr(x)), _d(_arr(u)), h, _fext(fe), _d(out))
     return out
 
 
-def step_jacobians(model, x, u, h):
+def step_jacobians(model, x, u, h, f_ext=None):
     nx, nu = 2 * model.dof, model.dof
     A = np.zeros((nx, nx))
     B = np.zeros((nx, nu))
     m = make_model(model)
-    lib().ora_step_jacobians(C.byref(m), _d(_arr(x)), _d(_arr(u)), h, _d(A), _d(B))
+    fe = None if f_ext is None else _arr(f_ext)
+    lib().ora_step_jacobians(C.byref(m), _d(_arr(x)), _d(_arr(u)), h, _fext(fe), _d(A), _d(B))
     return A, B
+
+
+def ee_joint_torque(model, q, f):
+    """J_p(q)^T f: joint torques of a base-frame force f at the end effector."""
+    tau = np.zeros(model.dof)
+    m = make_model(model)
+    lib().ora_ee_joint_torque(C.byref(m), _d(_arr(q)), _d(_arr(f)), _d(tau))
+    return tau
 
 
 def fk(model, q, jacobian=False):

@@ -62,6 +62,8 @@ typedef struct {
   const double* x_ref;    /* [(N+1)*nx] or NULL */
   const double* ee_ref;   /* [(N+1)*3] or NULL */
   double w[6];            /* wq, wqd, wr, terminal scale, wee, rho */
+  double f_ext[3];        /* constant external force on the end effector, base
+                             frame (Sec. IV-C's disturbance hypotheses); zeros = none */
 } ora_problem;
 
 typedef struct {
@@ -316,21 +318,59 @@ bool cholesky_solve(int n, std::vector<T> A, T* b) {
 }
 
 template <class T>
-bool forward_dynamics(const ora_model& m, const T* q, const T* qd, const T* tau, T* qdd) {
+void ee_joint_torque(const ora_model& m, const T* q, const double* f, T* tau) {
+  /* Joint torques of a force f (base frame) acting at the end-effector point:
+   * tau = J_p(q)^T f with the geometric Jacobian of a revolute chain, column
+   * i = z_i x (p_ee - o_i), z_i and o_i joint i's axis and origin in the base
+   * frame (the frames chained as in fk_ee). */
   int n = m.dof;
-  std::vector<T> M(n * n), z(n, T(0.0)), bias(n);
+  T R[3][3], pos[3];
+  std::vector<V3<T>> z(n), o(n);
+  for (int i = 0; i < 3; ++i) { pos[i] = T(0.0); for (int j = 0; j < 3; ++j) R[i][j] = T(i == j ? 1.0 : 0.0); }
+  for (int i = 0; i <= n; ++i) {
+    double L = (i == 0) ? 0.0 : m.link_len[i - 1];
+    for (int r = 0; r < 3; ++r) pos[r] = pos[r] + R[r][2] * T(L);
+    if (i == n) break;
+    M3<T> E = rot_coord(m.axis[i], q[i]);
+    T Rn[3][3];
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) {
+        T s = T(0.0);
+        for (int l = 0; l < 3; ++l) s = s + R[r][l] * E.a[c][l];
+        Rn[r][c] = s;
+      }
+    for (int r = 0; r < 3; ++r) for (int c = 0; c < 3; ++c) R[r][c] = Rn[r][c];
+    /* joint i turns about its own frame's axis, which the rotation leaves fixed */
+    for (int r = 0; r < 3; ++r) { z[i].a[r] = R[r][m.axis[i]]; o[i].a[r] = pos[r]; }
+  }
+  for (int i = 0; i < n; ++i) {
+    T d[3] = {pos[0] - o[i].a[0], pos[1] - o[i].a[1], pos[2] - o[i].a[2]};
+    V3<T> col = cross3(z[i].a, d);
+    tau[i] = col.a[0] * T(f[0]) + col.a[1] * T(f[1]) + col.a[2] * T(f[2]);
+  }
+}
+
+template <class T>
+bool forward_dynamics(const ora_model& m, const T* q, const T* qd, const T* tau, T* qdd,
+                      const double* f_ext = nullptr) {
+  /* M(q) qdd = tau + J_p(q)^T f_ext - ID(q, qd, 0). */
+  int n = m.dof;
+  std::vector<T> M(n * n), z(n, T(0.0)), bias(n), te(n, T(0.0));
   mass_matrix(m, q, M.data());
   rnea(m, q, qd, z.data(), true, bias.data());
-  for (int i = 0; i < n; ++i) qdd[i] = tau[i] - bias[i];
+  if (f_ext && (f_ext[0] != 0.0 || f_ext[1] != 0.0 || f_ext[2] != 0.0))
+    ee_joint_torque(m, q, f_ext, te.data());
+  for (int i = 0; i < n; ++i) qdd[i] = tau[i] + te[i] - bias[i];
   return cholesky_solve(n, M, qdd);
 }
 
 template <class T>
-bool step(const ora_model& m, const T* x, const T* u, double h, T* xn) {
+bool step(const ora_model& m, const T* x, const T* u, double h, T* xn,
+          const double* f_ext = nullptr) {
   /* Semi-implicit Euler: qd+ = qd + h qdd, q+ = q + h qd+. */
   int n = m.dof;
   std::vector<T> qdd(n);
-  bool ok = forward_dynamics(m, x, x + n, u, qdd.data());
+  bool ok = forward_dynamics(m, x, x + n, u, qdd.data(), f_ext);
   for (int i = 0; i < n; ++i) {
     T qdn = x[n + i] + T(h) * qdd[i];
     xn[n + i] = qdn;
@@ -340,14 +380,14 @@ bool step(const ora_model& m, const T* x, const T* u, double h, T* xn) {
 }
 
 void step_jacobians(const ora_model& m, const double* x, const double* u, double h,
-                    double* A, double* B) {
+                    double* A, double* B, const double* f_ext = nullptr) {
   /* A = d step / d x (nx x nx), B = d step / d u (nx x nu), one dual pass per column. */
   int n = m.dof, nx = 2 * n;
   std::vector<Dual> xd(nx), ud(n), out(nx);
   for (int j = 0; j < nx + n; ++j) {
     for (int l = 0; l < nx; ++l) xd[l] = Dual(x[l], (j == l) ? 1.0 : 0.0);
     for (int l = 0; l < n; ++l) ud[l] = Dual(u[l], (j == nx + l) ? 1.0 : 0.0);
-    step(m, xd.data(), ud.data(), h, out.data());
+    step(m, xd.data(), ud.data(), h, out.data(), f_ext);
     for (int i = 0; i < nx; ++i) {
       if (j < nx) A[i * nx + j] = out[i].d;
       else B[i * n + (j - nx)] = out[i].d;
@@ -496,9 +536,9 @@ Lin linearize(const ora_model& m, const ora_problem& p, const double* X, const d
   for (int k = 0; k < N; ++k) {
     const double* x = X + (size_t)k * nx;
     const double* u = U + (size_t)k * n;
-    if (!step(m, x, u, p.dt, xn.data())) L.ok = false;
+    if (!step(m, x, u, p.dt, xn.data(), p.f_ext)) L.ok = false;
     for (int i = 0; i < nx; ++i) L.c[(size_t)(k + 1) * nx + i] = xn[i] - X[(size_t)(k + 1) * nx + i];
-    step_jacobians(m, x, u, p.dt, &L.A[(size_t)k * nx * nx], &L.B[(size_t)k * nx * n]);
+    step_jacobians(m, x, u, p.dt, &L.A[(size_t)k * nx * nx], &L.B[(size_t)k * nx * n], p.f_ext);
     L.J += knot_cost(m, p, k, x, u, &L.q[(size_t)k * nx], &L.Q[(size_t)k * nx * nx],
                      &L.r[(size_t)k * n], &L.R[(size_t)k * n * n]);
   }
@@ -518,7 +558,7 @@ double merit(const ora_model& m, const ora_problem& p, const double* X, const do
   for (int k = 0; k < N; ++k) {
     const double* x = X + (size_t)k * nx;
     const double* u = U + (size_t)k * n;
-    if (!step(m, x, u, p.dt, xn.data())) good = false;
+    if (!step(m, x, u, p.dt, xn.data(), p.f_ext)) good = false;
     for (int i = 0; i < nx; ++i) c1 += std::fabs(xn[i] - X[(size_t)(k + 1) * nx + i]);
     J += knot_cost(m, p, k, x, u, nullptr, nullptr, nullptr, nullptr);
   }
@@ -733,18 +773,24 @@ void ora_rnea(const ora_model* m, const double* q, const double* qd, const doubl
 
 void ora_mass_matrix(const ora_model* m, const double* q, double* M) { mass_matrix(*m, q, M); }
 
+/* f_ext: NULL or the 3 components of a force at the end effector (base frame). */
 int32_t ora_forward_dynamics(const ora_model* m, const double* q, const double* qd,
-                             const double* tau, double* qdd) {
-  return forward_dynamics(*m, q, qd, tau, qdd) ? 0 : -1;
+                             const double* tau, const double* f_ext, double* qdd) {
+  return forward_dynamics(*m, q, qd, tau, qdd, f_ext) ? 0 : -1;
 }
 
-int32_t ora_step(const ora_model* m, const double* x, const double* u, double h, double* xn) {
-  return step(*m, x, u, h, xn) ? 0 : -1;
+int32_t ora_step(const ora_model* m, const double* x, const double* u, double h,
+                 const double* f_ext, double* xn) {
+  return step(*m, x, u, h, xn, f_ext) ? 0 : -1;
 }
 
 void ora_step_jacobians(const ora_model* m, const double* x, const double* u, double h,
-                        double* A, double* B) {
-  step_jacobians(*m, x, u, h, A, B);
+                        const double* f_ext, double* A, double* B) {
+  step_jacobians(*m, x, u, h, A, B, f_ext);
+}
+
+void ora_ee_joint_torque(const ora_model* m, const double* q, const double* f, double* tau) {
+  ee_joint_torque(*m, q, f, tau);
 }
 
 void ora_fk(const ora_model* m, const double* q, double* p, double* J) {

@@ -137,6 +137,9 @@ class Problem:
     ee_ref: np.ndarray | None = None
     seed: int = 0
     meta: dict = field(default_factory=dict)
+    # constant external force on the end effector (base frame, N); Sec. IV-C's
+    # disturbance hypotheses differ only in it
+    f_ext: tuple = (0.0, 0.0, 0.0)
 
 
 def figure_eight(t: np.ndarray) -> np.ndarray:
@@ -250,3 +253,28 @@ def state_disturbance(rng: np.random.Generator, nq: int, sigma_q: float = 0.05,
                       sigma_qd: float = 0.1) -> np.ndarray:
     """Gaussian disturbance added to the measured state between control ticks."""
     return np.concatenate([rng.normal(0.0, sigma_q, nq), rng.normal(0.0, sigma_qd, nq)])
+
+
+def force_hypotheses(seed: int, M: int, center=(0.0, 0.0, 0.0), radius: float = 10.0) -> np.ndarray:
+    """M candidate end-effector forces (N, base frame) around an estimate.
+
+    Sec. IV-C samples directions uniformly on the sphere and adds them, scaled,
+    to the current disturbance estimate.  Row 0 is the estimate itself; rows
+    1..M-1 are ``center + radius * d`` with ``d`` a normalised standard-normal
+    draw (uniform on the sphere).  Draws: an (M-1, 3) normal block.
+    """
+    rng = np.random.default_rng(seed)
+    d = rng.normal(0.0, 1.0, (max(M - 1, 0), 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    out = np.empty((M, 3))
+    out[0] = center
+    out[1:] = np.asarray(center, dtype=float) + radius * d
+    return out
+
+
+def disturbed_ee_problem(seed: int, f_ext, model: ArmModel | None = None, N: int = 64,
+                         dt: float = 0.01) -> Problem:
+    """``ee_problem`` (figure-eight tracking) with a constant end-effector force."""
+    p = ee_problem(seed, model, N, dt)
+    p.f_ext = tuple(float(v) for v in f_ext)
+    return p

@@ -225,3 +225,124 @@ def test_fk_jacobian_and_points(oracle):
         d[j] = eps
         col = (oracle.fk(model, q + d) - oracle.fk(model, q - d)) / (2 * eps)
         np.testing.assert_allclose(J[:, j], col, atol=1e-8)
+
+
+# ------------------------------------------- external end-effector force
+# Sec. IV-C's hypotheses differ only in a constant force on the end effector;
+# the dynamics become M(q) qdd = tau + J_p(q)^T f - ID(q, qd, 0).
+
+ARMS_AND_CHAINS = [I.arm7(), I.arm6()] + CHAINS
+
+
+@pytest.mark.parametrize("model", ARMS_AND_CHAINS, ids=lambda m: m.name)
+def test_ee_force_torque_is_fk_jacobian_transpose(oracle, model):
+    """J_p^T f against the FK Jacobian (dual numbers through the FK chain) and
+    against central differences of the FK position."""
+    rng = np.random.default_rng(21)
+    n = model.dof
+    for _ in range(4):
+        q = rng.uniform(-2, 2, n)
+        f = rng.uniform(-50, 50, 3)
+        _, J = oracle.fk(model, q, jacobian=True)
+        np.testing.assert_allclose(oracle.ee_joint_torque(model, q, f), J.T @ f, rtol=1e-12, atol=1e-12)
+        eps = 1e-6
+        Jn = np.zeros((3, n))
+        for j in range(n):
+            d = np.zeros(n)
+            d[j] = eps
+            Jn[:, j] = (oracle.fk(model, q + d) - oracle.fk(model, q - d)) / (2 * eps)
+        np.testing.assert_allclose(oracle.ee_joint_torque(model, q, f), Jn.T @ f, rtol=1e-7, atol=1e-7)
+
+
+def _with_tip_mass(model, mp):
+    """The same chain with a point mass mp added at the end-effector point."""
+    n = model.dof
+    L = model.link_len[n - 1]
+    m0 = model.mass[n - 1]
+    c0 = np.array(model.com[3 * (n - 1):3 * n])
+    c1 = (m0 * c0 + mp * np.array([0.0, 0.0, L])) / (m0 + mp)
+    mass = list(model.mass)
+    mass[n - 1] = m0 + mp
+    com = list(model.com)
+    com[3 * (n - 1):3 * n] = list(c1)
+    return I.ArmModel(n, model.axis, model.link_len, tuple(mass), tuple(com), model.inertia,
+                      model.gravity, model.name + "_tipmass")
+
+
+@pytest.mark.parametrize("model", [I.arm7(), I.arm6(), CHAINS[3]], ids=lambda m: m.name)
+def test_ee_force_equals_tip_weight_in_statics(oracle, model):
+    """At rest, a downward force m_p g on the end effector loads the joints like
+    a point mass m_p there: the holding torques of the chain with the mass
+    (inverse dynamics, gravity on) balance the chain without it plus the force,
+    so its forward dynamics gives zero acceleration."""
+    rng = np.random.default_rng(4)
+    n = model.dof
+    mp = 1.7
+    heavy = _with_tip_mass(model, mp)
+    f = np.array([0.0, 0.0, -mp * model.gravity])
+    z = np.zeros(n)
+    for _ in range(4):
+        q = rng.uniform(-2, 2, n)
+        hold = oracle.rnea(heavy, q, z, z)
+        np.testing.assert_allclose(oracle.rnea(model, q, z, z) - oracle.ee_joint_torque(model, q, f), hold,
+                                   rtol=1e-12, atol=1e-11)
+        np.testing.assert_allclose(oracle.forward_dynamics(model, q, z, hold, f_ext=f), z, atol=1e-10)
+        # without the force the same torques accelerate the arm
+        assert np.abs(oracle.forward_dynamics(model, q, z, hold)).max() > 1e-3
+
+
+def _rk4_force(oracle, model, x, tau, f, h):
+    n = model.dof
+
+    def fn(y):
+        return np.concatenate([y[n:], oracle.forward_dynamics(model, y[:n], y[n:], tau, f_ext=f)])
+    k1 = fn(x)
+    k2 = fn(x + 0.5 * h * k1)
+    k3 = fn(x + 0.5 * h * k2)
+    k4 = fn(x + h * k3)
+    return x + h / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
+
+
+def test_energy_conservation_with_constant_ee_force(oracle):
+    """A constant force is conservative with potential -f . p_ee: tau = 0, RK4
+    at h = 1e-4 for 0.25 s keeps T + V_gravity - f . p_ee; the force's work is
+    far above the drift bound."""
+    model = I.chain([2, 1, 1], [0.3, 0.3, 0.3], [2.0, 2.0, 2.0], name="3zyy")
+    f = np.array([12.0, -7.0, -30.0])
+    x = np.array([0.3, 0.6, -0.4, 1.0, 0.0, 0.5])
+
+    def energy(y):
+        return _energy(oracle, model, y) - f @ oracle.fk(model, y[:3])
+    E0 = energy(x)
+    W0 = f @ oracle.fk(model, x[:3])
+    scale = sum(model.mass) * model.gravity * sum(model.link_len)
+    for _ in range(2500):
+        x = _rk4_force(oracle, model, x, np.zeros(3), f, 1e-4)
+    assert abs(energy(x) - E0) / scale < 1e-8
+    assert abs(f @ oracle.fk(model, x[:3]) - W0) / scale > 1e-3
+
+
+@pytest.mark.parametrize("model", [I.arm7(), I.arm6()], ids=lambda m: m.name)
+def test_step_jacobians_with_ee_force_match_central_differences(oracle, model):
+    rng = np.random.default_rng(15)
+    n = model.dof
+    x = np.concatenate([rng.uniform(-1, 1, n), rng.uniform(-2, 2, n)])
+    u = rng.uniform(-10, 10, n)
+    f = np.array([20.0, -10.0, -50.0])
+    h = 0.01
+    A, B = oracle.step_jacobians(model, x, u, h, f_ext=f)
+    A0, _ = oracle.step_jacobians(model, x, u, h)
+    eps = 1e-6
+    An = np.zeros_like(A)
+    Bn = np.zeros_like(B)
+    for j in range(2 * n):
+        d = np.zeros(2 * n)
+        d[j] = eps
+        An[:, j] = (oracle.step(model, x + d, u, h, f_ext=f) - oracle.step(model, x - d, u, h, f_ext=f)) / (2 * eps)
+    for j in range(n):
+        d = np.zeros(n)
+        d[j] = eps
+        Bn[:, j] = (oracle.step(model, x, u + d, h, f_ext=f) - oracle.step(model, x, u - d, h, f_ext=f)) / (2 * eps)
+    np.testing.assert_allclose(A, An, rtol=1e-6, atol=1e-8)
+    np.testing.assert_allclose(B, Bn, rtol=1e-6, atol=1e-8)
+    assert np.abs(A - A0).max() > 1e-4  # the force's q-dependence reaches A

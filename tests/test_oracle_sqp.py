@@ -167,3 +167,25 @@ def test_rho_adaptation_rule(oracle):
         rho = max(rho / 3.0, 1e-8) if r["alpha_idx"][0] >= 0 else min(rho * 2.0, 1e1)
     np.testing.assert_allclose(full["X"], X, rtol=0, atol=1e-12 * max(1.0, np.abs(X).max()))
     np.testing.assert_allclose(full["U"], U, rtol=0, atol=1e-12 * max(1.0, np.abs(U).max()))
+
+
+def test_external_force_enters_defects_and_solution(oracle):
+    """A solve with a constant end-effector force (Sec. IV-C's hypotheses):
+    converged, its trajectory follows the forced dynamics (defects of the
+    separately pinned one-step map with the force vanish) and not the free ones,
+    and it differs from the unforced solve's."""
+    import dataclasses
+
+    base = I.joint_problem(3, I.arm6(), 16, 0.02)
+    forced = dataclasses.replace(base, f_ext=(0.0, 0.0, -50.0))
+    rf = oracle.solve(forced, max_iter=30, kkt_tol=1e-9)
+    r0 = oracle.solve(base, max_iter=30, kkt_tol=1e-9)
+    assert rf["flags"] & 1 and r0["flags"] & 1
+    m, n = forced.model, forced.model.dof
+    X, U = rf["X"].reshape(-1, 2 * n), rf["U"].reshape(-1, n)
+    d_forced = max(np.abs(oracle.step(m, X[k], U[k], forced.dt, f_ext=forced.f_ext) - X[k + 1]).max()
+                   for k in range(forced.N))
+    d_free = max(np.abs(oracle.step(m, X[k], U[k], forced.dt) - X[k + 1]).max() for k in range(forced.N))
+    assert d_forced < 1e-8
+    assert d_free > 1e-3
+    assert np.abs(rf["U"] - r0["U"]).max() > 1.0  # the controls push back against the force
