@@ -114,6 +114,10 @@ typedef struct {
   float dt;                /* time step h > 0 */
   int32_t cost_kind;       /* GATO_COST_JOINT or GATO_COST_EE */
   float w[6];              /* weights: q, qd, u, terminal scale, ee, rho (diag damping) */
+  float f_ext[3];          /* constant external force on the end-effector point, base
+                              frame (N): the dynamics become M qdd = u + J_p^T f_ext -
+                              ID(q, qd, 0); zeros = none.  Sec. IV-C's disturbance
+                              hypotheses are solves differing only in it */
   int32_t mem;             /* GATO_MEM_HOST or GATO_MEM_DEVICE for every pointer below */
   const float* x_s;
   const float* x_ref;      /* used when cost_kind == JOINT, else may be NULL */

@@ -174,6 +174,8 @@ gato_status validate_problem(gato_batch* b, const gato_problem& p, int idx) {
   if (!p.x_s || !p.X || !p.U) return bad("x_s, X and U are required");
   for (int i = 0; i < 6; ++i)
     if (!std::isfinite(p.w[i]) || p.w[i] < 0.f) return bad("weights must be finite and >= 0");
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(p.f_ext[i])) return bad("f_ext must be finite");
   const float wq = p.w[0], wqd = p.w[1], wr = p.w[2], ts = p.w[3], rho = p.w[5];
   if (!(wr > 0.f)) return bad("control weight must be > 0");
   if (!(ts > 0.f)) return bad("terminal scale must be > 0");
@@ -242,6 +244,7 @@ gato_status prepare(gato_batch* b, const gato_problem* probs, int n, int* nmax_o
     d.dof = dof;
     d.dt = p.dt;
     for (int k = 0; k < 6; ++k) d.w[k] = p.w[k];
+    for (int k = 0; k < 3; ++k) d.fext[k] = p.f_ext[k];
     nmax = std::max(nmax, N);
     if (p.mem == GATO_MEM_DEVICE) {
       d.x_s = p.x_s;

@@ -40,7 +40,7 @@ struct ProbDesc {
   int model, N, cost_kind, dof;
   float dt;
   float w[6];
-  int pad0;
+  float fext[3];  // constant external force on the end effector (base frame)
   const float* x_s;
   const float* x_ref;
   const float* ee_ref;
@@ -210,11 +210,15 @@ __device__ __forceinline__ Vec3<T> minert(const DevModel& M, int i) {
 }
 
 // Inverse dynamics tau = ID(q, qd, qdd) by RNEA.  sq/cq are sin/cos of q.
-// `grav` is the magnitude of gravity along -z (0 turns it off).  When rec is
-// non-null (float only) the link quantities are stored for a tangent pass.
+// `grav` is the magnitude of gravity along -z (0 turns it off).  fw is a force
+// on the end-effector point (0, 0, L_last) of the last frame, in base
+// coordinates: rotated into each frame on the way out like gravity, it is
+// taken off the last link's force and moment on the way back, so the result is
+// ID - J_p^T fw.  When rec is non-null (float only) the link quantities are
+// stored for a tangent pass.
 template <typename T>
 __device__ __forceinline__ void rnea_value(const DevModel& M, const T* sq, const T* cq, const T* qd,
-                                           const T* qdd, T grav, T* tau, LinkRec* rec) {
+                                           const T* qdd, T grav, Vec3<T> fw, T* tau, LinkRec* rec) {
   using W = Vec3<T>;
   W F[QM], Nm[QM];
   W wp = vzero<T>(), wdp = vzero<T>(), ap = v3t<T>(T(0), T(0), grav);
@@ -249,6 +253,13 @@ __device__ __forceinline__ void rnea_value(const DevModel& M, const T* sq, const
     wdp = wd;
     ap = acc;
   }
+  // the force in the last frame's coordinates, taken off the last link
+  if (fw.x != T(0) || fw.y != T(0) || fw.z != T(0)) {
+#pragma unroll
+    for (int i = 0; i < QM; ++i) fw = rotT(M.axis[i], sq[i], cq[i], fw);
+    F[QM - 1] = F[QM - 1] - fw;
+    Nm[QM - 1] = Nm[QM - 1] - cross(v3t<T>(T(0), T(0), T(M.L[QM - 1])), fw) + cross(mcom<T>(M, QM - 1), fw);
+  }
   W fc = vzero<T>(), nc = vzero<T>();
 #pragma unroll
   for (int i = QM - 1; i >= 0; --i) {
@@ -274,9 +285,11 @@ __device__ __forceinline__ void rnea_value(const DevModel& M, const T* sq, const
 }
 
 // Directional derivative of ID at the stored value pass, along q_j
-// (wrt_qd = false) or qd_j (wrt_qd = true); qdd is held fixed.
+// (wrt_qd = false) or qd_j (wrt_qd = true); qdd is held fixed.  fw is the
+// value pass's end-effector force (base frame): its coordinates in frame i
+// turn with q, so their tangent follows the same rotation rule as gravity's.
 __device__ __forceinline__ void rnea_tangent(const DevModel& M, const LinkRec* R, const float* qd,
-                                             bool wrt_qd, int j, float* dtau) {
+                                             bool wrt_qd, int j, V3 fw, float* dtau) {
   V3 Ft[QM], Nt[QM];
   V3 wpt = vzero(), wdpt = vzero(), apt = vzero();
 #pragma unroll
@@ -302,6 +315,18 @@ __device__ __forceinline__ void rnea_tangent(const DevModel& M, const LinkRec* R
     wpt = wt;
     wdpt = wdt;
     apt = at;
+  }
+  // tangent of the force's last-frame coordinates (only q_j turns them)
+  if (!wrt_qd && (fw.x != 0.f || fw.y != 0.f || fw.z != 0.f)) {
+    V3 fet = vzero();
+#pragma unroll
+    for (int i = 0; i < QM; ++i) {
+      const int a = M.axis[i];
+      fw = rotT(a, R[i].s, R[i].c, fw);
+      fet = rotT(a, R[i].s, R[i].c, fet) - (i == j ? 1.f : 0.f) * ecross(a, fw);
+    }
+    Ft[QM - 1] = Ft[QM - 1] - fet;
+    Nt[QM - 1] = Nt[QM - 1] - cross(v3(0.f, 0.f, M.L[QM - 1]), fet) + cross(mcom(M, QM - 1), fet);
   }
   V3 fct = vzero(), nct = vzero();
 #pragma unroll
@@ -439,9 +464,10 @@ __device__ __forceinline__ void chol7_solve(const float* Lf, float* b) {
   }
 }
 
-// Semi-implicit Euler step (the build's f(x, u, h)): returns qdd as well.
+// Forward dynamics M(q) qdd = u + J_p^T fw - ID(q, qd, 0) of one knot
+// (fw: end-effector force, base frame).
 __device__ __forceinline__ bool forward_dynamics(const DevModel& M, const float* q, const float* qd,
-                                                 const float* u, float* qdd) {
+                                                 const float* u, V3 fw, float* qdd) {
   float sq[QM], cq[QM], Ml[QM * (QM + 1) / 2], z[QM], b[QM];
 #pragma unroll
   for (int i = 0; i < QM; ++i) {
@@ -449,7 +475,7 @@ __device__ __forceinline__ bool forward_dynamics(const DevModel& M, const float*
     z[i] = 0.f;
   }
   mass_matrix_crba(M, sq, cq, Ml);
-  rnea_value(M, sq, cq, qd, z, M.g, b, nullptr);
+  rnea_value(M, sq, cq, qd, z, M.g, fw, b, nullptr);
 #pragma unroll
   for (int i = 0; i < QM; ++i) qdd[i] = u[i] - b[i];
   const bool ok = chol7(Ml);

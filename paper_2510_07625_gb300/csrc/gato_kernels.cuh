@@ -213,7 +213,10 @@ __global__ void __launch_bounds__(NTHR, REG ? 1 : 2) sqp_fused(FusedLaunch a) {
       C.vk0r = C.k1 - 2;
     }
   }
-  if (threadIdx.x < SCAL_FLOATS) scal[threadIdx.x] = 0.f;
+  if (threadIdx.x < SCAL_FLOATS) {  // the force read from the descriptor in memory, not P's copy
+    const int t = threadIdx.x - S_FEXT;
+    scal[threadIdx.x] = (t >= 0 && t < 3) ? a.probs[b].fext[t] : 0.f;
+  }
   for (int i = threadIdx.x; i < 196; i += NTHR) zblock[i] = 0.f;
   __syncthreads();
   sqp_solve<REG>(C, P, a.prm, a.iters, a.results + b);
@@ -266,7 +269,11 @@ __global__ void __launch_bounds__(NTHR, 1) sqp_plain_stage(int stage, PlainArgs 
   int* rflags = reinterpret_cast<int*>(C.scal + S_RFLAGS);
   int rbuf = 0;
   if (stage == PS_LOAD) {
-    if (rank == 0 && threadIdx.x < SCAL_FLOATS) C.scal[threadIdx.x] = threadIdx.x == S_RHO ? P.w[5] : 0.f;
+    if (rank == 0 && threadIdx.x < SCAL_FLOATS) {
+      const int t = threadIdx.x;
+      C.scal[t] = t == S_RHO ? P.w[5]
+                : (t == S_FEXT ? P.fext[0] : (t == S_FEXT + 1 ? P.fext[1] : (t == S_FEXT + 2 ? P.fext[2] : 0.f)));
+    }
     load_iterate(C, P);
     return;
   }

@@ -101,8 +101,14 @@ static_assert(S_MDF + 2 + 2 * MAX_ALPHA <= SCAL_FLOATS, "merit pairs fit the sca
 enum : int {
   S_KKT = 0, S_MERIT0, S_CMAX, S_GMAX, S_DMAX, S_ALPHA, S_FLAGS, S_PCG, S_ITERS, S_MERITF,
   S_CHOICE, S_REDBUF, S_DONE, S_NSQP, S_NPCG, S_RFLAGS, S_MERITS = 16,  // S_MERITS..+15
-  S_RHO = 32  // the adapted rho between the plain form's launches
+  S_RHO = 32,  // the adapted rho between the plain form's launches
+  S_FEXT = 33  // S_FEXT..+2: the solve's end-effector force (base frame)
 };
+
+// The solve's constant end-effector force (Sec. IV-C's disturbance hypotheses).
+__device__ __forceinline__ V3 ee_force(const Ctx& C) {
+  return v3(C.scal[S_FEXT], C.scal[S_FEXT + 1], C.scal[S_FEXT + 2]);
+}
 
 // rho after an SQP iteration (Sec. IV-C adjusts it from the line search's
 // outcome): / 3 after an accepted step, * 2 after a rejected one, within
@@ -387,7 +393,7 @@ __device__ inline void st_mass_bias(const Ctx& C) {
       qd[i] = (col == 7) ? x[QM + i] : 0.f;
       acc[i] = (i == col) ? 1.f : 0.f;
     }
-    rnea_value(M, sq, cq, qd, acc, col == 7 ? M.g : 0.f, tau, nullptr);
+    rnea_value(M, sq, cq, qd, acc, col == 7 ? M.g : 0.f, col == 7 ? ee_force(C) : vzero(), tau, nullptr);
     if (col < 7) {
 #pragma unroll
       for (int r = 0; r < QM; ++r) C.Mi[k * FQS + r * QM + col] = tau[r];
@@ -535,7 +541,7 @@ __device__ inline void st_value_and_cost(const Ctx& C) {
       const float* x = C.X + k * VS;
 #pragma unroll
       for (int i = 0; i < QM; ++i) sincosf(x[i], &sq[i], &cq[i]);
-      rnea_value(*C.M, sq, cq, x + QM, C.qdd + k * US, C.M->g, tau, C.LV + k * QM);
+      rnea_value(*C.M, sq, cq, x + QM, C.qdd + k * US, C.M->g, ee_force(C), tau, C.LV + k * QM);
     } else {
       knot_cost(C, C.k0 + it - nd);
     }
@@ -569,10 +575,11 @@ __device__ inline void st_value_and_cost(const Ctx& C) {
 // Directional derivatives of ID along every q_j and qd_j.
 __device__ inline void st_tangents(const Ctx& C) {
   const int ke = C.k1 < C.N ? C.k1 : C.N;
+  const V3 fw = ee_force(C);
   for (int it = threadIdx.x; it < (ke - C.k0) * 14; it += NTHR) {
     const int k = C.k0 + it / 14, d = it % 14;
     float dtau[QM];
-    rnea_tangent(*C.M, C.LV + k * QM, C.X + k * VS + QM, d >= QM, d % QM, dtau);
+    rnea_tangent(*C.M, C.LV + k * QM, C.X + k * VS + QM, d >= QM, d % QM, fw, dtau);
 #pragma unroll
     for (int i = 0; i < QM; ++i) C.dT[k * DTS + d * 8 + i] = dtau[i];
   }
@@ -1541,7 +1548,7 @@ __device__ inline void st_line_search(const Ctx& C, float mu, float beta, int n_
 #pragma unroll
       for (int i = 0; i < QM; ++i) u[i] = uat(k * US + i);
       float qdd[QM];
-      forward_dynamics(*C.M, x, x + QM, u, qdd);
+      forward_dynamics(*C.M, x, x + QM, u, ee_force(C), qdd);
       float c1 = 0.f;
 #pragma unroll
       for (int i = 0; i < QM; ++i) {

@@ -116,7 +116,7 @@ struct Session {
   bool open = false;
   bool busy = false;  // a request is pending or on the GPU
   int model = 0, N = 0, cost_kind = 0, dof = 0;
-  float dt = 0.f, w[6] = {};
+  float dt = 0.f, w[6] = {}, fext[3] = {};
   float *x_s = nullptr, *ref = nullptr, *X = nullptr, *U = nullptr, *lam = nullptr;
 };
 
@@ -225,6 +225,7 @@ cudaError_t dispatch(gato_server* s, LaunchCtx* c) {
     d.dof = ss.dof;
     d.dt = ss.dt;
     for (int k = 0; k < 6; ++k) d.w[k] = ss.w[k];
+    for (int k = 0; k < 3; ++k) d.fext[k] = ss.fext[k];
     d.x_s = ss.x_s;
     d.x_ref = ss.cost_kind == GATO_COST_JOINT ? ss.ref : nullptr;
     d.ee_ref = ss.cost_kind == GATO_COST_EE ? ss.ref : nullptr;
@@ -514,6 +515,7 @@ gato_status gato_server_open(gato_server* s, const gato_problem* p, int32_t* ses
   ss.dof = batch_model_dof(s->models, p->model);
   ss.dt = p->dt;
   for (int k = 0; k < 6; ++k) ss.w[k] = p->w[k];
+  for (int k = 0; k < 3; ++k) ss.fext[k] = p->f_ext[k];
   const int nx = 2 * ss.dof, nu = ss.dof, N = ss.N;
   const size_t K = N + 1;
   // the slot image in pinned memory: x_s | ref | X | lambda | U (cold start

@@ -101,6 +101,8 @@ bool problem_ok(const gato_problem& p, int n_models) {
   if (!(p.dt > 0.f) || !std::isfinite(p.dt) || !p.x_s || !p.X || !p.U) return false;
   for (int i = 0; i < 6; ++i)
     if (!std::isfinite(p.w[i]) || p.w[i] < 0.f) return false;
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(p.f_ext[i])) return false;
   const float wq = p.w[0], wqd = p.w[1], wr = p.w[2], ts = p.w[3], rho = p.w[5];
   if (!(wr > 0.f) || !(ts > 0.f)) return false;
   if (p.cost_kind == GATO_COST_JOINT) return p.x_ref && wq + rho > 0.f && wqd + rho > 0.f;
@@ -146,6 +148,7 @@ extern "C" gato_status gato_solve_noalloc(const gato_model_desc* models, int32_t
     d.dof = dofs[p.model];
     d.dt = p.dt;
     for (int k = 0; k < 6; ++k) d.w[k] = p.w[k];
+    for (int k = 0; k < 3; ++k) d.fext[k] = p.f_ext[k];
     d.x_s = p.x_s;
     d.x_ref = p.cost_kind == GATO_COST_JOINT ? p.x_ref : nullptr;
     d.ee_ref = p.cost_kind == GATO_COST_EE ? p.ee_ref : nullptr;

@@ -59,7 +59,8 @@ class BatchDesc(C.Structure):
 
 class Problem(C.Structure):
     _fields_ = [("model", C.c_int32), ("N", C.c_int32), ("dt", C.c_float),
-                ("cost_kind", C.c_int32), ("w", C.c_float * 6), ("mem", C.c_int32),
+                ("cost_kind", C.c_int32), ("w", C.c_float * 6), ("f_ext", C.c_float * 3),
+                ("mem", C.c_int32),
                 ("x_s", C.c_void_p), ("x_ref", C.c_void_p), ("ee_ref", C.c_void_p),
                 ("X", C.c_void_p), ("U", C.c_void_p), ("lam", C.c_void_p)]
 
@@ -578,6 +579,8 @@ class HostProblems:
             a.cost_kind = p.cost_kind
             for k in range(6):
                 a.w[k] = p.w[k]
+            for k, f in enumerate(getattr(p, "f_ext", (0.0, 0.0, 0.0))):
+                a.f_ext[k] = f
             a.mem = MEM_HOST
             a.x_s = xs.ctypes.data
             a.x_ref = ref.ctypes.data if p.cost_kind == COST_JOINT else None
@@ -629,6 +632,8 @@ class DeviceProblems:
             a.cost_kind = p.cost_kind
             for k in range(6):
                 a.w[k] = p.w[k]
+            for k, f in enumerate(getattr(p, "f_ext", (0.0, 0.0, 0.0))):
+                a.f_ext[k] = f
             a.mem = MEM_DEVICE
             a.x_s = self.x_s.data_ptr() + i * 14 * es
             rp = self.ref.data_ptr() + i * (Nmax + 1) * 14 * es

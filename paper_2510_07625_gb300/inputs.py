@@ -278,3 +278,11 @@ def disturbed_ee_problem(seed: int, f_ext, model: ArmModel | None = None, N: int
     p = ee_problem(seed, model, N, dt)
     p.f_ext = tuple(float(v) for v in f_ext)
     return p
+
+
+def disturbed_joint_problem(seed: int, f_ext, model: ArmModel | None = None, N: int = 32,
+                            dt: float = 0.01) -> Problem:
+    """``joint_problem`` with a constant end-effector force."""
+    p = joint_problem(seed, model, N, dt)
+    p.f_ext = tuple(float(v) for v in f_ext)
+    return p

@@ -89,6 +89,8 @@ class _HostProblem:
         a.cost_kind = prob.cost_kind
         for k in range(6):
             a.w[k] = prob.w[k]
+        for k, f in enumerate(getattr(prob, "f_ext", (0.0, 0.0, 0.0))):
+            a.f_ext[k] = f
         a.mem = gato.MEM_HOST
         xs = np.ascontiguousarray(prob.x_s, np.float32)
         ref = np.ascontiguousarray(prob.x_ref if prob.cost_kind == gato.COST_JOINT else prob.ee_ref, np.float32)

@@ -81,3 +81,45 @@ def test_binding_fails_loudly_without_the_library(tmp_path, monkeypatch):
     monkeypatch.setattr(gato, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="missing"):
         gato.load()
+
+
+STRUCTS = {  # ctypes mirror in the binding -> C typedef in include/gato.h
+    "ModelDesc": "gato_model_desc", "SolverParams": "gato_solver_params",
+    "BatchDesc": "gato_batch_desc", "Problem": "gato_problem", "LaunchConfig": "gato_launch_config",
+    "LaunchInfo": "gato_launch_info", "Result": "gato_result", "ServerDesc": "gato_server_desc",
+    "Reply": "gato_reply", "DriveStats": "gato_drive_stats", "ServerStats": "gato_server_stats",
+}
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every ctypes struct of the binding has the size and field offsets that a
+    C compiler gives the header's typedef (gcc on this host)."""
+    import shutil
+    import subprocess
+
+    from paper_2510_07625_gb300 import gato
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "gato.h"', "int main(void) {"]
+    want = {}
+    for py, c in STRUCTS.items():
+        cls = getattr(gato, py)
+        lines.append(f'  printf("{py} size %zu\\n", sizeof({c}));')
+        want[f"{py} size"] = ctypes.sizeof(cls)
+        for name, _ in cls._fields_:
+            cname = "lambda" if (py == "Problem" and name == "lam") else name
+            lines.append(f'  printf("{py}.{name} %zu\\n", offsetof({c}, {cname}));')
+            want[f"{py}.{name}"] = getattr(cls, name).offset
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = {}
+    for line in out.splitlines():
+        key, val = line.rsplit(" ", 1)
+        got[key] = int(val)
+    assert got == want
