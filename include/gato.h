@@ -116,7 +116,7 @@ typedef struct {
   float w[6];              /* weights: q, qd, u, terminal scale, ee, rho (diag damping) */
   float f_ext[3];          /* constant external force on the end-effector point, base
                               frame (N): the dynamics become M qdd = u + J_p^T f_ext -
-                              ID(q, qd, 0); zeros = none.  Sec. IV-C's disturbance
+                              ID(q, qd, 0); zeros = none.  Sec. IV-D's disturbance
                               hypotheses are solves differing only in it */
   int32_t mem;             /* GATO_MEM_HOST or GATO_MEM_DEVICE for every pointer below */
   const float* x_s;
@@ -156,7 +156,7 @@ gato_status gato_create_batch(const gato_batch_desc* desc, void* cuda_stream, ga
 gato_status gato_solve(gato_batch* b, const gato_problem* problems, int32_t n,
                        int32_t max_sqp_iters, gato_result* results);
 
-/* One SQP iteration ("real-time iteration", Sec. IV-A) = gato_solve with 1. */
+/* One SQP iteration ("real-time iteration", Sec. IV-B) = gato_solve with 1. */
 gato_status gato_step(gato_batch* b, const gato_problem* problems, int32_t n,
                       gato_result* results);
 

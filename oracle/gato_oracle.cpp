@@ -63,7 +63,7 @@ typedef struct {
   const double* ee_ref;   /* [(N+1)*3] or NULL */
   double w[6];            /* wq, wqd, wr, terminal scale, wee, rho */
   double f_ext[3];        /* constant external force on the end effector, base
-                             frame (Sec. IV-C's disturbance hypotheses); zeros = none */
+                             frame (Sec. IV-D's disturbance hypotheses); zeros = none */
 } ora_problem;
 
 typedef struct {
@@ -508,7 +508,7 @@ double knot_cost(const ora_model& m, const ora_problem& p, int k, const double* 
       if (Qh) Qh[(n + i) * nx + (n + i)] = s * wqd;
     }
   }
-  if (Qh) for (int i = 0; i < nx; ++i) Qh[i * nx + i] += rho;  /* damping rho on diag(Q_k), Sec. IV-B */
+  if (Qh) for (int i = 0; i < nx; ++i) Qh[i * nx + i] += rho;  /* damping rho on diag(Q_k), Sec. IV-C */
   if (u) {
     for (int i = 0; i < n; ++i) {
       J += 0.5 * wr * u[i] * u[i];

@@ -105,7 +105,7 @@ enum : int {
   S_FEXT = 33  // S_FEXT..+2: the solve's end-effector force (base frame)
 };
 
-// The solve's constant end-effector force (Sec. IV-C's disturbance hypotheses).
+// The solve's constant end-effector force (Sec. IV-D's disturbance hypotheses).
 __device__ __forceinline__ V3 ee_force(const Ctx& C) {
   return v3(C.scal[S_FEXT], C.scal[S_FEXT + 1], C.scal[S_FEXT + 2]);
 }

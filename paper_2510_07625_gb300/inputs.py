@@ -4,8 +4,8 @@ This module only draws inputs: robot descriptions, start states, targets and
 reference tracks, arrival times.  It holds none of the solver's arithmetic, so
 both the FP64 oracle (through the tests) and the CUDA path are fed from here.
 
-Workloads stand in for the paper's robots (6-DoF Indy7 in Sec. IV-A, 7-DoF
-iiwa14 in Sec. IV-B/C), whose parameters are not published in the paper:
+Workloads stand in for the paper's robots (6-DoF Indy7 in Sec. IV-B, 7-DoF
+iiwa14 in Sec. IV-C/E), whose parameters are not published in the paper:
 
 * ``arm7``: 7 revolute joints, axes z,y,z,y,z,y,z, links 0.2 m, 2.0 kg.
 * ``arm6``: 6 revolute joints, axes z,y,z,y,z,y, links 0.25 m, 3.0 kg.
@@ -37,7 +37,7 @@ COST_EE = 1
 ROD_RADIUS = 0.05
 GRAVITY = 9.81
 
-# Figure-eight end-effector track (Sec. IV-A task; amplitude and period from
+# Figure-eight end-effector track (Sec. IV-B task; amplitude and period from
 # the benchmark configuration): p(t) = c + a * [0, sin wt, sin wt cos wt].
 FIG8_CENTER = (0.5, 0.0, 0.7)
 FIG8_AMPLITUDE = 0.15
@@ -47,7 +47,7 @@ FIG8_OMEGA = math.pi  # period 2 s
 # terminal scale, end-effector position, diagonal damping rho.
 W_JOINT = (1.0, 0.1, 1e-3, 10.0, 0.0, 0.0)
 # rho = 1 on the end-effector cost: with rho <= 1e-2 the Gauss-Newton Q_k (rank-3
-# JᵀJ plus rho) makes FP32 PCG break down (Sec. IV-B uses rho as exactly this
+# JᵀJ plus rho) makes FP32 PCG break down (Sec. IV-C uses rho as exactly this
 # numerical-stability damping).
 W_EE = (0.0, 0.1, 1e-3, 10.0, 100.0, 1.0)
 
@@ -137,7 +137,7 @@ class Problem:
     ee_ref: np.ndarray | None = None
     seed: int = 0
     meta: dict = field(default_factory=dict)
-    # constant external force on the end effector (base frame, N); Sec. IV-C's
+    # constant external force on the end effector (base frame, N); Sec. IV-D's
     # disturbance hypotheses differ only in it
     f_ext: tuple = (0.0, 0.0, 0.0)
 
@@ -258,7 +258,7 @@ def state_disturbance(rng: np.random.Generator, nq: int, sigma_q: float = 0.05,
 def force_hypotheses(seed: int, M: int, center=(0.0, 0.0, 0.0), radius: float = 10.0) -> np.ndarray:
     """M candidate end-effector forces (N, base frame) around an estimate.
 
-    Sec. IV-C samples directions uniformly on the sphere and adds them, scaled,
+    Sec. IV-D samples directions uniformly on the sphere and adds them, scaled,
     to the current disturbance estimate.  Row 0 is the estimate itself; rows
     1..M-1 are ``center + radius * d`` with ``d`` a normalised standard-normal
     draw (uniform on the sphere).  Draws: an (M-1, 3) normal block.

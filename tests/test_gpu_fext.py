@@ -1,5 +1,5 @@
 """A constant external end-effector force per solve (gato_problem.f_ext) on
-the GPU: Sec. IV-C solves a batch whose problems differ only in the assumed
+the GPU: Sec. IV-D solves a batch whose problems differ only in the assumed
 force and keeps the one whose model best matches the measured motion.
 
 * SQP steps with a force against the oracle's FP64 steps from the same

@@ -73,7 +73,7 @@ PROBS = [
     ("arm7_joint", lambda: I.joint_problem(0, I.arm7(), N=8, dt=0.01)),
     ("arm6_joint", lambda: I.joint_problem(3, I.arm6(), N=6, dt=0.02)),
     ("arm7_ee", lambda: I.ee_problem(2, I.arm7(), N=7, dt=0.01)),
-    # a constant end-effector force (Sec. IV-C): in the bias, the tangents and
+    # a constant end-effector force (Sec. IV-D): in the bias, the tangents and
     # the line search's dynamics
     ("arm6_ee_force", lambda: I.disturbed_ee_problem(5, (0.0, 0.0, -50.0), I.arm6(), N=7, dt=0.01)),
     ("arm7_joint_force", lambda: I.disturbed_joint_problem(1, (20.0, -10.0, -30.0), I.arm7(), N=8, dt=0.01)),

@@ -228,7 +228,7 @@ def test_fk_jacobian_and_points(oracle):
 
 
 # ------------------------------------------- external end-effector force
-# Sec. IV-C's hypotheses differ only in a constant force on the end effector;
+# Sec. IV-D's hypotheses differ only in a constant force on the end effector;
 # the dynamics become M(q) qdd = tau + J_p(q)^T f - ID(q, qd, 0).
 
 ARMS_AND_CHAINS = [I.arm7(), I.arm6()] + CHAINS

@@ -170,7 +170,7 @@ def test_rho_adaptation_rule(oracle):
 
 
 def test_external_force_enters_defects_and_solution(oracle):
-    """A solve with a constant end-effector force (Sec. IV-C's hypotheses):
+    """A solve with a constant end-effector force (Sec. IV-D's hypotheses):
     converged, its trajectory follows the forced dynamics (defects of the
     separately pinned one-step map with the force vanish) and not the free ones,
     and it differs from the unforced solve's."""
