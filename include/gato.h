@@ -399,6 +399,24 @@ int64_t gato_debug_layout(const gato_batch* b, int64_t* offsets);
 const char* gato_status_string(gato_status s);
 const char* gato_last_error(const gato_batch* b);
 
+/* ------------------------------------------------------------------ plant
+ * The simulated robot of closed-loop runs (Sec. IV-E simulates its plant with
+ * RK4 at 1 kHz while the solver runs at its own rate).  Host code in double;
+ * no GPU call and not part of the solve path. */
+
+/* Advances x = (q, qd) (2*dof doubles) by `steps` classic RK4 steps of size h
+ * under a control u (dof) held constant and the constant end-effector force
+ * f_ext (3, base frame; NULL = none):
+ *     qdd = M(q)^-1 (u + J_p(q)^T f_ext - ID(q, qd, 0)).
+ * x_out (2*dof) may alias x.  GATO_E_INVALID for a bad model or argument, a
+ * mass matrix that is not positive definite or a non-finite result (x_out
+ * then unchanged). */
+gato_status gato_plant_rk4(const gato_model_desc* model, const double* x, const double* u,
+                           const double* f_ext, double h, int32_t steps, double* x_out);
+
+/* End-effector position p (3, base frame) at configuration q (dof). */
+gato_status gato_plant_ee(const gato_model_desc* model, const double* q, double* p);
+
 #ifdef __cplusplus
 }
 #endif

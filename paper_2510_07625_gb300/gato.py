@@ -34,7 +34,7 @@ EXPORTED = (
     "gato_graph_launch", "gato_graph_wait", "gato_graph_destroy", "gato_server_create",
     "gato_server_open", "gato_server_submit", "gato_server_poll", "gato_server_read",
     "gato_server_close", "gato_server_get_stats", "gato_server_last_error", "gato_server_destroy",
-    "gato_server_drive", "gato_query_launch",
+    "gato_server_drive", "gato_query_launch", "gato_plant_rk4", "gato_plant_ee",
 )
 LAYOUT_NAMES = ("X", "U", "dX", "dU", "Fq", "Fv", "Minv", "qdd", "dTau", "Qinv", "Rinv", "q", "r",
                 "c", "Jk", "Linv", "links", "D", "L", "P", "vec", "scal", "Dx", "Du", "nu")
@@ -180,6 +180,11 @@ def load() -> C.CDLL:
     L.gato_server_drive.argtypes = [bp, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.c_void_p, C.c_int64, C.c_void_p, C.POINTER(DriveStats)]
     L.gato_server_drive.restype = C.c_int
+    dp = C.POINTER(C.c_double)
+    L.gato_plant_rk4.argtypes = [C.POINTER(ModelDesc), dp, dp, dp, C.c_double, C.c_int32, dp]
+    L.gato_plant_rk4.restype = C.c_int
+    L.gato_plant_ee.argtypes = [C.POINTER(ModelDesc), dp, dp]
+    L.gato_plant_ee.restype = C.c_int
     _lib = L
     return L
 
@@ -658,3 +663,38 @@ class DeviceProblems:
         U = self.U[i, : p.N * nu].reshape(p.N, nu).double().cpu().numpy()
         L = self.lam[i, : (p.N + 1) * nx].reshape(p.N + 1, nx).double().cpu().numpy()
         return X, U, L
+
+
+# ------------------------------------------------------------------ plant
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class Plant:
+    """The simulated robot of closed-loop runs (host, double): RK4 of the
+    rigid-body dynamics with an end-effector force (gato_plant_rk4)."""
+
+    def __init__(self, model):
+        self.model = model
+        self.desc = model_desc(model)
+        self.lib = load()
+
+    def rk4(self, x, u, h, steps, f_ext=None):
+        x = np.ascontiguousarray(x, np.float64)
+        u = np.ascontiguousarray(u, np.float64)
+        out = np.empty_like(x)
+        fe = None if f_ext is None else np.ascontiguousarray(f_ext, np.float64)
+        st = self.lib.gato_plant_rk4(C.byref(self.desc), _dptr(x), _dptr(u),
+                                     _dptr(fe) if fe is not None else None, h, steps, _dptr(out))
+        if st != 0:
+            raise GatoError(st, "gato_plant_rk4 failed")
+        return out
+
+    def ee(self, q):
+        q = np.ascontiguousarray(q, np.float64)
+        p = np.empty(3)
+        st = self.lib.gato_plant_ee(C.byref(self.desc), _dptr(q), _dptr(p))
+        if st != 0:
+            raise GatoError(st, "gato_plant_ee failed")
+        return p

@@ -15,7 +15,7 @@ def declared_functions():
     with open(os.path.join(ROOT, "include", "gato.h")) as f:
         text = f.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(gato_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(gato_[a-z0-9_]+)\s*\(", text)))
 
 
 @pytest.fixture(scope="module")
