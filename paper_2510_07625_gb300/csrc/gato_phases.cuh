@@ -1289,23 +1289,33 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
 // --------------------------------------- stage 3b: direct linear solve
 //
 // The direct alternative to PCG that Sec. II-B sets against iterative
-// methods, for the same system S dnu = rhs, by block elimination along the
-// horizon:
-//   D~_0 = D_0, y~_0 = rhs_0;  W_k = L_k D~_{k-1}^-1,
-//   D~_k = D_k - W_k L_k^T,    y~_k = rhs_k - W_k y~_{k-1};
-//   dnu_N = D~_N^-1 y~_N,      dnu_k = D~_k^-1 (y~_k - L_{k+1}^T dnu_{k+1}).
-// Sequential over knots and parallel inside a 14x14 block (one element per
-// thread, block barriers between the products).  The CTAs of a cluster take
-// the forward sweep in rank order and the backward sweep in reverse, each
-// handing its last D~^-1 and y~ (forward) or its first dnu (backward) to the
-// next CTA through distributed shared memory, with a cluster barrier per
-// hand-over.  D~_k^-1 (Gauss-Jordan without pivoting: D~_k is SPD, a Schur
-// complement of the SPD S; a pivot that is not positive flags the solve)
-// goes to the preconditioner's block slot, y~ to the y window; the
-// reduction slots serve as scratch.
+// methods, for the same system S dnu = rhs, by block elimination from both
+// ends of the horizon towards the knot m = floor((N+1)/2):
+//   from the top, k < m:     D~_0 = D_0,  D~_k = D_k - L_k D~_{k-1}^-1 L_k^T,
+//                            y~_k = rhs_k - L_k D~_{k-1}^-1 y~_{k-1};
+//   from the bottom, k >= m: D^_N = D_N,  D^_k = D_k - L_{k+1}^T D^_{k+1}^-1 L_{k+1},
+//                            y^_k = rhs_k - L_{k+1}^T D^_{k+1}^-1 y^_{k+1};
+//   at m both meet:          G_m = D^_m - L_m D~_{m-1}^-1 L_m^T,
+//                            g_m = y^_m - L_m D~_{m-1}^-1 y~_{m-1},  dnu_m = G_m^-1 g_m;
+//   then outwards:           dnu_k = D~_k^-1 (y~_k - L_{k+1}^T dnu_{k+1})  (k < m),
+//                            dnu_k = D^_k^-1 (y^_k - L_k dnu_{k-1})        (k > m).
+// (Eliminating the last equation into the one above gives the bottom
+// recursion; G_m is what is left of row m after both.)  The chain is about
+// N/2 knots long when the two halves sit on different CTAs of a cluster, and
+// m depends on N only, so every knot's arithmetic, and the result, is the
+// same for any split of the knots over CTAs.  Inside a knot the work is
+// parallel over the 14x14 block (one element per thread, block barriers
+// between the products); the inverses by Gauss-Jordan without pivoting (every
+// eliminated block is a Schur complement of the SPD S, so SPD; a pivot that
+// is not positive flags the solve).  Stage s of the sweeps runs rank s from
+// the top and rank C-1-s from the bottom; the back substitution starts at the
+// rank holding m and moves one rank outwards per stage.  Hand-overs go
+// through distributed shared memory with one cluster barrier per stage;
+// inverses go to the preconditioner's block slot, y~ / y^ to the y window,
+// and the reduction slots are the scratch.
 __device__ __forceinline__ void st_direct_body(const Ctx& C) {
   constexpr int BB = XM * XM;
-  static_assert(4 * BB + 2 * XM <= 2 * RED_SLOTS * RED_W, "scratch in the reduction slots");
+  static_assert(5 * BB + 4 * XM <= 2 * RED_SLOTS * RED_W, "scratch in the reduction slots");
   static_assert(BB + XM <= NTHR, "one block element per thread");
   const int t = threadIdx.x;
   const int i = t % XM, j = t / XM;  // element (i, j) of a column-major block, t < BB
@@ -1313,87 +1323,180 @@ __device__ __forceinline__ void st_direct_body(const Ctx& C) {
   float* const W = C.red;
   float* const G0 = W + BB;
   float* const G1 = G0 + BB;
-  float* const carry = G1 + BB;  // [BB] D~^-1, [XM] y~, [XM] dnu
+  float* const cF = G1 + BB;       // from the left neighbour: [BB] D~_{k0-1}^-1, [XM] y~_{k0-1}
+  float* const cB = cF + BB + XM;  // from the right neighbour: [BB] D^_{k1}^-1, [XM] y^_{k1}
+  float* const dL = cB + BB + XM;  // dnu_{k0-1} from the left neighbour
+  float* const dR = dL + XM;       // dnu_{k1} from the right neighbour
+  const int N = C.N, m = (N + 1) / 2;
+  const int rm = m / kpc_for(N, C.csize);  // the rank holding m
+  const bool own = C.k0 < C.k1;
   csync(C);  // every CTA has finished reading the reduction slots of earlier stages
-  // forward sweep
-  for (int s = 0; s < C.csize; ++s) {
-    if (C.rank == s) {
-      for (int k = C.k0; k < C.k1; ++k) {
-        const float* Dk = &bD(C, k, 0, 0);
-        const float* Lk = &bL(C, k, 0, 0);
-        const float* rk = vec(C, V_RHS, k);
-        float* yk = vec(C, V_Y, k);
-        if (k == 0) {
-          if (el) G0[t] = Dk[t];
-          else if (t < BB + XM) yk[t - BB] = rk[t - BB];
-        } else {
-          const float* Pp = (k == C.k0) ? carry : &bP(C, k - 1, 0, 0);
-          const float* yp = (k == C.k0) ? carry + BB : vec(C, V_Y, k - 1);
-          if (el) {
-            float a = 0.f;
-#pragma unroll
-            for (int l = 0; l < XM; ++l) a += Lk[l * XM + i] * Pp[j * XM + l];
-            W[t] = a;
-          }
-          __syncthreads();
-          if (el) {
-            float a = Dk[t];
-#pragma unroll
-            for (int l = 0; l < XM; ++l) a -= W[l * XM + i] * Lk[l * XM + j];
-            G0[t] = a;
-          } else if (t < BB + XM) {
-            const int r = t - BB;
-            float a = rk[r];
-#pragma unroll
-            for (int l = 0; l < XM; ++l) a -= W[l * XM + r] * yp[l];
-            yk[r] = a;
-          }
-        }
-        __syncthreads();
-        float* A = G0;
-        float* B = G1;
-        float* const Pk = &bP(C, k, 0, 0);
-        for (int p = 0; p < XM; ++p) {
-          if (el) {
-            const float piv = A[p * XM + p];
-            const float inv = 1.f / piv;
-            const float aip = A[p * XM + i], apj = A[j * XM + p], aij = A[t];
-            float out;
-            if (i == p)
-              out = (j == p) ? inv : apj * inv;
-            else
-              out = (j == p) ? -aip * inv : aij - aip * (apj * inv);
-            (p == XM - 1 ? Pk : B)[t] = out;
-            if (t == 0 && !(piv > 0.f && piv < INFINITY)) flag_nonfinite(C);
-          }
-          __syncthreads();
-          float* const tmp = A;
-          A = B;
-          B = tmp;
-        }
+
+  // G0 (SPD) inverted into Pk
+  auto invert_into = [&](float* Pk) {
+    float* A = G0;
+    float* B = G1;
+    for (int p = 0; p < XM; ++p) {
+      if (el) {
+        const float piv = A[p * XM + p];
+        const float inv = 1.f / piv;
+        const float aip = A[p * XM + i], apj = A[j * XM + p], aij = A[t];
+        float out;
+        if (i == p)
+          out = (j == p) ? inv : apj * inv;
+        else
+          out = (j == p) ? -aip * inv : aij - aip * (apj * inv);
+        (p == XM - 1 ? Pk : B)[t] = out;
+        if (t == 0 && !(piv > 0.f && piv < INFINITY)) flag_nonfinite(C);
       }
-      if (C.rank + 1 < C.csize) {  // D~^-1 and y~ of the last knot to the next CTA
-        float* dst = cg::this_cluster().map_shared_rank(carry, C.rank + 1);
+      __syncthreads();
+      float* const tmp = A;
+      A = B;
+      B = tmp;
+    }
+  };
+  // G0 = Ds - L_k Pp L_k^T, y_k = rs - L_k Pp yp (a step from the top; Ds / rs
+  // may be the knot's own D^ / y^ slots at the meeting knot)
+  auto from_top = [&](int k, const float* Ds, const float* rs, const float* Pp, const float* yp) {
+    const float* Lk = &bL(C, k, 0, 0);
+    float* yk = vec(C, V_Y, k);
+    if (el) {
+      float a = 0.f;
+#pragma unroll
+      for (int l = 0; l < XM; ++l) a += Lk[l * XM + i] * Pp[j * XM + l];
+      W[t] = a;
+    }
+    __syncthreads();
+    if (el) {
+      float a = Ds[t];
+#pragma unroll
+      for (int l = 0; l < XM; ++l) a -= W[l * XM + i] * Lk[l * XM + j];
+      G0[t] = a;
+    } else if (t < BB + XM) {
+      const int r = t - BB;
+      float a = rs[r];
+#pragma unroll
+      for (int l = 0; l < XM; ++l) a -= W[l * XM + r] * yp[l];
+      yk[r] = a;
+    }
+    __syncthreads();
+  };
+  // G0 = D_k - L_{k+1}^T Pn L_{k+1}, y_k = rhs_k - L_{k+1}^T Pn yn (a step from the bottom)
+  auto from_bottom = [&](int k, const float* Pn, const float* yn) {
+    const float* Ln = &bL(C, k + 1, 0, 0);  // (L_{k+1}^T)(i, l) = L_{k+1}(l, i)
+    const float* Dk = &bD(C, k, 0, 0);
+    const float* rk = vec(C, V_RHS, k);
+    float* yk = vec(C, V_Y, k);
+    if (el) {
+      float a = 0.f;
+#pragma unroll
+      for (int l = 0; l < XM; ++l) a += Ln[i * XM + l] * Pn[j * XM + l];
+      W[t] = a;
+    }
+    __syncthreads();
+    if (el) {
+      float a = Dk[t];
+#pragma unroll
+      for (int l = 0; l < XM; ++l) a -= W[l * XM + i] * Ln[j * XM + l];
+      G0[t] = a;
+    } else if (t < BB + XM) {
+      const int r = t - BB;
+      float a = rk[r];
+#pragma unroll
+      for (int l = 0; l < XM; ++l) a -= W[l * XM + r] * yn[l];
+      yk[r] = a;
+    }
+    __syncthreads();
+  };
+  // the block as it is: D_k, rhs_k (the first knot from either end)
+  auto as_is = [&](int k) {
+    if (el) G0[t] = bD(C, k, i, j);
+    else if (t < BB + XM) vec(C, V_Y, k)[t - BB] = vec(C, V_RHS, k)[t - BB];
+    __syncthreads();
+  };
+
+  // sweeps from both ends
+  for (int s = 0; s < C.csize; ++s) {
+    if (C.rank == s && own) {  // from the top: knots [k0, min(k1, m))
+      const int ke = min(C.k1, m);
+      for (int k = C.k0; k < ke; ++k) {
+        if (k == 0)
+          as_is(k);
+        else
+          from_top(k, &bD(C, k, 0, 0), vec(C, V_RHS, k), k == C.k0 ? cF : &bP(C, k - 1, 0, 0),
+                   k == C.k0 ? cF + BB : vec(C, V_Y, k - 1));
+        invert_into(&bP(C, k, 0, 0));
+      }
+      if (C.k1 <= m && C.rank + 1 < C.csize) {  // D~^-1 and y~ of the last knot to the next CTA
+        float* dst = cg::this_cluster().map_shared_rank(cF, C.rank + 1);
         if (el)
           dst[t] = bP(C, C.k1 - 1, i, j);
         else if (t < BB + XM)
           dst[t] = vec(C, V_Y, C.k1 - 1)[t - BB];
       }
     }
+    if (C.rank == C.csize - 1 - s && own && C.k1 > m) {  // from the bottom: knots [max(k0, m), k1)
+      const int kb = max(C.k0, m);
+      for (int k = C.k1 - 1; k >= kb; --k) {
+        if (k == N)
+          as_is(k);
+        else
+          from_bottom(k, k == C.k1 - 1 ? cB : &bP(C, k + 1, 0, 0), k == C.k1 - 1 ? cB + BB : vec(C, V_Y, k + 1));
+        if (k > m) {
+          invert_into(&bP(C, k, 0, 0));
+        } else {  // D^_m is kept as it is for the meeting step
+          if (el) bP(C, k, i, j) = G0[t];
+          __syncthreads();
+        }
+      }
+      if (C.k0 > m && C.rank > 0) {  // D^^-1 and y^ of the first knot to the previous CTA
+        float* dst = cg::this_cluster().map_shared_rank(cB, C.rank - 1);
+        if (el)
+          dst[t] = bP(C, C.k0, i, j);
+        else if (t < BB + XM)
+          dst[t] = vec(C, V_Y, C.k0)[t - BB];
+      }
+    }
     csync(C);
   }
-  // backward sweep
-  for (int s = C.csize - 1; s >= 0; --s) {
-    if (C.rank == s) {
-      for (int k = C.k1 - 1; k >= C.k0; --k) {
+  // the meeting knot: G_m^-1 and dnu_m; dnu_m goes at once to a neighbour
+  // whose first (last) knot is next to m
+  const int kpc = kpc_for(N, C.csize);
+  const int k0m = rm * kpc, k1m = min(k0m + kpc, N + 1);
+  if (own && C.rank == rm) {
+    const bool loc = m - 1 >= C.k0;
+    from_top(m, &bP(C, m, 0, 0), vec(C, V_Y, m), loc ? &bP(C, m - 1, 0, 0) : cF, loc ? vec(C, V_Y, m - 1) : cF + BB);
+    invert_into(&bP(C, m, 0, 0));
+    if (t < XM) W[t] = vec(C, V_Y, m)[t];
+    __syncthreads();
+    if (t < XM) {
+      const float* Pm = &bP(C, m, 0, 0);
+      float x = 0.f;
+#pragma unroll
+      for (int l = 0; l < XM; ++l) x += Pm[l * XM + t] * W[l];
+      vec(C, V_DNU, m)[t] = x;
+      if (m == C.k1 - 1 && C.rank + 1 < C.csize && C.k1 <= N)
+        cg::this_cluster().map_shared_rank(dL, C.rank + 1)[t] = x;
+      if (m == C.k0 && C.rank > 0) cg::this_cluster().map_shared_rank(dR, C.rank - 1)[t] = x;
+    }
+  }
+  csync(C);
+  // back substitution outwards: rank rm at stage 0, its neighbours one stage
+  // later (at once when dnu_m reached them above), and so on
+  const int sdown = rm - C.rank - (m == k0m ? 1 : 0);  // stage of a rank below rm
+  const int sup = C.rank - rm - (m == k1m - 1 ? 1 : 0);  // stage of a rank above rm
+  for (int s = 0; s < C.csize; ++s) {
+    const bool mid = own && C.rank == rm && s == 0;
+    const bool down = mid || (own && C.rank < rm && s == sdown);
+    const bool up = mid || (own && C.rank > rm && s == sup);
+    if (down) {  // k from m-1 (rank rm) or k1-1 down to k0
+      for (int k = (C.rank == rm ? m - 1 : C.k1 - 1); k >= C.k0; --k) {
         if (t < XM) {
           float b = vec(C, V_Y, k)[t];
-          if (k < C.N) {
-            const float* xn = (k == C.k1 - 1) ? carry + BB + XM : vec(C, V_DNU, k + 1);
-            const float* Ln = &bL(C, k + 1, 0, 0);  // (L_{k+1}^T)(t, l) = L_{k+1}(l, t)
+          const float* xn = (k == C.k1 - 1) ? dR : vec(C, V_DNU, k + 1);
+          const float* Ln = &bL(C, k + 1, 0, 0);  // (L_{k+1}^T)(t, l) = L_{k+1}(l, t)
 #pragma unroll
-            for (int l = 0; l < XM; ++l) b -= Ln[t * XM + l] * xn[l];
-          }
+          for (int l = 0; l < XM; ++l) b -= Ln[t * XM + l] * xn[l];
           W[t] = b;
         }
         __syncthreads();
@@ -1406,15 +1509,41 @@ __device__ __forceinline__ void st_direct_body(const Ctx& C) {
         }
         __syncthreads();
       }
-      if (t < XM) {
-        // the right neighbour's first dnu is this CTA's halo for the recovery
-        if (C.rank + 1 < C.csize && C.k1 <= C.N) vec(C, V_DNU, C.k1)[t] = carry[BB + XM + t];
-        if (C.rank > 0)  // this CTA's first dnu to the previous CTA
-          cg::this_cluster().map_shared_rank(carry, C.rank - 1)[BB + XM + t] = vec(C, V_DNU, C.k0)[t];
+      // the first dnu to the previous CTA (unless dnu_m went there already)
+      if (t < XM && C.rank > 0 && !(C.rank == rm && m == C.k0))
+        cg::this_cluster().map_shared_rank(dR, C.rank - 1)[t] = vec(C, V_DNU, C.k0)[t];
+    }
+    if (up) {  // k from m+1 (rank rm) or k0 up to k1-1
+      for (int k = (C.rank == rm ? m + 1 : C.k0); k < C.k1; ++k) {
+        if (t < XM) {
+          float b = vec(C, V_Y, k)[t];
+          const float* xp = (k == C.k0) ? dL : vec(C, V_DNU, k - 1);
+          const float* Lk = &bL(C, k, 0, 0);
+#pragma unroll
+          for (int l = 0; l < XM; ++l) b -= Lk[l * XM + t] * xp[l];
+          W[t] = b;
+        }
+        __syncthreads();
+        if (t < XM) {
+          const float* Pk = &bP(C, k, 0, 0);
+          float x = 0.f;
+#pragma unroll
+          for (int l = 0; l < XM; ++l) x += Pk[l * XM + t] * W[l];
+          vec(C, V_DNU, k)[t] = x;
+        }
+        __syncthreads();
       }
+      // the last dnu to the next CTA (unless dnu_m went there already)
+      if (t < XM && C.rank + 1 < C.csize && C.k1 <= N && !(C.rank == rm && m == C.k1 - 1))
+        cg::this_cluster().map_shared_rank(dL, C.rank + 1)[t] = vec(C, V_DNU, C.k1 - 1)[t];
     }
     csync(C);
   }
+  // the right neighbour's first dnu is this CTA's halo for the recovery
+  if (t < XM && C.rank > 0 && own)
+    cg::this_cluster().map_shared_rank(dR, C.rank - 1)[t] = vec(C, V_DNU, C.k0)[t];
+  csync(C);
+  if (t < XM && C.rank + 1 < C.csize && C.k1 <= N) vec(C, V_DNU, C.k1)[t] = dR[t];
 }
 
 // The direct solve as a call of its own (kept out of the kernel body so that

@@ -6,9 +6,11 @@ S dnu = rhs by block elimination along the horizon instead of PCG (GPU).
   the condition of S times FP32 rounding; the bar is the PCG stage test's
   5e-3 and the measured error is far below it;
 * the fused kernel equals the plain form bit for bit, and one SQP step is
-  the same bit for bit for every split of the knots over a cluster (the
-  elimination runs the same operations in the same order whatever the split;
-  the step's merit sums differ only in order, which picks the same alpha);
+  the same bit for bit for every split of the knots over a cluster (the two
+  ends meet at m = floor((N+1)/2) whatever the split, so every knot's
+  operations are the same; the step's merit sums differ only in order, which
+  picks the same alpha).  N = 63 puts m on a CTA's first knot for 8 and 4
+  CTAs, N = 64 on the first CTA's last knot for 2;
 * each SQP step against the oracle's step with its direct solver (the
   per-step bound of the PCG parity tests).
 """
@@ -65,7 +67,8 @@ def test_direct_fused_equals_plain_bitwise(G):
 @pytest.mark.parametrize("launch", [(1, 9, 0), (1, 0, 4), (2, 0, 0), (1, 17, 0)],
                          ids=["kpc9", "uniform4", "throughput", "kpc17"])
 def test_direct_step_independent_of_the_split(G, launch):
-    probs = [I.ee_problem(4, I.arm7(), 64), I.joint_problem(5, I.arm7(), 64, 0.01)]
+    probs = [I.ee_problem(4, I.arm7(), 64), I.joint_problem(5, I.arm7(), 64, 0.01),
+             I.joint_problem(6, I.arm7(), 63, 0.01)]
     a = gpu_solve(G, probs, 1, launch=(1, 0, 0), linsolve=DIRECT)
     b = gpu_solve(G, probs, 1, launch=launch, linsolve=DIRECT)
     for x, y in zip(a, b):

@@ -28,6 +28,8 @@ def _mix(n=12):
 
 def test_tick_equals_gato_solve(S):
     probs = _mix(4)
+    # sessions carry the end-effector force (Sec. IV-D) like gato_solve's problems
+    probs[1].f_ext = (10.0, -5.0, -40.0)
     srv = S.Server(MODELS, 8, 128, sqp_iters=3)
     for p in probs:
         sid = srv.open(p)
