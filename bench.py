@@ -221,6 +221,7 @@ def run_gpu(args):
         plain = plain_form(gato, I, torch)
         uneven = uneven_graph(gato, I, torch)
         serve = serving_runs(gato, I)
+        serve_direct = serving_runs(gato, I, rates=(1000.0, 5000.0, 20000.0), linsolve=1)
         e2e = e2e_run(gato, I, args)
         cpu = cpu_baseline()
         out = {
@@ -234,7 +235,7 @@ def run_gpu(args):
                        "parallelism": f"replicas x{ws}", "l2": "flushed between timed launches (512 MB write)",
                        "launch": launch},
             "latency_ms": lat, "direct_linear_solve": direct, "rho_sampling": rho, "disturbance_rejection": dist, "plain_gpu_form": plain,
-            "uneven_graph": uneven, "serving": serve,
+            "uneven_graph": uneven, "serving": serve, "serving_direct_linear_solve": serve_direct,
             "speedup_vs_plain_B32": round(lat["B32_iters10"]["solves_per_s"] / plain["solves_per_s_B32"], 2),
             "speedup_vs_plain_B256": round(value / ws / plain[f"solves_per_s_B{B_MAIN}"], 2),
             "pcg_iters_per_solve": round(pcg / dp.n, 1), "sqp_iters_per_solve": round(sqp / dp.n, 2),
@@ -434,13 +435,15 @@ def uneven_graph(gato, I, torch, reps=10):
 
 
 def serving_runs(gato, I, rates=(1000.0, 2000.0, 5000.0, 10000.0, 20000.0), duration_s=10.0,
-                 max_requests=50000):
+                 max_requests=50000, linsolve=0):
     """Serving loop: Poisson ticks over 128 resident sessions of the uneven mix,
-    each rate for 10 s or 50k requests, whichever comes first."""
+    each rate for 10 s or 50k requests, whichever comes first (linsolve 1: the
+    direct linear solve in place of PCG)."""
     from paper_2510_07625_gb300 import serving
 
     probs = I.config_uneven(128)
-    srv = serving.Server([I.arm7(), I.arm6()], 128, 128, max_batch=128, max_inflight=4, sqp_iters=3)
+    srv = serving.Server([I.arm7(), I.arm6()], 128, 128, max_batch=128, max_inflight=4, sqp_iters=3,
+                         linsolve=linsolve)
     sids = [srv.open(p) for p in probs]
     # warm every session up with one tick (cold start -> warm start)
     for s, p in zip(sids, probs):

@@ -26,16 +26,17 @@ def _mix(n=12):
     return I.config_uneven(B=n)
 
 
-def test_tick_equals_gato_solve(S):
+@pytest.mark.parametrize("linsolve", [0, 1], ids=["pcg", "direct"])
+def test_tick_equals_gato_solve(S, linsolve):
     probs = _mix(4)
     # sessions carry the end-effector force (Sec. IV-D) like gato_solve's problems
     probs[1].f_ext = (10.0, -5.0, -40.0)
-    srv = S.Server(MODELS, 8, 128, sqp_iters=3)
+    srv = S.Server(MODELS, 8, 128, sqp_iters=3, linsolve=linsolve)
     for p in probs:
         sid = srv.open(p)
         r = srv.tick(sid, p.x_s, shift=False)
         X, U, lam = srv.read(sid)
-        g = gpu_solve(S.gato, [p], 3)[0]
+        g = gpu_solve(S.gato, [p], 3, linsolve=linsolve)[0]
         np.testing.assert_array_equal(X, g["X"].astype(np.float32))
         np.testing.assert_array_equal(U, g["U"].astype(np.float32))
         np.testing.assert_array_equal(lam, g["lam"].astype(np.float32))
