@@ -11,7 +11,7 @@ from a CUDA graph, the serving loop under Poisson arrivals (1k, 2k, 5k, 10k
 and 20k ticks/s over 128 resident sessions of that mix, 3 SQP iterations per
 tick, each rate for 10 s or 50k requests, whichever comes first), and the same
 B=32 latencies and B=256 throughput with the optional direct linear solve
-(block elimination along the horizon in place of PCG).
+(block elimination from both ends of the horizon in place of PCG).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -291,7 +291,7 @@ def latency_runs(gato, I, torch, stream, flush, n_calls=200, launch_cfg=False, *
 
 
 def direct_solver_runs(gato, I, torch, stream, flush, steps=10):
-    """The direct linear solve (block elimination along the horizon instead of
+    """The direct linear solve (block elimination from both ends of the horizon instead of
     PCG; an option, not the paper's method): B = 32 p50/p99 latency at 10 and
     3 SQP iterations and the B = 256 throughput of the headline workload, each
     with its own autotuned launch configuration and the L2 flushed between

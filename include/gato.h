@@ -90,8 +90,10 @@ typedef struct {
   float kkt_tol;           /* > 0: a solve stops once its KKT residual <= kkt_tol */
   int32_t linsolve;        /* GATO_LINSOLVE_PCG (the method, default) or
                               GATO_LINSOLVE_DIRECT: S dnu = rhs by block elimination
-                              along the horizon (sequential over knots; precond,
-                              pcg_eps and pcg_max_iter unused; pcg_iters reads 0) */
+                              from both ends of the horizon towards knot (N+1)/2
+                              (sequential over knots; the same result for any split
+                              of a solve over CTAs; precond, pcg_eps and
+                              pcg_max_iter unused; pcg_iters reads 0) */
   int32_t rho_adapt;       /* 1: each solve's rho (w[5]) is adjusted after every SQP
                               iteration from its line search (Sec. IV-C): / 3 after an
                               accepted step, * 2 after a rejected one, within

@@ -1,5 +1,6 @@
 """The direct linear solve (gato_solver_params.linsolve = GATO_LINSOLVE_DIRECT):
-S dnu = rhs by block elimination along the horizon instead of PCG (GPU).
+S dnu = rhs by block elimination from both ends of the horizon instead of
+PCG (GPU).
 
 * on the GPU's own Schur system, read back and solved densely in FP64: the
   block elimination is backward stable for SPD S, so its error is bounded by
