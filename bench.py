@@ -562,11 +562,11 @@ def one_launch(B_n, N):
     B.close()
 
 
-def sweep(Bs=(1, 16, 32, 64, 128, 256), Ns=(32, 64, 128), iters=ITERS, reps=5):
+def sweep(Bs=(1, 16, 32, 64, 128, 256), Ns=(32, 64, 128), iters=ITERS, reps=5, linsolve=0):
     """The batch/horizon sweep (figure-eight EE, 10 SQP iterations): for every
     (B, N) the autotuner picks the launch configuration, then the median of
-    `reps` timed calls (CUDA events, cold start each) gives solves/s; the
-    plain form is timed at B = 1 for reference.  One JSON line per point."""
+    `reps` timed calls (CUDA events, cold start each) gives solves/s.  One JSON
+    line per point.  linsolve 1: the direct linear solve in place of PCG."""
     import torch
     from paper_2510_07625_gb300 import build, gato, inputs as I
 
@@ -575,7 +575,7 @@ def sweep(Bs=(1, 16, 32, 64, 128, 256), Ns=(32, 64, 128), iters=ITERS, reps=5):
     for N in Ns:
         for Bn in Bs:
             probs = I.config_sweep(Bn, N)
-            B = gato.Batch([I.arm7()], Bn, N, stream=stream.cuda_stream)
+            B = gato.Batch([I.arm7()], Bn, N, stream=stream.cuda_stream, linsolve=linsolve)
             dp = gato.DeviceProblems(B, probs)
             cfg, _ = B.autotune(dp.arr, dp.n, iters, reps=1)
             ts = []
@@ -593,7 +593,8 @@ def sweep(Bs=(1, 16, 32, 64, 128, 256), Ns=(32, 64, 128), iters=ITERS, reps=5):
             res = gato.gato_get_results(B.handle, dp.n)
             pcg = [res[i].pcg_iters for i in range(dp.n)]
             shape = gato.gato_query_launch(N, Bn, **cfg)
-            print(json.dumps({"sweep": {"B": Bn, "N": N, "ms": round(t, 4), "solves_per_s": round(Bn / (t / 1e3), 1),
+            print(json.dumps({"sweep": {"B": Bn, "N": N, "linsolve": "direct" if linsolve else "pcg",
+                                        "ms": round(t, 4), "solves_per_s": round(Bn / (t / 1e3), 1),
                                         "launch": cfg, "ctas_per_solve": shape["ctas_per_solve"],
                                         "resident_solves": shape["max_resident_solves"],
                                         "pcg_per_solve": round(sum(pcg) / Bn, 1), "pcg_max": max(pcg)}}),
@@ -610,9 +611,11 @@ def main():
     ap.add_argument("--one-launch", nargs=2, type=int, metavar=("B", "N"),
                     help="profiling case: 3 launches of B solves of horizon N, no measurement")
     ap.add_argument("--sweep", action="store_true", help="batch/horizon sweep with the autotuner (one line per point)")
+    ap.add_argument("--linsolve", default="pcg", choices=["pcg", "direct"],
+                    help="linear solver of --sweep (the method's PCG, or the direct block elimination)")
     args = ap.parse_args()
     if args.sweep:
-        sweep()
+        sweep(linsolve=1 if args.linsolve == "direct" else 0)
         return
     if args.one_launch:
         one_launch(*args.one_launch)
