@@ -35,6 +35,15 @@
  *              that case open: the iterate is kept).
  *   KKT resid  max(||c||_inf, ||g + C^T nu||_inf / max(1, ||g||_inf)) (the paper names no
  *              formula).
+ *
+ * Pinned by the tests against things other than itself: the dynamics (a
+ * symbolic Lagrangian, central differences, energy, power balance, a tip
+ * point mass for the end-effector force), the KKT system and Schur blocks
+ * (dense LU), the preconditioner identity, PCG and block elimination (dense
+ * solves), one SQP step of a linear-quadratic special case (Riccati) and the
+ * merit's closed form.  Parity unpinned: the full SQP loop with its line search
+ * on the nonlinear arm, which only invariants (accepted steps lower the merit,
+ * full steps near the solution), the special cases and the GPU's agreement check.
  */
 #include <cmath>
 #include <cstdint>
