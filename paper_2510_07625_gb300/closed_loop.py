@@ -42,11 +42,17 @@ class LoopResult:
     picks: list = field(default_factory=list)  # chosen hypothesis index per tick
 
 
-def select_hypothesis(plant, x_start, u_applied, steps, h, forces, x_measured):
+NONFINITE = 16  # the solve stopped on a non-finite value (gato_result.flags)
+
+
+def select_hypothesis(plant, x_start, u_applied, steps, h, forces, x_measured, usable=None):
     """Index of the force whose model best predicts the measured state after
-    ``steps`` plant steps from ``x_start`` under ``u_applied`` (ties: first)."""
-    best, best_err = 0, math.inf
+    ``steps`` plant steps from ``x_start`` under ``u_applied`` (ties: first),
+    among the indices in ``usable`` (default: all); None if none is usable."""
+    best, best_err = None, math.inf
     for j, f in enumerate(forces):
+        if usable is not None and j not in usable:
+            continue
         pred = plant.rk4(x_start, u_applied, h, steps, f_ext=f)
         err = float(np.linalg.norm(pred - x_measured))
         if err < best_err:
@@ -124,14 +130,16 @@ def run(solver, plant, M, f_true, *, model=None, N=32, dt=0.01, sim_s=1.0, plant
                 p = plant.ee(x[:nq])
                 errs.append(float(np.linalg.norm(p - I.figure_eight(np.array([t0 + t]))[0])))
                 qds.append(float(np.abs(x[nq:]).mean()))
-        j = select_hypothesis(plant, x_start, u_prev, steps, plant_h, forces, x)
+        usable = {i for i, sl in enumerate(sols) if not (sl["flags"] & NONFINITE)}
+        j = select_hypothesis(plant, x_start, u_prev, steps, plant_h, forces, x, usable)
         picks.append(j)
-        f_hat = np.asarray(forces[j], dtype=np.float64)
-        u_prev = np.array(sols[j]["U"][0], dtype=np.float64)
-        # every hypothesis warm-starts from the kept solution
-        X = [sols[j]["X"]] * M
-        U = [sols[j]["U"]] * M
-        lam = [sols[j]["lam"]] * M
+        if j is not None:  # else the previous control and warm start stay
+            f_hat = np.asarray(forces[j], dtype=np.float64)
+            u_prev = np.array(sols[j]["U"][0], dtype=np.float64)
+            # every hypothesis warm-starts from the kept solution
+            X = [sols[j]["X"]] * M
+            U = [sols[j]["U"]] * M
+            lam = [sols[j]["lam"]] * M
         tick += 1
     lat_ms = np.array(lat) * 1e3
     return LoopResult(M=M, ticks=tick, sim_s=t,

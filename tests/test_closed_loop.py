@@ -64,3 +64,13 @@ def test_estimate_moves_toward_an_unknown_force(plant, oracle):
     r = CL.run(oracle_solver(oracle), plant, 8, f, N=8, sim_s=0.04, latency_s=0.004, settle_s=0.0,
                radius=15.0, warm_iters=5)
     assert r.f_err < 0.8 * np.linalg.norm(f)
+
+
+def test_selection_skips_failed_solves(plant):
+    rng = np.random.default_rng(5)
+    x = np.concatenate([rng.uniform(-1, 1, 6), rng.uniform(-1, 1, 6)])
+    u = rng.uniform(-20, 20, 6)
+    F = I.force_hypotheses(12, 6, center=(0.0, 0.0, -30.0), radius=15.0)
+    meas = plant.rk4(x, u, 1e-3, 3, f_ext=F[2])
+    assert CL.select_hypothesis(plant, x, u, 3, 1e-3, F, meas, usable={0, 1, 3, 4, 5}) != 2
+    assert CL.select_hypothesis(plant, x, u, 3, 1e-3, F, meas, usable=set()) is None
