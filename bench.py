@@ -541,16 +541,17 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
-def one_launch(B_n, N):
+def one_launch(B_n, N, linsolve=0):
     """Profiling case: two warm-up solves and one solve of B_n figure-eight
     problems (horizon N, 10 SQP iterations) in the latency form with 33 knots
-    per CTA; profile the third launch (ncu -k regex:sqp_fused -s 2 -c 1)."""
+    per CTA; profile the third launch (ncu -k regex:sqp_fused -s 2 -c 1).
+    linsolve 1: the direct linear solve in place of PCG."""
     import torch
     from paper_2510_07625_gb300 import build, gato, inputs as I
 
     build.build_library()
     probs = I.config_sweep(B_n, N)
-    B = gato.Batch([I.arm7()], B_n, N)
+    B = gato.Batch([I.arm7()], B_n, N, linsolve=linsolve)
     B.set_launch_config(1, 0, 0)
     dp = gato.DeviceProblems(B, probs)
     for _ in range(3):
@@ -612,13 +613,13 @@ def main():
                     help="profiling case: 3 launches of B solves of horizon N, no measurement")
     ap.add_argument("--sweep", action="store_true", help="batch/horizon sweep with the autotuner (one line per point)")
     ap.add_argument("--linsolve", default="pcg", choices=["pcg", "direct"],
-                    help="linear solver of --sweep (the method's PCG, or the direct block elimination)")
+                    help="linear solver of --sweep and --one-launch (the method's PCG, or the direct block elimination)")
     args = ap.parse_args()
     if args.sweep:
         sweep(linsolve=1 if args.linsolve == "direct" else 0)
         return
     if args.one_launch:
-        one_launch(*args.one_launch)
+        one_launch(*args.one_launch, linsolve=1 if args.linsolve == "direct" else 0)
         return
     if args.warmup < 3:
         args.warmup = 3

@@ -73,3 +73,12 @@ def test_force_hypothesis_batch(G, oracle):
             sens, dmax = qp_sensitivity(oracle, probs[j], X, U, lam)
             tol = 1e-4 * max(1.0, np.abs(o["X"]).max()) + 30.0 * 0.5 ** o["alpha_idx"][0] * sens * dmax
             assert np.abs(g["X"] - o["X"]).max() <= tol, j
+
+
+def test_forced_direct_fused_equals_plain_bitwise(G):
+    p = FORCED[0][1]()
+    a = gpu_solve(G, [p], 3, linsolve=1)[0]
+    b = gpu_solve(G, [p], 3, plain=True, linsolve=1)[0]
+    assert a["flags"] == b["flags"]
+    for k in ("X", "U", "lam"):
+        np.testing.assert_array_equal(a[k], b[k])

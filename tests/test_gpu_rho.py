@@ -83,3 +83,15 @@ def test_log_spaced_rho_batch(G):
         assert np.isfinite(g["X"]).all() and not (g["flags"] & 16), (r, g["flags"])
     # different rho, different paths
     assert len({round(float(g["merit"]), 6) for g in res}) > 1
+
+
+def test_rho_adapt_with_the_direct_solve(G):
+    # the adapted rho reaches the Schur blocks the direct solve eliminates:
+    # fused and plain agree bit for bit, and the rule replays like with PCG
+    p = with_rho(I.joint_problem(2, I.arm7(), 40, 0.01), 1e-1)
+    a = gpu_solve(G, [p], 5, rho_adapt=1, linsolve=1)[0]
+    b = gpu_solve(G, [p], 5, plain=True, rho_adapt=1, linsolve=1)[0]
+    assert a["flags"] == b["flags"]
+    np.testing.assert_array_equal(a["X"], b["X"])
+    fixed = gpu_solve(G, [p], 5, rho_adapt=0, linsolve=1)[0]
+    assert np.abs(a["X"] - fixed["X"]).max() > 0  # the adaptation changed the path
