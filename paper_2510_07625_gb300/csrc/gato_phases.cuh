@@ -1305,9 +1305,9 @@ __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bo
 // m depends on N only, so every knot's arithmetic, and the result, is the
 // same for any split of the knots over CTAs.  Inside a knot the work is
 // parallel over the 14x14 block (one element per thread, block barriers
-// between the products); the inverses by Gauss-Jordan without pivoting (every
-// eliminated block is a Schur complement of the SPD S, so SPD; a pivot that
-// is not positive flags the solve).  Stage s of the sweeps runs rank s from
+// between the products); the inverses by Gauss-Jordan on 2x2 pivot blocks
+// without pivoting (every eliminated block is a Schur complement of the SPD
+// S, so SPD; a pivot block that is not positive definite flags the solve).  Stage s of the sweeps runs rank s from
 // the top and rank C-1-s from the bottom; the back substitution starts at the
 // rank holding m and moves one rank outwards per stage.  Hand-overs go
 // through distributed shared memory with one cluster barrier per stage;
@@ -1332,22 +1332,39 @@ __device__ __forceinline__ void st_direct_body(const Ctx& C) {
   const bool own = C.k0 < C.k1;
   csync(C);  // every CTA has finished reading the reduction slots of earlier stages
 
-  // G0 (SPD) inverted into Pk
+  // G0 (SPD) inverted into Pk by Gauss-Jordan on 2x2 pivot blocks: with
+  // P = {p, p+1} and Pi = A[P,P]^-1, the pivot block becomes Pi, pivot rows
+  // Pi A[P,j], pivot columns -A[i,P] Pi, the rest A - A[:,P] Pi A[P,:] (seven
+  // block barriers for 14 pivots; every leading block of an SPD matrix is SPD)
+  static_assert(XM % 2 == 0, "pivot pairs");
   auto invert_into = [&](float* Pk) {
     float* A = G0;
     float* B = G1;
-    for (int p = 0; p < XM; ++p) {
+    for (int p = 0; p < XM; p += 2) {
+      const int q = p + 1;
       if (el) {
-        const float piv = A[p * XM + p];
-        const float inv = 1.f / piv;
-        const float aip = A[p * XM + i], apj = A[j * XM + p], aij = A[t];
+        // element (r, c) at c * XM + r
+        const float a = A[p * XM + p], b = A[q * XM + p], c = A[p * XM + q], d = A[q * XM + q];
+        const float det = a * d - b * c;
+        const float id = 1.f / det;
+        const float P00 = d * id, P01 = -b * id, P10 = -c * id, P11 = a * id;
+        const bool ip = (i == p || i == q), jp = (j == p || j == q);
         float out;
-        if (i == p)
-          out = (j == p) ? inv : apj * inv;
-        else
-          out = (j == p) ? -aip * inv : aij - aip * (apj * inv);
-        (p == XM - 1 ? Pk : B)[t] = out;
-        if (t == 0 && !(piv > 0.f && piv < INFINITY)) flag_nonfinite(C);
+        if (ip && jp) {
+          out = (i == p) ? (j == p ? P00 : P01) : (j == p ? P10 : P11);
+        } else if (ip) {
+          const float apj = A[j * XM + p], aqj = A[j * XM + q];
+          out = (i == p) ? P00 * apj + P01 * aqj : P10 * apj + P11 * aqj;
+        } else if (jp) {
+          const float aip = A[p * XM + i], aiq = A[q * XM + i];
+          out = (j == p) ? -(aip * P00 + aiq * P10) : -(aip * P01 + aiq * P11);
+        } else {
+          const float aip = A[p * XM + i], aiq = A[q * XM + i], apj = A[j * XM + p], aqj = A[j * XM + q];
+          const float v0 = P00 * apj + P01 * aqj, v1 = P10 * apj + P11 * aqj;
+          out = A[t] - (aip * v0 + aiq * v1);
+        }
+        (p == XM - 2 ? Pk : B)[t] = out;
+        if (t == 0 && !(a > 0.f && det > 0.f && det < INFINITY)) flag_nonfinite(C);
       }
       __syncthreads();
       float* const tmp = A;
