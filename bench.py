@@ -255,9 +255,9 @@ def run_gpu(args):
 
 # DRAM bytes per launch of the dominant kernel on this workload (latency form,
 # 33 knots per CTA), from the ncu capture summarised in
-# profiles/sqp_fused_b256_n64_metrics.md: 18,353,664 read + 6,708,736 written.
+# profiles/sqp_fused_b256_n64_metrics.md: 18,174,976 read + 6,727,424 written.
 # Set to None when the kernel changes until it is measured again.
-TRAFFIC_BYTES = 25062400
+TRAFFIC_BYTES = 24902400
 
 
 def latency_runs(gato, I, torch, stream, flush, n_calls=200, launch_cfg=False, **prm):
