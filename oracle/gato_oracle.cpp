@@ -40,10 +40,13 @@
  * symbolic Lagrangian, central differences, energy, power balance, a tip
  * point mass for the end-effector force), the KKT system and Schur blocks
  * (dense LU), the preconditioner identity, PCG and block elimination (dense
- * solves), one SQP step of a linear-quadratic special case (Riccati) and the
- * merit's closed form.  Parity unpinned: the full SQP loop with its line search
- * on the nonlinear arm, which only invariants (accepted steps lower the merit,
- * full steps near the solution), the special cases and the GPU's agreement check.
+ * solves), one SQP step of a linear-quadratic special case (Riccati), the
+ * merit's closed form, and single SQP iterations on the nonlinear arms (joint
+ * and end-effector costs, full and shortened steps) rebuilt from those pinned
+ * parts: dense KKT solve, merit and KKT residual restated from their
+ * definitions, the first argmin over the step lengths.  The loop repeats that
+ * iteration; across iterations only invariants check it (accepted steps lower
+ * the merit, full steps near the solution, zero defects at convergence).
  */
 #include <cmath>
 #include <cstdint>

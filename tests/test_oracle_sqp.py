@@ -189,3 +189,97 @@ def test_external_force_enters_defects_and_solution(oracle):
     assert d_forced < 1e-8
     assert d_free > 1e-3
     assert np.abs(rf["U"] - r0["U"]).max() > 1.0  # the controls push back against the force
+
+
+@pytest.mark.parametrize("kind,model,seed,dt,warm,i_want", [
+    ("joint", I.arm7(), 2, 0.05, 0, 3), ("joint", I.arm6(), 4, 0.05, 2, 2), ("joint", I.arm7(), 9, 0.02, 2, 0),
+    ("ee", I.arm7(), 2, 0.05, 1, 2), ("ee", I.arm6(), 1, 0.05, 0, 3)],
+    ids=["joint_arm7_cold_alpha1/8", "joint_arm6_alpha1/4", "joint_arm7_full_step", "ee_arm7_alpha1/4",
+         "ee_arm6_cold_alpha1/8"])
+def test_one_nonlinear_sqp_iteration_from_pinned_parts(oracle, kind, model, seed, dt, warm, i_want):
+    """One SQP iteration on the nonlinear arm rebuilt from separately pinned
+    parts: the QP (Eq. 1) from the step Jacobians (pinned by central
+    differences), the cost's gradient and (Gauss-Newton) Hessian written out
+    from its definition (the end-effector terms through the FK Jacobian,
+    pinned by a closed form and central differences; rho on the whole
+    diagonal) and the one-step map's defects, solved densely in Eq. 1's
+    convention; the merit (Eq. 3) by its definition at every alpha_i = 2^-i
+    (Eq. 7); alpha* the first argmin.  The oracle's iteration must pick the
+    same alpha and land on Z + alpha* dZ."""
+    from tests.test_oracle_kkt import dense_kkt
+
+    mk = I.joint_problem if kind == "joint" else I.ee_problem
+    prob = mk(seed, model, N=5, dt=dt)
+    n, N = model.dof, prob.N
+    nx = 2 * n
+    wq, wqd, wr, ts, wee, rho = prob.w
+    W = np.diag([wq] * n + [wqd] * n)
+    # the cold start or the iterate after `warm` oracle iterations
+    if warm:
+        rw = oracle.solve(prob, max_iter=warm, pcg_eps=1e-12, pcg_max=1000)
+        X, U, lam = rw["X"].reshape(N + 1, nx), rw["U"].reshape(N, n), rw["lam"]
+    else:
+        X, U, lam = oracle.cold_start(prob)
+        X, U = X.reshape(N + 1, nx), U.reshape(N, n)
+
+    scale = [1.0] * N + [ts]
+
+    def J(X, U):
+        out = 0.5 * wr * np.sum(U ** 2)
+        for k in range(N + 1):
+            if kind == "joint":
+                d = X[k] - prob.x_ref[k]
+                out += 0.5 * scale[k] * d @ W @ d
+            else:
+                d = oracle.fk(model, X[k][:n]) - prob.ee_ref[k]
+                out += 0.5 * scale[k] * (wee * d @ d + wqd * X[k][n:] @ X[k][n:])
+        return out
+
+    def expansion(k):
+        """q_k and Q_k of the cost at X[k] (Gauss-Newton for the end effector)."""
+        if kind == "joint":
+            return scale[k] * W @ (X[k] - prob.x_ref[k]), scale[k] * W + rho * np.eye(nx)
+        p, Jp = oracle.fk(model, X[k][:n], jacobian=True)
+        q = np.concatenate([scale[k] * wee * Jp.T @ (p - prob.ee_ref[k]), scale[k] * wqd * X[k][n:]])
+        Q = np.zeros((nx, nx))
+        Q[:n, :n] = scale[k] * wee * Jp.T @ Jp
+        Q[n:, n:] = scale[k] * wqd * np.eye(n)
+        return q, Q + rho * np.eye(nx)
+
+    def defects(X, U):
+        c = [prob.x_s - X[0]] + [oracle.step(model, X[k], U[k], prob.dt) - X[k + 1] for k in range(N)]
+        return np.array(c)
+
+    def merit(X, U):
+        return J(X, U) + 10.0 * np.abs(defects(X, U)).sum()
+
+    AB = [oracle.step_jacobians(model, X[k], U[k], prob.dt) for k in range(N)]
+    qQ = [expansion(k) for k in range(N + 1)]
+    lin = dict(A=np.array([a for a, _ in AB]), B=np.array([b for _, b in AB]),
+               Q=np.array([Q for _, Q in qQ]), R=np.array([wr * np.eye(n)] * N),
+               q=np.array([q for q, _ in qQ]), r=wr * U, c=defects(X, U))
+    G, g, C, c, xi, ui = dense_kkt(lin)
+    nz, nc = G.shape[0], C.shape[0]
+    K = np.block([[G, C.T], [C, np.zeros((nc, nc))]])
+    dz = np.linalg.solve(K, np.concatenate([-g, c]))[:nz]
+    dX = np.array([dz[xi(k):xi(k) + nx] for k in range(N + 1)])
+    dU = np.array([dz[ui(k):ui(k) + n] for k in range(N)])
+    m0 = merit(X, U)
+    ms = [merit(X + 0.5 ** i * dX, U + 0.5 ** i * dU) for i in range(8)]
+    i_star = int(np.argmin(ms))
+    assert i_star == i_want  # the case exercises the step length it is meant to
+    assert ms[i_star] < m0
+    gap = sorted(ms)[1] - ms[i_star]
+    assert gap > 1e-9 * m0  # not a near tie: the choice is unambiguous
+    o = oracle.solve(prob, max_iter=1, X=X, U=U, lam=lam, pcg_eps=1e-12, pcg_max=1000)
+    assert o["alpha_idx"][0] == i_star
+    a = 0.5 ** i_star
+    np.testing.assert_allclose(o["X"].reshape(N + 1, nx), X + a * dX, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(o["U"].reshape(N, n), U + a * dU, rtol=0, atol=1e-8)
+    assert abs(o["merit_before"][0] - m0) <= 1e-10 * m0
+    assert abs(o["merit_after"][0] - ms[i_star]) <= 1e-10 * m0
+    # the KKT residual at this iterate with its multiplier, from the same pieces:
+    # max(|c|_inf, |g + C^T nu|_inf / max(1, |g|_inf))
+    nu = np.asarray(lam, dtype=np.float64).ravel()
+    kkt = max(np.abs(c).max(), np.abs(g + C.T @ nu).max() / max(1.0, np.abs(g).max()))
+    assert abs(oracle.kkt_residual(prob, X, U, lam) - kkt) <= 1e-12 * max(1.0, kkt)
