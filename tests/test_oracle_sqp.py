@@ -193,9 +193,9 @@ def test_external_force_enters_defects_and_solution(oracle):
 
 @pytest.mark.parametrize("kind,model,seed,dt,warm,i_want", [
     ("joint", I.arm7(), 2, 0.05, 0, 3), ("joint", I.arm6(), 4, 0.05, 2, 2), ("joint", I.arm7(), 9, 0.02, 2, 0),
-    ("ee", I.arm7(), 2, 0.05, 1, 2), ("ee", I.arm6(), 1, 0.05, 0, 3)],
+    ("ee", I.arm7(), 2, 0.05, 1, 2), ("ee", I.arm6(), 1, 0.05, 0, 3), ("ee_force", I.arm6(), 1, 0.05, 1, 4)],
     ids=["joint_arm7_cold_alpha1/8", "joint_arm6_alpha1/4", "joint_arm7_full_step", "ee_arm7_alpha1/4",
-         "ee_arm6_cold_alpha1/8"])
+         "ee_arm6_cold_alpha1/8", "ee_force_arm6_alpha1/16"])
 def test_one_nonlinear_sqp_iteration_from_pinned_parts(oracle, kind, model, seed, dt, warm, i_want):
     """One SQP iteration on the nonlinear arm rebuilt from separately pinned
     parts: the QP (Eq. 1) from the step Jacobians (pinned by central
@@ -208,8 +208,11 @@ def test_one_nonlinear_sqp_iteration_from_pinned_parts(oracle, kind, model, seed
     same alpha and land on Z + alpha* dZ."""
     from tests.test_oracle_kkt import dense_kkt
 
-    mk = I.joint_problem if kind == "joint" else I.ee_problem
-    prob = mk(seed, model, N=5, dt=dt)
+    if kind == "ee_force":  # a constant end-effector force in the dynamics (Sec. IV-D)
+        prob = I.disturbed_ee_problem(seed, (0.0, 0.0, -50.0), model, N=5, dt=dt)
+    else:
+        prob = (I.joint_problem if kind == "joint" else I.ee_problem)(seed, model, N=5, dt=dt)
+    fe = np.array(prob.f_ext)
     n, N = model.dof, prob.N
     nx = 2 * n
     wq, wqd, wr, ts, wee, rho = prob.w
@@ -247,13 +250,13 @@ def test_one_nonlinear_sqp_iteration_from_pinned_parts(oracle, kind, model, seed
         return q, Q + rho * np.eye(nx)
 
     def defects(X, U):
-        c = [prob.x_s - X[0]] + [oracle.step(model, X[k], U[k], prob.dt) - X[k + 1] for k in range(N)]
+        c = [prob.x_s - X[0]] + [oracle.step(model, X[k], U[k], prob.dt, f_ext=fe) - X[k + 1] for k in range(N)]
         return np.array(c)
 
     def merit(X, U):
         return J(X, U) + 10.0 * np.abs(defects(X, U)).sum()
 
-    AB = [oracle.step_jacobians(model, X[k], U[k], prob.dt) for k in range(N)]
+    AB = [oracle.step_jacobians(model, X[k], U[k], prob.dt, f_ext=fe) for k in range(N)]
     qQ = [expansion(k) for k in range(N + 1)]
     lin = dict(A=np.array([a for a, _ in AB]), B=np.array([b for _, b in AB]),
                Q=np.array([Q for _, Q in qQ]), R=np.array([wr * np.eye(n)] * N),
