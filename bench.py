@@ -218,6 +218,7 @@ def run_gpu(args):
         direct = direct_solver_runs(gato, I, torch, stream, flush)
         rho = rho_sampling(gato, I, torch, stream)
         dist = disturbance_rejection(gato, stream)
+        dist_direct = disturbance_rejection(gato, stream, linsolve=1)
         plain = plain_form(gato, I, torch)
         uneven = uneven_graph(gato, I, torch)
         serve = serving_runs(gato, I)
@@ -234,7 +235,7 @@ def run_gpu(args):
                        "B": B_MAIN, "N": N_MAIN, "sqp_iters": ITERS, "dof": 7,
                        "parallelism": f"replicas x{ws}", "l2": "flushed between timed launches (512 MB write)",
                        "launch": launch},
-            "latency_ms": lat, "direct_linear_solve": direct, "rho_sampling": rho, "disturbance_rejection": dist, "plain_gpu_form": plain,
+            "latency_ms": lat, "direct_linear_solve": direct, "rho_sampling": rho, "disturbance_rejection": dist, "disturbance_rejection_direct_linear_solve": dist_direct, "plain_gpu_form": plain,
             "uneven_graph": uneven, "serving": serve, "serving_direct_linear_solve": serve_direct,
             "speedup_vs_plain_B32": round(lat["B32_iters10"]["solves_per_s"] / plain["solves_per_s_B32"], 2),
             "speedup_vs_plain_B256": round(value / ws / plain[f"solves_per_s_B{B_MAIN}"], 2),
@@ -358,21 +359,23 @@ def rho_sampling(gato, I, torch, stream, M=32, iters=(1, 5, 20, 100)):
     return out
 
 
-def disturbance_rejection(gato, stream, Ms=(1, 8, 32, 128), f_true=(0.0, 0.0, -50.0), sim_s=1.0):
+def disturbance_rejection(gato, stream, Ms=(1, 8, 32, 128), f_true=(0.0, 0.0, -50.0), sim_s=1.0, linsolve=0):
     """Closed-loop hypothesize-and-test (Sec. IV-D): the 6-DoF arm tracks the
     figure-eight (N = 32, h = 0.01, 3 SQP iterations per tick) under an
     unmodelled constant end-effector force; each tick solves M force
     hypotheses in one call while the RK4 plant (1 kHz) runs on for the
     measured solve time.  Per M: ticks, solve latency, mean tracking error
-    and joint speed after 0.25 s, and the final force-estimate error."""
+    and joint speed after 0.25 s, and the final force-estimate error
+    (linsolve 1: the batch solves use the direct linear solve)."""
     from paper_2510_07625_gb300 import closed_loop as CL
     from paper_2510_07625_gb300 import inputs as I
 
     model = I.arm6()
     plant = gato.Plant(model)
-    out = {"f_true": list(f_true), "sim_s": sim_s, "N": 32, "sqp_iters": 3, "runs": []}
+    out = {"f_true": list(f_true), "sim_s": sim_s, "N": 32, "sqp_iters": 3,
+           "linsolve": "direct" if linsolve else "pcg", "runs": []}
     for M in Ms:
-        solver = CL.GpuBatchSolver(model, M, 32, 3, stream=stream.cuda_stream)
+        solver = CL.GpuBatchSolver(model, M, 32, 3, stream=stream.cuda_stream, linsolve=linsolve)
         r = CL.run(solver, plant, M, f_true, N=32, sim_s=sim_s, radius=10.0, seed=0)
         solver.close()
         out["runs"].append({"M": M, "ticks": r.ticks, "solve_ms_mean": round(r.solve_ms_mean, 3),

@@ -61,13 +61,14 @@ def select_hypothesis(plant, x_start, u_applied, steps, h, forces, x_measured, u
 
 
 class GpuBatchSolver:
-    """Solves the tick's batch through the library (one gato_solve call)."""
+    """Solves the tick's batch through the library (one gato_solve call;
+    linsolve 1: the direct linear solve in place of PCG)."""
 
-    def __init__(self, model, M, N, sqp_iters, stream=None):
+    def __init__(self, model, M, N, sqp_iters, stream=None, linsolve=0):
         from . import gato
 
         self.gato = gato
-        self.B = gato.Batch([model], M, N, stream=stream)
+        self.B = gato.Batch([model], M, N, stream=stream, linsolve=linsolve)
         self.iters = sqp_iters
 
     def __call__(self, probs, X, U, lam, iters=None):
