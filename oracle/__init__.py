@@ -319,7 +319,7 @@ def kkt_residual(prob, X, U, nu):
                                   _d(_arr(nu)))
 
 
-DEFAULTS = dict(mu=10.0, beta=2.0, n_alpha=8, pcg_eps=1e-6, pcg_max=200, precond=0,
+DEFAULTS = dict(mu=10.0, beta=2.0, n_alpha=8, pcg_eps=1e-6, pcg_max=1000, precond=0,
                 kkt_tol=0.0, max_iter=10, linsolve=0, rho_adapt=0)
 
 
