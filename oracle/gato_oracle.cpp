@@ -880,8 +880,9 @@ double ora_kkt_residual(const ora_model* m, const ora_problem* p, const double* 
    X, U, nu: in = initial guess / warm start, out = final iterate.
    replay: NULL, or [max_iter] line-search indices to force (-1 = reject).
    Per-iteration logs (each [max_iter] or NULL): chosen alpha index (-1 reject),
-   PCG iterations, merit before the step, merit after, KKT residual, the gap
-   between the two best trial merits relative to the best. */
+   PCG iterations, merit before the step, merit after, KKT residual, and the
+   margin of the line-search decision relative to the best trial merit (the
+   smaller of its gaps to the runner-up trial and to the current merit). */
 int32_t ora_blocktri_solve(int32_t N, int32_t nx, const double* Sd, const double* Ss,
                            const double* rhs, double* x);
 
@@ -941,8 +942,15 @@ int32_t ora_solve(const ora_model* m, const ora_problem* p, const ora_params* pr
     for (int i = 0; i < prm->n_alpha; ++i) if (i != best) second = std::min(second, mer[i]);
     int choice = (bestm < m0) ? best : -1;
     if (replay) choice = replay[it];
-    if (log_gap && it < prm->max_iter)
-      log_gap[it] = std::isfinite(second) ? (second - bestm) / std::max(1e-300, std::fabs(bestm)) : INFINITY;
+    if (log_gap && it < prm->max_iter) {
+      /* the margin of the decision of Eq. 7, relative to the best merit: the
+         gap to the runner-up trial merit and the gap to the current merit
+         (accept versus reject), whichever is smaller */
+      const double sc = std::max(1e-300, std::fabs(bestm));
+      double g = std::isfinite(second) ? (second - bestm) / sc : INFINITY;
+      if (std::isfinite(bestm)) g = std::min(g, std::fabs(m0 - bestm) / sc);
+      log_gap[it] = g;
+    }
     if (log_m0 && it < prm->max_iter) log_m0[it] = m0;
     if (choice >= 0) {
       double a = std::pow(prm->beta, -choice);
