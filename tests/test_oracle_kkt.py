@@ -184,3 +184,35 @@ def test_stair_needs_fewer_iterations_than_jacobi(oracle):
         S = oracle.schur(prob, X, U, precond=pc)
         its.append(oracle.pcg(S["Sd"], S["Ss"], S["Pd"], S["Ps"], S["rhs"], eps=1e-8, maxit=5000)[1])
     assert its[0] < its[1]
+
+
+def test_fp32_storage_of_the_schur_matrix_moves_the_step(oracle):
+    """The accuracy an FP32 step can have, measured with the oracle alone.
+
+    At the cold start of a figure-eight solve (N = 64) the Schur complement
+    S = C G^-1 C^T has a condition number near 1e9.  Rounding its assembled
+    entries to FP32 and solving the residual-form system exactly in FP64
+    changes the recovered step dZ = -G^-1 (d + C^T dnu) by 1e-4..2e-3 of its
+    size, while rounding the inputs A, B, G^-1 it is formed from changes it by
+    far less: an FP32 step is accurate to ~eps_32 sqrt(kappa(S)) of its size,
+    whatever the solver.  (The GPU tests' per-step bound is this number.)
+    """
+    prob = I.ee_problem(1, I.arm7(), N=64, dt=0.01)
+    X, U, lam = oracle.cold_start(prob)
+    lin = oracle.linearize(prob, X, U)
+    G, g, C, c, _, _ = dense_kkt(lin)
+    Gi = np.linalg.inv(G)
+    S = C @ Gi @ C.T
+    d = g + C.T @ lam.ravel()
+    rhs = -c - C @ Gi @ d
+    f32 = lambda a: a.astype(np.float32).astype(np.float64)
+    step = lambda Sm: -Gi @ (d + C.T @ np.linalg.solve(Sm, rhs))
+    exact = step(S)
+    moved = np.abs(step(f32(S)) - exact).max() / np.abs(exact).max()
+    assert np.linalg.cond(S) > 1e8
+    assert 1e-4 < moved < 2e-3, moved
+    lin32 = {k: (f32(v) if isinstance(v, np.ndarray) else v) for k, v in lin.items()}
+    G2, _, C2, _, _, _ = dense_kkt(lin32)
+    S2 = C2 @ np.linalg.inv(G2) @ C2.T
+    inputs_moved = np.abs(step(S2) - exact).max() / np.abs(exact).max()
+    assert inputs_moved < 0.1 * moved, (inputs_moved, moved)

@@ -286,3 +286,33 @@ def test_one_nonlinear_sqp_iteration_from_pinned_parts(oracle, kind, model, seed
     nu = np.asarray(lam, dtype=np.float64).ravel()
     kkt = max(np.abs(c).max(), np.abs(g + C.T @ nu).max() / max(1.0, np.abs(g).max()))
     assert abs(oracle.kkt_residual(prob, X, U, lam) - kkt) <= 1e-12 * max(1.0, kkt)
+
+
+def test_fixed_count_iterate_depends_on_pcg_truncation(oracle):
+    """What a fixed-count comparison can ask of any implementation.
+
+    Two FP64 runs of the method that differ only in how exactly each QP is
+    solved (PCG stopped by its rule at eps = 1e-6, Sec. II-B, or the direct
+    block elimination, its exact solution) follow the same step-length
+    sequence, yet after the single-solve workload's 5 iterations from seed 5
+    their iterates differ by more than 1e-4 relative: the unconverged SQP
+    amplifies the PCG's per-step truncation (~1e-6 of the step).  Run to
+    convergence, both reach the same KKT point.  So the iterate after a fixed
+    count is determined by the method only up to this spread, and the GPU
+    tests compare fixed-count iterates only where the spread is below 1e-5.
+    """
+    prob = I.joint_problem(5, I.arm7(), 32, 0.01)
+    a = oracle.solve(prob, max_iter=5)
+    b = oracle.solve(prob, max_iter=5, linsolve=1)
+    assert list(a["alpha_idx"]) == list(b["alpha_idx"])
+    rel = np.abs(a["X"] - b["X"]).max() / max(1.0, np.abs(b["X"]).max())
+    assert rel > 1e-4, rel
+    ca = oracle.solve(prob, max_iter=80, kkt_tol=1e-9)
+    cb = oracle.solve(prob, max_iter=80, kkt_tol=1e-9, linsolve=1)
+    assert ca["kkt"] <= 1e-7 and cb["kkt"] <= 1e-7
+    np.testing.assert_allclose(ca["X"], cb["X"], atol=1e-6 * max(1.0, np.abs(cb["X"]).max()), rtol=0)
+    # the same start at seed 1 is determined: there the spread is below 1e-5
+    p1 = I.joint_problem(1, I.arm7(), 32, 0.01)
+    a1 = oracle.solve(p1, max_iter=5)
+    b1 = oracle.solve(p1, max_iter=5, linsolve=1)
+    assert np.abs(a1["X"] - b1["X"]).max() / max(1.0, np.abs(b1["X"]).max()) < 1e-5
