@@ -60,6 +60,8 @@ enum { GATO_PRECOND_STAIR = 0, GATO_PRECOND_JACOBI = 1 };
 /* Linear solver of the Schur system (gato_solver_params.linsolve). */
 enum { GATO_LINSOLVE_PCG = 0, GATO_LINSOLVE_DIRECT = 1 };
 enum { GATO_MEM_HOST = 0, GATO_MEM_DEVICE = 1 };
+/* Arithmetic of a solve (gato_solver_params.precision). */
+enum { GATO_PRECISION_FP32 = 0, GATO_PRECISION_ESCALATE = 1 };
 
 /* Serial revolute chain (Sec. II-A "discrete-time dynamical system"; the
  * paper's robots are modelled the same way by its dynamics library).  Joint i
@@ -99,6 +101,17 @@ typedef struct {
                               accepted step, * 2 after a rejected one, within
                               [1e-8, 1e1]; it starts from w[5] at every call.
                               0 (default): rho fixed */
+  int32_t precision;       /* GATO_PRECISION_ESCALATE (default): the bulk runs in FP32;
+                              a solve whose FP32 line search finds no merit decrease
+                              (near a solution, where FP32 rounding of the dynamics
+                              and of the iterate exceeds the decrease) repeats that
+                              SQP iteration in a high-precision mode and stays in it
+                              for the rest of the call: FP64 mass matrix and bias,
+                              each dynamics solve refined once in FP64, the iterate
+                              kept as double-float pairs, trial merits in FP64.  The
+                              repeated iteration counts once.
+                              GATO_PRECISION_FP32: never escalate (the step is then
+                              rejected with GATO_SOLVE_LSFAIL) */
 } gato_solver_params;
 
 typedef struct {
@@ -140,7 +153,8 @@ typedef struct {
 
 typedef struct gato_batch gato_batch;
 
-/* Fills the library defaults (mu 10, beta 2, A 8, eps 1e-6, cap 1000, stair, no tolerance). */
+/* Fills the library defaults (mu 10, beta 2, A 8, eps 1e-6, cap 1000, stair, no tolerance,
+ * PCG, rho fixed, precision escalation on). */
 void gato_default_params(gato_solver_params* out);
 
 /* Creates a batch: validates and copies the models, allocates device scratch
@@ -176,14 +190,16 @@ gato_status gato_solve_plain(gato_batch* b, const gato_problem* problems, int32_
  *
  * Same solver and kernel as gato_solve, but it needs no gato_batch: its
  * scratch (per-solve workspace, descriptors, models, launch order) is a set of
- * fixed-size arrays compiled into the library, about 2.6 MiB held on every GPU
+ * fixed-size arrays compiled into the library, about 2.7 MiB held on every GPU
  * that loads it until the process exits.  Limits: n <= 16 solves, N <= 64,
  * n_models <= 8, and every problem must use GATO_MEM_DEVICE pointers; larger
  * or host problems return GATO_E_INVALID and launch nothing.  `results` is a
  * DEVICE array of n gato_result that the kernel writes.  The call is
  * asynchronous on cuda_stream (a cudaStream_t, NULL = legacy default stream);
  * synchronise the stream before reading X, U, lambda or results.  It calls no
- * cudaMalloc or cudaFree.  The first call on each device looks up the device
+ * cudaMalloc or cudaFree, and it makes no host-to-device copy: the call's
+ * descriptors travel as the by-value argument of a one-block kernel launched
+ * on cuda_stream ahead of the solve, which stores them into the arrays.  The first call on each device looks up the device
  * addresses of the arrays (cudaGetSymbolAddress) with that device current;
  * make that first call before any stream capture.  All calls share the same
  * arrays, so calls whose kernels overlap on the GPU (another stream, another
@@ -391,6 +407,21 @@ gato_status gato_debug_plain_stage(gato_batch* b, const gato_problem* problems, 
  * tangents, Jacobians, KKT, Schur, block inverse, PCG start, PCG S-phase,
  * PCG y-phase, PCG w/z-phase, recovery, line search, accept. */
 gato_status gato_debug_stage_cycles(gato_batch* b, int32_t enable, int64_t* cycles, int32_t n);
+
+/* Per-iteration log of the fused kernel (the parity tests compare the
+ * line-search choices with the FP64 oracle's, Sec. II-A Step 3 / Eq. 7).
+ * enable = 1 allocates a log of max_iters records per solve (device memory);
+ * every following gato_solve / gato_step call of the batch rewrites it from
+ * iteration 0.  enable = 0 copies n x max_iters records to `log` (if non-NULL;
+ * max_iters must equal the enabled value) and frees it.  A record is 4 int32:
+ * the line search's choice (alpha index i of alpha = beta^-i, -1 = step
+ * rejected, -2 = iteration not reached), the PCG iterations of that SQP
+ * iteration, the KKT residual at its linearisation (the bits of a float), and
+ * 1 if the iteration ran in the high-precision mode.  Synchronous.
+ * GATO_E_INVALID for bad arguments, GATO_E_NOMEM if the log cannot be
+ * allocated. */
+gato_status gato_debug_iteration_log(gato_batch* b, int32_t enable, int32_t max_iters, int32_t* log,
+                                     int32_t n);
 
 /* Fills offsets[0..24] (floats) of the workspace arrays in the order
  * X U dX dU Fq Fv Minv qdd dTau Qinv Rinv q r c Jk Linv links D L P vec scal

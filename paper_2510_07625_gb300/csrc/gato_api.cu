@@ -33,6 +33,78 @@ struct HostCopyBack {
 
 }  // namespace
 
+namespace gato {
+
+const char* check_model(const gato_model_desc& d, DevModel& m) {
+  if (d.dof < 1 || d.dof > QM) return "model dof must be 1..7";
+  if (!(d.gravity >= 0.f) || !std::isfinite(d.gravity)) return "gravity must be finite and >= 0";
+  std::memset(&m, 0, sizeof(m));
+  m.dof = d.dof;
+  m.g = d.gravity;
+  for (int i = 0; i < QM; ++i) {
+    if (i < d.dof) {
+      if (d.axis[i] < 0 || d.axis[i] > 2) return "joint axis must be 0, 1 or 2";
+      if (!(d.link_len[i] >= 0.f) || !std::isfinite(d.link_len[i])) return "link lengths must be finite and >= 0";
+      if (!(d.mass[i] > 0.f) || !std::isfinite(d.mass[i])) return "link masses must be finite and > 0";
+      m.axis[i] = d.axis[i];
+      m.L[i] = d.link_len[i];
+      m.m[i] = d.mass[i];
+      for (int a = 0; a < 3; ++a) {
+        const float c = d.com[3 * i + a], I = d.inertia[3 * i + a];
+        if (!std::isfinite(c) || !(I >= 0.f) || !std::isfinite(I)) return "com / inertia must be finite, inertia >= 0";
+        m.com[3 * i + a] = c;
+        m.Ic[3 * i + a] = I;
+      }
+    } else {
+      // massless padding joint at the end effector: exact zero rows downstream
+      m.axis[i] = 2;
+    }
+  }
+  return nullptr;
+}
+
+const char* check_params(const gato_solver_params& p) {
+  if (!(p.mu >= 0.f) || !std::isfinite(p.mu)) return "mu must be finite and >= 0";
+  if (!(p.beta > 1.f) || !std::isfinite(p.beta)) return "beta must be > 1";
+  if (p.n_alpha < 1 || p.n_alpha > MAX_ALPHA) return "n_alpha must be 1..16";
+  if (!(p.pcg_eps > 0.f)) return "pcg_eps must be > 0";
+  if (p.pcg_max_iter < 1) return "pcg_max_iter must be >= 1";
+  if (p.precond != GATO_PRECOND_STAIR && p.precond != GATO_PRECOND_JACOBI) return "unknown preconditioner";
+  if (p.linsolve != GATO_LINSOLVE_PCG && p.linsolve != GATO_LINSOLVE_DIRECT) return "unknown linear solver";
+  if (p.rho_adapt != 0 && p.rho_adapt != 1) return "rho_adapt must be 0 or 1";
+  if (p.precision != GATO_PRECISION_FP32 && p.precision != GATO_PRECISION_ESCALATE)
+    return "precision must be GATO_PRECISION_FP32 or GATO_PRECISION_ESCALATE";
+  if (!std::isfinite(p.kkt_tol)) return "kkt_tol must be finite";
+  return nullptr;
+}
+
+const char* check_problem(const gato_problem& p, int n_models, int max_horizon) {
+  if (p.model < 0 || p.model >= n_models) return "model index out of range";
+  if (p.N < 1 || p.N > max_horizon) return "N must be 1..max_horizon";
+  if (!(p.dt > 0.f) || !std::isfinite(p.dt)) return "dt must be finite and > 0";
+  if (p.mem != GATO_MEM_HOST && p.mem != GATO_MEM_DEVICE) return "mem must be HOST or DEVICE";
+  if (!p.x_s || !p.X || !p.U) return "x_s, X and U are required";
+  for (int i = 0; i < 6; ++i)
+    if (!std::isfinite(p.w[i]) || p.w[i] < 0.f) return "weights must be finite and >= 0";
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(p.f_ext[i])) return "f_ext must be finite";
+  const float wq = p.w[0], wqd = p.w[1], wr = p.w[2], ts = p.w[3], rho = p.w[5];
+  if (!(wr > 0.f)) return "control weight must be > 0";
+  if (!(ts > 0.f)) return "terminal scale must be > 0";
+  if (p.cost_kind == GATO_COST_JOINT) {
+    if (!p.x_ref) return "joint cost needs x_ref";
+    if (!(wq + rho > 0.f) || !(wqd + rho > 0.f)) return "joint cost Hessian must be positive definite";
+  } else if (p.cost_kind == GATO_COST_EE) {
+    if (!p.ee_ref) return "end-effector cost needs ee_ref";
+    if (!(rho > 0.f) || !(wqd + rho > 0.f)) return "end-effector cost needs rho > 0";
+  } else {
+    return "unknown cost kind";
+  }
+  return nullptr;
+}
+
+}  // namespace gato
+
 struct gato_batch {
   int max_batch = 0, max_horizon = 0, n_models = 0;
   DevModel models_h[8];
@@ -60,6 +132,8 @@ struct gato_batch {
   std::vector<HostCopyBack> copy_back;
   std::vector<int> N_h;   // horizon of each solve of the current call
   long long* timing_d = nullptr;  // per-stage cycle counters while profiling is on
+  int* itlog_d = nullptr;         // per-iteration records while the log is on
+  int itlog_iters = 0;
   // launch plans: one set by gato_set_launch_config, else the autotuner's
   // choice for the call's (batch size, horizon) bucket, else automatic
   bool forced = false;
@@ -119,46 +193,14 @@ size_t stage_floats(int nmax) {
 }
 
 bool convert_model(const gato_model_desc& d, DevModel& m, std::string& why) {
-  if (d.dof < 1 || d.dof > QM) { why = "model dof must be 1..7"; return false; }
-  if (!(d.gravity >= 0.f) || !std::isfinite(d.gravity)) { why = "gravity must be finite and >= 0"; return false; }
-  std::memset(&m, 0, sizeof(m));
-  m.dof = d.dof;
-  m.g = d.gravity;
-  for (int i = 0; i < QM; ++i) {
-    if (i < d.dof) {
-      if (d.axis[i] < 0 || d.axis[i] > 2) { why = "joint axis must be 0, 1 or 2"; return false; }
-      if (!(d.link_len[i] >= 0.f) || !std::isfinite(d.link_len[i])) { why = "link lengths must be finite and >= 0"; return false; }
-      if (!(d.mass[i] > 0.f) || !std::isfinite(d.mass[i])) { why = "link masses must be finite and > 0"; return false; }
-      m.axis[i] = d.axis[i];
-      m.L[i] = d.link_len[i];
-      m.m[i] = d.mass[i];
-      for (int a = 0; a < 3; ++a) {
-        const float c = d.com[3 * i + a], I = d.inertia[3 * i + a];
-        if (!std::isfinite(c) || !(I >= 0.f) || !std::isfinite(I)) { why = "com / inertia must be finite, inertia >= 0"; return false; }
-        m.com[3 * i + a] = c;
-        m.Ic[3 * i + a] = I;
-      }
-    } else {
-      // massless padding joint at the end effector: exact zero rows downstream
-      m.axis[i] = 2;
-    }
-  }
-  return true;
+  const char* r = check_model(d, m);
+  if (r) why = r;
+  return r == nullptr;
 }
 
 gato_status validate_params(gato_batch* b, const gato_solver_params& p) {
-  if (!(p.mu >= 0.f) || !std::isfinite(p.mu)) return fail(b, GATO_E_INVALID, "mu must be finite and >= 0");
-  if (!(p.beta > 1.f) || !std::isfinite(p.beta)) return fail(b, GATO_E_INVALID, "beta must be > 1");
-  if (p.n_alpha < 1 || p.n_alpha > MAX_ALPHA) return fail(b, GATO_E_INVALID, "n_alpha must be 1..16");
-  if (!(p.pcg_eps > 0.f)) return fail(b, GATO_E_INVALID, "pcg_eps must be > 0");
-  if (p.pcg_max_iter < 1) return fail(b, GATO_E_INVALID, "pcg_max_iter must be >= 1");
-  if (p.precond != GATO_PRECOND_STAIR && p.precond != GATO_PRECOND_JACOBI)
-    return fail(b, GATO_E_INVALID, "unknown preconditioner");
-  if (p.linsolve != GATO_LINSOLVE_PCG && p.linsolve != GATO_LINSOLVE_DIRECT)
-    return fail(b, GATO_E_INVALID, "unknown linear solver");
-  if (p.rho_adapt != 0 && p.rho_adapt != 1) return fail(b, GATO_E_INVALID, "rho_adapt must be 0 or 1");
-  if (!std::isfinite(p.kkt_tol)) return fail(b, GATO_E_INVALID, "kkt_tol must be finite");
-  return GATO_OK;
+  const char* r = check_params(p);
+  return r ? fail(b, GATO_E_INVALID, r) : GATO_OK;
 }
 
 gato_status validate_problem(gato_batch* b, const gato_problem& p, int idx) {
@@ -167,27 +209,7 @@ gato_status validate_problem(gato_batch* b, const gato_problem& p, int idx) {
     std::snprintf(buf, sizeof(buf), "problem %d: %s", idx, why);
     return fail(b, GATO_E_INVALID, buf);
   };
-  if (p.model < 0 || p.model >= b->n_models) return bad("model index out of range");
-  if (p.N < 1 || p.N > b->max_horizon) return bad("N must be 1..max_horizon");
-  if (!(p.dt > 0.f) || !std::isfinite(p.dt)) return bad("dt must be finite and > 0");
-  if (p.mem != GATO_MEM_HOST && p.mem != GATO_MEM_DEVICE) return bad("mem must be HOST or DEVICE");
-  if (!p.x_s || !p.X || !p.U) return bad("x_s, X and U are required");
-  for (int i = 0; i < 6; ++i)
-    if (!std::isfinite(p.w[i]) || p.w[i] < 0.f) return bad("weights must be finite and >= 0");
-  for (int i = 0; i < 3; ++i)
-    if (!std::isfinite(p.f_ext[i])) return bad("f_ext must be finite");
-  const float wq = p.w[0], wqd = p.w[1], wr = p.w[2], ts = p.w[3], rho = p.w[5];
-  if (!(wr > 0.f)) return bad("control weight must be > 0");
-  if (!(ts > 0.f)) return bad("terminal scale must be > 0");
-  if (p.cost_kind == GATO_COST_JOINT) {
-    if (!p.x_ref) return bad("joint cost needs x_ref");
-    if (!(wq + rho > 0.f) || !(wqd + rho > 0.f)) return bad("joint cost Hessian must be positive definite");
-  } else if (p.cost_kind == GATO_COST_EE) {
-    if (!p.ee_ref) return bad("end-effector cost needs ee_ref");
-    if (!(rho > 0.f) || !(wqd + rho > 0.f)) return bad("end-effector cost needs rho > 0");
-  } else {
-    return bad("unknown cost kind");
-  }
+  if (const char* r = check_problem(p, b->n_models, b->max_horizon)) return bad(r);
   if (p.mem == GATO_MEM_HOST) {
     const int nx = 2 * b->model_dof[p.model], nu = b->model_dof[p.model];
     if (!finite_all(p.x_s, nx)) return bad("x_s is not finite");
@@ -214,6 +236,7 @@ Params to_params(const gato_solver_params& p, int iters) {
   o.max_iter = iters;
   o.linsolve = p.linsolve;
   o.rho_adapt = p.rho_adapt;
+  o.escalate = p.precision == GATO_PRECISION_ESCALATE;
   return o;
 }
 
@@ -350,6 +373,8 @@ cudaError_t launch_solve(gato_batch* b, int n, int nmax, int iters) {
   a.iters = iters;
   a.prm = to_params(b->params, iters);
   a.timing = b->timing_d;
+  a.itlog = b->itlog_d;
+  a.itlog_iters = b->itlog_iters;
   a.variant = 0;
   return launch_fused_grouped(a, b->order_h, b->order_d, b->N_h.data(), n, b->stream, b->cur_plan);
 }
@@ -447,6 +472,7 @@ void gato_default_params(gato_solver_params* o) {
   o->kkt_tol = 0.f;
   o->linsolve = GATO_LINSOLVE_PCG;
   o->rho_adapt = 0;
+  o->precision = GATO_PRECISION_ESCALATE;
 }
 
 const char* gato_status_string(gato_status s) {
@@ -539,6 +565,7 @@ void gato_destroy_batch(gato_batch* b) {
   cudaFree(b->plain_ws_d);
   cudaFree(b->stage_d);
   cudaFree(b->timing_d);
+  cudaFree(b->itlog_d);
   cudaFreeHost(b->probs_h);
   cudaFreeHost(b->order_h);
   cudaFreeHost(b->res_h);
@@ -690,6 +717,41 @@ gato_status gato_debug_stage_cycles(gato_batch* b, int32_t enable, int64_t* cycl
   }
   cudaFree(b->timing_d);
   b->timing_d = nullptr;
+  return GATO_OK;
+}
+
+gato_status gato_debug_iteration_log(gato_batch* b, int32_t enable, int32_t max_iters, int32_t* log,
+                                     int32_t n) {
+  if (!b) return GATO_E_INVALID;
+  if (b->pending) {
+    gato_status s = gato_sync(b, -1);
+    if (s != GATO_OK) return s;
+  }
+  if (enable) {
+    if (max_iters < 1) return fail(b, GATO_E_INVALID, "max_iters must be >= 1");
+    cudaFree(b->itlog_d);
+    b->itlog_d = nullptr;
+    b->itlog_iters = 0;
+    const size_t bytes = (size_t)b->max_batch * max_iters * ITLOG_W * sizeof(int);
+    if (cudaMalloc(&b->itlog_d, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(b, GATO_E_NOMEM, "iteration log");
+    }
+    if (cudaMemsetAsync(b->itlog_d, 0, bytes, b->stream) != cudaSuccess) return GATO_E_CUDA;
+    b->itlog_iters = max_iters;
+    return GATO_OK;
+  }
+  if (!b->itlog_d) return fail(b, GATO_E_INVALID, "the iteration log was not enabled");
+  if (log) {
+    if (n < 1 || n > b->max_batch) return fail(b, GATO_E_INVALID, "bad solve count");
+    if (max_iters != b->itlog_iters) return fail(b, GATO_E_INVALID, "max_iters differs from the enabled log");
+    if (cudaMemcpy(log, b->itlog_d, (size_t)n * max_iters * ITLOG_W * sizeof(int), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+      return GATO_E_CUDA;
+  }
+  cudaFree(b->itlog_d);
+  b->itlog_d = nullptr;
+  b->itlog_iters = 0;
   return GATO_OK;
 }
 

@@ -5,6 +5,7 @@
 #include <cstddef>
 #include <cuda_runtime.h>
 
+#include "../../include/gato.h"
 #include "gato_device.cuh"
 #include "gato_phases.cuh"
 
@@ -29,6 +30,8 @@ struct FusedLaunch {
   int iters;
   Params prm;
   long long* timing;       // device [n_total][T_COUNT] cycle counters, or null
+  int* itlog = nullptr;    // device [n_total][itlog_iters][ITLOG_W] iteration records, or null
+  int itlog_iters = 0;
   int variant;             // 0 = automatic, 1 = register rows (1 CTA/SM), 2 = 2 CTAs/SM
 };
 
@@ -78,6 +81,14 @@ size_t fused_smem_bytes(int nmax, int csize);
 // Clusters of csize CTAs of the fused kernel (latency form if reg) that the
 // current device holds at once for a launch whose largest horizon is nmax.
 cudaError_t fused_active_clusters(int nmax, int csize, bool reg, int* out);
+
+// Host-side input checks shared by every entry point.  Each returns nullptr
+// when its input is valid, else a short reason.  check_model also fills the
+// device form of the model (padded to QM joints).  check_problem looks at the
+// fields of one problem, not at the contents of its arrays.
+const char* check_model(const gato_model_desc& d, DevModel& m);
+const char* check_params(const gato_solver_params& p);
+const char* check_problem(const gato_problem& p, int n_models, int max_horizon);
 
 enum PlainStage : int {
   PS_LOAD = 0, PS_MASS, PS_FD, PS_VALUE, PS_TANGENT, PS_JAC, PS_KKT, PS_SCHUR, PS_BINV, PS_PCG,

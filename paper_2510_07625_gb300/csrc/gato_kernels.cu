@@ -194,6 +194,7 @@ cudaError_t launch_plain(const ProbDesc* probs, const DevModel* models, Result* 
   a.iters = iters;
   a.prm = prm;
   a.it = 0;
+  a.redo = 0;
   a.csize = cluster_for(N_b);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)a.csize);
@@ -217,10 +218,27 @@ cudaError_t launch_plain(const ProbDesc* probs, const DevModel* models, Result* 
       if ((e = go(st)) != cudaSuccess) return e;
       if (stop_stage == st) return cudaSuccess;
     }
-    if (it == iters) break;
+    if (it == iters) {
+      if (prm.escalate && prm.kkt_tol > 0.f) {
+        // a convergence test passed in FP32 is repeated in the high-precision mode
+        a.redo = 1;
+        for (int st = PS_MASS; st <= PS_KKT; ++st)
+          if ((e = go(st)) != cudaSuccess) return e;
+        a.redo = 0;
+      }
+      break;
+    }
     for (int st = PS_SCHUR; st <= PS_ACCEPT; ++st) {
       if ((e = go(st)) != cudaSuccess) return e;
       if (stop_stage == st) return cudaSuccess;
+    }
+    if (prm.escalate) {
+      // the pass that repeats the iteration in the high-precision mode when its
+      // FP32 line search found no decrease (each launch returns at once otherwise)
+      a.redo = 1;
+      for (int st = PS_MASS; st <= PS_ACCEPT; ++st)
+        if ((e = go(st)) != cudaSuccess) return e;
+      a.redo = 0;
     }
   }
   return go(PS_STORE);

@@ -34,6 +34,8 @@ __device__ __forceinline__ void bind_workspace(Ctx& C, float* ws, const WsLayout
   C.Dx = ws + L.Dx;
   C.Du = ws + L.Du;
   C.nu = ws + L.nu;
+  C.Xlo = ws + L.Xlo;
+  C.Ulo = ws + L.Ulo;
   C.LV = reinterpret_cast<LinkRec*>(ws + L.LV);
 }
 
@@ -61,16 +63,24 @@ __device__ __forceinline__ void bind_partition(Ctx& C, int rank, int csize) {
 
 // The whole SQP loop of one solve (Sec. II-A Steps 1-3, repeated).
 template <bool REG>
-__device__ void sqp_solve(Ctx& C, const ProbDesc& P, const Params& prm, int iters, Result* out) {
+__device__ void sqp_solve(Ctx& C, const ProbDesc& P, const Params& prm, int iters, Result* out,
+                          int* itlog = nullptr, int itlog_iters = 0) {
   int rbuf = 0;
   long long tl = C.tm ? clock64() : 0;
+  const bool logging = itlog && C.rank == 0 && threadIdx.x == 0;
+  if (logging)
+    for (int i = 0; i < itlog_iters * ITLOG_W; ++i) itlog[i] = (i % ITLOG_W == 0) ? -2 : 0;
   load_iterate(C, P);
   csync(C);
   tstamp(C, T_LOAD, tl);
   int flags = 0, sqp = 0, pcg_total = 0;
   float kkt = 0.f, merit = 0.f;
+  bool base_stale = true;  // the iterate's own merit is due (first iteration, or after escalating)
+  int pcg_at_start = 0;    // pcg_total when the iteration began (for the log)
   for (int it = 0;; ++it) {
     if (it == iters && !(prm.kkt_tol > 0.f)) break;
+    pcg_at_start = pcg_total;
+  retry:
     st_mass_bias(C);
     __syncthreads();
     tstamp(C, T_MASS, tl);
@@ -87,7 +97,10 @@ __device__ void sqp_solve(Ctx& C, const ProbDesc& P, const Params& prm, int iter
     csync(C);  // defect c_k0 comes from the neighbour's last knot
     tstamp(C, T_JAC, tl);
     st_kkt_merit(C, prm.mu, rbuf);
-    if (it == 0) st_line_search(C, prm.mu, prm.beta, prm.n_alpha, rbuf, true);  // the iterate's merit
+    if (base_stale) {  // the iterate's merit, by the code that evaluates the trial merits
+      st_line_search(C, prm.mu, prm.beta, prm.n_alpha, rbuf, true);
+      base_stale = false;
+    }
     tstamp(C, T_KKT, tl);
     kkt = C.scal[S_KKT];
     merit = C.scal[S_MERIT0];
@@ -97,6 +110,13 @@ __device__ void sqp_solve(Ctx& C, const ProbDesc& P, const Params& prm, int iter
       break;
     }
     if (prm.kkt_tol > 0.f && kkt <= prm.kkt_tol) {
+      if (prm.escalate && !C.hp) {
+        // confirm convergence with the high-precision residual: the FP32
+        // dual residual carries the kappa(M)-amplified error of A_k
+        C.hp = 1;
+        base_stale = true;
+        goto retry;
+      }
       flags |= F_CONVERGED;
       break;
     }
@@ -136,6 +156,20 @@ __device__ void sqp_solve(Ctx& C, const ProbDesc& P, const Params& prm, int iter
     tstamp(C, T_LS, tl);
     const int choice = st_accept(C, prm.beta, prm.n_alpha);
     csync(C);
+    if (choice < 0 && prm.escalate && !C.hp) {
+      // the FP32 line search found no decrease: repeat this iteration in the
+      // high-precision mode (every thread takes the same branch)
+      C.hp = 1;
+      base_stale = true;
+      goto retry;
+    }
+    if (logging && it < itlog_iters) {
+      int* r = itlog + it * ITLOG_W;
+      r[0] = choice;
+      r[1] = pcg_total - pcg_at_start;
+      r[2] = __float_as_int(kkt);
+      r[3] = C.hp;
+    }
     if (prm.rho_adapt) C.w[5] = rho_next(C.w[5], choice);  // every thread, the same choice
     tstamp(C, T_ACCEPT, tl);
     if (choice >= 0)
@@ -219,7 +253,8 @@ __global__ void __launch_bounds__(NTHR, REG ? 1 : 2) sqp_fused(FusedLaunch a) {
   }
   for (int i = threadIdx.x; i < 196; i += NTHR) zblock[i] = 0.f;
   __syncthreads();
-  sqp_solve<REG>(C, P, a.prm, a.iters, a.results + b);
+  sqp_solve<REG>(C, P, a.prm, a.iters, a.results + b,
+                 a.itlog ? a.itlog + (size_t)b * a.itlog_iters * ITLOG_W : nullptr, a.itlog_iters);
   if (a.timing) {
     __syncthreads();
     if (rank == 0 && threadIdx.x < T_COUNT) a.timing[(size_t)b * T_COUNT + threadIdx.x] += tm_sh[threadIdx.x];
@@ -235,6 +270,7 @@ struct PlainArgs {
   float* ws;
   WsLayout layout;
   int b, nmax, iters, it, csize;
+  int redo;  // 1: the pass that repeats an iteration in the high-precision mode
   Params prm;
 };
 
@@ -278,6 +314,7 @@ __global__ void __launch_bounds__(NTHR, 1) sqp_plain_stage(int stage, PlainArgs 
     return;
   }
   if (a.prm.rho_adapt) C.w[5] = C.scal[S_RHO];  // the adapted rho of this SQP iteration
+  C.hp = C.scal[S_HP] != 0.f;
   if (stage == PS_STORE) {
     store_iterate(C, P);
     if (rank == 0 && threadIdx.x == 0) {
@@ -291,6 +328,9 @@ __global__ void __launch_bounds__(NTHR, 1) sqp_plain_stage(int stage, PlainArgs 
     return;
   }
   if (C.scal[S_DONE] != 0.f) return;
+  if (a.redo && C.scal[S_REDO] == 0.f) return;  // no escalation in this iteration
+  // an escalation decided at the KKT stage skips the rest of the first pass
+  if (!a.redo && stage > PS_KKT && C.scal[S_REDO] != 0.f) return;
   const bool lead = rank == 0 && threadIdx.x == 0;
   switch (stage) {
     case PS_MASS: st_mass_bias(C); break;
@@ -300,7 +340,7 @@ __global__ void __launch_bounds__(NTHR, 1) sqp_plain_stage(int stage, PlainArgs 
     case PS_JAC: st_dyn_jacobians(C); break;
     case PS_KKT: {
       st_kkt_merit(C, prm.mu, rbuf);
-      if (a.it == 0) st_line_search(C, prm.mu, prm.beta, prm.n_alpha, rbuf, true);  // the iterate's merit
+      if (a.it == 0 || a.redo) st_line_search(C, prm.mu, prm.beta, prm.n_alpha, rbuf, true);  // the iterate's merit
       const bool bad = *reinterpret_cast<volatile int*>(C.scal + S_FLAGS) != 0;
       if (lead) {
         C.scal[S_MERITF] = C.scal[S_MERIT0];
@@ -309,6 +349,11 @@ __global__ void __launch_bounds__(NTHR, 1) sqp_plain_stage(int stage, PlainArgs 
         if (bad) {
           f |= F_NONFINITE;
           done = true;
+        } else if (prm.kkt_tol > 0.f && C.scal[S_KKT] <= prm.kkt_tol && prm.escalate && !C.hp) {
+          // confirm convergence with the high-precision residual (the pass
+          // that repeats this iteration in that mode)
+          C.scal[S_HP] = 1.f;
+          C.scal[S_REDO] = 1.f;
         } else if (prm.kkt_tol > 0.f && C.scal[S_KKT] <= prm.kkt_tol) {
           f |= F_CONVERGED;
           done = true;
@@ -359,6 +404,15 @@ __global__ void __launch_bounds__(NTHR, 1) sqp_plain_stage(int stage, PlainArgs 
     case PS_LS: st_line_search(C, prm.mu, prm.beta, prm.n_alpha, rbuf); break;
     case PS_ACCEPT: {
       const int choice = st_accept(C, prm.beta, prm.n_alpha);
+      if (choice < 0 && prm.escalate && !C.hp) {
+        // repeat this iteration in the high-precision mode (the next pass)
+        if (lead) {
+          C.scal[S_HP] = 1.f;
+          C.scal[S_REDO] = 1.f;
+        }
+        break;
+      }
+      if (lead) C.scal[S_REDO] = 0.f;
       if (lead && prm.rho_adapt) C.scal[S_RHO] = rho_next(C.w[5], choice);
       if (lead) {
         if (choice >= 0)

@@ -55,6 +55,12 @@ struct Ctx {
   float *X, *U, *dX, *dU, *Fq, *Fv, *Mi, *qdd, *dT, *Qi, *Ri, *qg, *rg, *cv, *Jk;
   float *Dx, *Du;       // dual residual d = g + C^T nu at the current linearisation
   float* nu;            // multiplier (global, all knots)
+  // low parts of the iterate (X + Xlo, U + Ulo as double-float pairs); zero
+  // until the solve escalates to the high-precision mode
+  float *Xlo, *Ulo;
+  // 1 once the solve has escalated: FP64 mass matrix and bias, refined
+  // dynamics solves, double-float iterate, FP64 trial merits
+  int hp = 0;
   LinkRec* LV;
   float* xs;            // padded x_s [VS]
   // Schur / preconditioner blocks: knot k at index k - bk0
@@ -102,7 +108,9 @@ enum : int {
   S_KKT = 0, S_MERIT0, S_CMAX, S_GMAX, S_DMAX, S_ALPHA, S_FLAGS, S_PCG, S_ITERS, S_MERITF,
   S_CHOICE, S_REDBUF, S_DONE, S_NSQP, S_NPCG, S_RFLAGS, S_MERITS = 16,  // S_MERITS..+15
   S_RHO = 32,  // the adapted rho between the plain form's launches
-  S_FEXT = 33  // S_FEXT..+2: the solve's end-effector force (base frame)
+  S_FEXT = 33, // S_FEXT..+2: the solve's end-effector force (base frame)
+  S_HP = 36,   // plain form: 1 once the solve is in the high-precision mode
+  S_REDO = 37  // plain form: 1 while an iteration is to be repeated in that mode
 };
 
 // The solve's constant end-effector force (Sec. IV-D's disturbance hypotheses).
@@ -117,12 +125,18 @@ __device__ __forceinline__ float rho_next(float rho, int choice) {
   return choice >= 0 ? fmaxf(rho / 3.f, 1e-8f) : fminf(rho * 2.f, 1e1f);
 }
 
+// One record of the per-iteration log (int32 each): the line search's choice
+// (alpha index, -1 rejected; -2 for an iteration not reached), the PCG
+// iterations of the iteration, the KKT residual at its linearisation (float
+// bits), 1 if it ran in the high-precision mode.
+constexpr int ITLOG_W = 4;
+
 // Per-knot strides of the global workspace arrays.
 constexpr int FQS = 49, QIS = 56, DTS = 14 * 8, LIS = 196;
 
 struct WsLayout {
   size_t X, U, dX, dU, Fq, Fv, Mi, qdd, dT, Qi, Ri, qg, rg, cv, Jk, Li, LV, Dm, Lm, Pm, vec, Dx, Du,
-      nu, total;
+      nu, Xlo, Ulo, total;
 };
 
 __host__ __device__ inline size_t align32(size_t n) { return (n + 31) & ~size_t(31); }
@@ -153,6 +167,8 @@ __host__ __device__ inline WsLayout ws_layout(int Nmax, bool global_blocks, bool
   L.Dx = o; o += align32(K * VS);
   L.Du = o; o += align32(Nmax * US);
   L.nu = o; o += align32(K * VS);
+  L.Xlo = o; o += align32(K * VS);
+  L.Ulo = o; o += align32(Nmax * US);
   if (global_blocks) {
     L.Dm = o; o += align32(K * BS);
     L.Lm = o; o += align32(K * BS);
@@ -346,9 +362,13 @@ __device__ inline void load_iterate(const Ctx& C, const ProbDesc& P) {
   const int ke = C.k1 < N ? C.k1 : N;  // dynamics knots [k0, ke)
   for (int i = threadIdx.x; i < (C.k1 - C.k0) * VS; i += NTHR) {
     C.X[C.k0 * VS + i] = 0.f;
+    C.Xlo[C.k0 * VS + i] = 0.f;
     C.nu[C.k0 * VS + i] = 0.f;
   }
-  for (int i = threadIdx.x; i < (ke - C.k0) * US; i += NTHR) C.U[C.k0 * US + i] = 0.f;
+  for (int i = threadIdx.x; i < (ke - C.k0) * US; i += NTHR) {
+    C.U[C.k0 * US + i] = 0.f;
+    C.Ulo[C.k0 * US + i] = 0.f;
+  }
   if (threadIdx.x < VS) C.xs[threadIdx.x] = 0.f;
   __syncthreads();
   for (int i = threadIdx.x; i < (C.k1 - C.k0) * nx; i += NTHR) {
@@ -368,20 +388,93 @@ __device__ inline void store_iterate(const Ctx& C, const ProbDesc& P) {
   const int ke = C.k1 < N ? C.k1 : N;
   for (int i = threadIdx.x; i < (C.k1 - C.k0) * nx; i += NTHR) {
     const int k = C.k0 + i / nx, ui = i % nx;
-    P.X[k * nx + ui] = C.X[k * VS + pad_state(ui, dof)];
+    P.X[k * nx + ui] = C.X[k * VS + pad_state(ui, dof)] + C.Xlo[k * VS + pad_state(ui, dof)];
     if (P.lam) P.lam[k * nx + ui] = C.nu[k * VS + pad_state(ui, dof)];
   }
   for (int i = threadIdx.x; i < (ke - C.k0) * dof; i += NTHR) {
     const int k = C.k0 + i / dof, ui = i % dof;
-    P.U[k * dof + ui] = C.U[k * US + ui];
+    P.U[k * dof + ui] = C.U[k * US + ui] + C.Ulo[k * US + ui];
   }
 }
 
 // --------------------------------------------------- stage 1: linearisation
 
+// ---- high-precision mode (a solve escalates to it when its FP32 line search
+// finds no decrease; see sqp_solve)
+//
+// For the rod arms M's smallest eigenvalue (a thin link turning about its own
+// axis, m r^2 / 2) is about 1/3000 of its largest, while the RNEA rounds every
+// entry of M and of the bias at the scale of the largest forces in the chain;
+// solving M qdd = tau - b amplifies that rounding by kappa(M) (in FP32: ~1e-5
+// relative in A_k and in qdd, measured against the FP64 oracle).  Near a
+// solution that noise, and the FP32 rounding of the iterate itself, are larger
+// than the merit decrease of a step, so the FP32 line search stalls with a
+// KKT residual of 1e-6..1e-4.  The high-precision mode removes both: M and the
+// bias in FP64, each dynamics solve refined once against them, the iterate as
+// double-float (hi, lo) pairs, the trial merits in FP64.
+//
+// The stages below run as out-of-line calls with their fields passed by
+// value, so that their FP64 registers do not enter the allocation of the
+// kernel that calls them.
+
+// Mass-matrix columns and bias in FP64 at q = X + Xlo, one (knot, column) per
+// thread.  Each value is stored as an (hi, lo) float pair: hi in Mi (the bias
+// in qdd), lo in the tangent array dT (column c at dT + c * 8, the bias at
+// dT + 56), which is free until the tangent stage.
+struct MassView {
+  const DevModel* M;
+  const float *X, *Xlo;
+  float *Mi, *qdd, *dT;
+  float fx, fy, fz;
+  int k0, ke;
+};
+
+static __device__ __noinline__ void st_mass_bias_hp(MassView v) {
+  const DevModel& M = *v.M;
+  for (int it = threadIdx.x; it < (v.ke - v.k0) * 8; it += NTHR) {
+    const int k = v.k0 + (it >> 3), col = it & 7;
+    double sq[QM], cq[QM], qd[QM], acc[QM], tau[QM];
+    const float* x = v.X + k * VS;
+    const float* xl = v.Xlo + k * VS;
+#pragma unroll
+    for (int i = 0; i < QM; ++i) {
+      sincos((double)x[i] + (double)xl[i], &sq[i], &cq[i]);
+      qd[i] = (col == 7) ? (double)x[QM + i] + (double)xl[QM + i] : 0.0;
+      acc[i] = (i == col) ? 1.0 : 0.0;
+    }
+    const Vec3<double> fw = col == 7 ? v3t<double>(v.fx, v.fy, v.fz) : vzero<double>();
+    rnea_value<double>(M, sq, cq, qd, acc, col == 7 ? (double)M.g : 0.0, fw, tau, nullptr);
+    float* lo = v.dT + k * DTS + col * 8;
+#pragma unroll
+    for (int r = 0; r < QM; ++r) {
+      const float hi = (float)tau[r];
+      lo[r] = (float)(tau[r] - (double)hi);
+      if (col < 7) v.Mi[k * FQS + r * QM + col] = hi;
+      else v.qdd[k * US + r] = hi;
+    }
+  }
+}
+
 // Mass-matrix columns (unit-acceleration RNEA) and bias forces per knot.
 __device__ inline void st_mass_bias(const Ctx& C) {
   const int ke = C.k1 < C.N ? C.k1 : C.N;
+  if (C.hp) {
+    MassView v;
+    v.M = C.M;
+    v.X = C.X;
+    v.Xlo = C.Xlo;
+    v.Mi = C.Mi;
+    v.qdd = C.qdd;
+    v.dT = C.dT;
+    const V3 fw = ee_force(C);
+    v.fx = fw.x;
+    v.fy = fw.y;
+    v.fz = fw.z;
+    v.k0 = C.k0;
+    v.ke = ke;
+    st_mass_bias_hp(v);
+    return;
+  }
   const DevModel& M = *C.M;
   for (int it = threadIdx.x; it < (ke - C.k0) * 8; it += NTHR) {
     const int k = C.k0 + (it >> 3), col = it & 7;
@@ -404,12 +497,133 @@ __device__ inline void st_mass_bias(const Ctx& C) {
   }
 }
 
+// High-precision forward dynamics: M^-1 and qdd = M^-1 (u - bias) with one
+// step of iterative refinement each (the residual of the FP32 solution against
+// the FP64 (hi, lo) matrix, formed in FP64 and solved with the same FP32
+// factor: the refined error is ~kappa(M) eps_32 times the first one), and the
+// defects of the double-float iterate formed in FP64 from differences of the
+// iterates, e = (qd_k - qd_{k+1}) + h qdd, so that their rounding scales with
+// e itself rather than with the state.
+struct FdView {
+  const float *X, *Xlo, *U, *Ulo, *xs;
+  float *Mi, *qdd, *dT, *cv, *scal;
+  float h;
+  int N, dof, k0, k1;
+};
+
+static __device__ __noinline__ void st_forward_dynamics_hp(FdView v) {
+  const int N = v.N;
+  const int ke = v.k1 < N ? v.k1 : N;
+  const double h = v.h;
+  const int nk = ke - v.k0;
+  const int it = threadIdx.x;
+  const int k = v.k0 + (it >> 3), col = it & 7;
+  const bool act = it < 8 * nk;
+  float Ml[28];
+  if (act) {
+#pragma unroll
+    for (int i = 0; i < QM; ++i)
+#pragma unroll
+      for (int j2 = 0; j2 <= i; ++j2)
+        Ml[i * (i + 1) / 2 + j2] = 0.5f * (v.Mi[k * FQS + i * QM + j2] + v.Mi[k * FQS + j2 * QM + i]);
+#pragma unroll
+    for (int i = 0; i < QM; ++i)
+      if (i >= v.dof) Ml[i * (i + 1) / 2 + i] = 1.f;
+  }
+  // the FP64 right-hand side and the residual of the first solve against the
+  // (hi, lo) matrix, both read before any column of M^-1 overwrites M
+  double res[QM];
+  float x[QM];
+  bool ok = true;
+  if (act) {
+    const float* lo = v.dT + k * DTS;
+    double rhs[QM];
+#pragma unroll
+    for (int i = 0; i < QM; ++i)
+      rhs[i] = col == 7 ? ((double)v.U[k * US + i] + (double)v.Ulo[k * US + i]) -
+                              ((double)v.qdd[k * US + i] + (double)lo[56 + i])
+                        : (i == col ? 1.0 : 0.0);
+    ok = chol7(Ml);
+#pragma unroll
+    for (int i = 0; i < QM; ++i) x[i] = (float)rhs[i];
+    chol7_solve(Ml, x);
+#pragma unroll
+    for (int i = 0; i < QM; ++i) {
+      double r = rhs[i];
+#pragma unroll
+      for (int j2 = 0; j2 < QM; ++j2) {
+        double m;
+        if (i >= v.dof || j2 >= v.dof) {
+          m = (i == j2) ? 1.0 : 0.0;
+        } else {
+          m = 0.5 * (((double)v.Mi[k * FQS + i * QM + j2] + (double)lo[j2 * 8 + i]) +
+                     ((double)v.Mi[k * FQS + j2 * QM + i] + (double)lo[i * 8 + j2]));
+        }
+        r -= m * (double)x[j2];
+      }
+      res[i] = r;
+    }
+  }
+  __syncthreads();  // every M_k is read before a column of M_k^-1 overwrites it
+  if (act) {
+    float d[QM];
+#pragma unroll
+    for (int i = 0; i < QM; ++i) d[i] = (float)res[i];
+    chol7_solve(Ml, d);
+    if (col == 7) {
+      if (!ok) atomicOr(reinterpret_cast<int*>(v.scal + S_FLAGS), F_NONFINITE);
+      const float* xk = v.X + k * VS;
+      const float* xkl = v.Xlo + k * VS;
+      const float* xn = v.X + (k + 1) * VS;
+      const float* xnl = v.Xlo + (k + 1) * VS;
+#pragma unroll
+      for (int i = 0; i < QM; ++i) {
+        const double a = (double)x[i] + (double)d[i];
+        v.qdd[k * US + i] = (float)a;
+        // qd+ = qd + h qdd, q+ = q + h qd+ = q + h qd + h^2 qdd
+        const double dqd = ((double)xk[QM + i] - (double)xn[QM + i]) + ((double)xkl[QM + i] - (double)xnl[QM + i]);
+        const double dq = ((double)xk[i] - (double)xn[i]) + ((double)xkl[i] - (double)xnl[i]);
+        const double qdk = (double)xk[QM + i] + (double)xkl[QM + i];
+        v.cv[(k + 1) * VS + QM + i] = (float)(dqd + h * a);
+        v.cv[(k + 1) * VS + i] = (float)(dq + h * qdk + h * h * a);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < QM; ++i) v.Mi[k * FQS + i * QM + col] = (float)((double)x[i] + (double)d[i]);
+    }
+  }
+  if (it == 8 * nk && v.k0 == 0) {  // c_0 = x_s - x_0, by the CTA owning knot 0
+#pragma unroll
+    for (int i = 0; i < XM; ++i) v.cv[i] = (float)(((double)v.xs[i] - (double)v.X[i]) - (double)v.Xlo[i]);
+  }
+}
+
 // Cholesky of M, explicit M^-1, qdd = M^-1 (u - bias), dynamics defects.
 // One (knot, right-hand side) per thread: column c < 7 of M^-1 or, for c = 7,
 // qdd and the defects; every thread of a knot factors M_k itself (the same
 // bits), so the eight triangular solves run side by side.
 __device__ inline void st_forward_dynamics(const Ctx& C) {
   const int N = C.N;
+  if (C.hp) {
+    FdView v;
+    v.X = C.X;
+    v.Xlo = C.Xlo;
+    v.U = C.U;
+    v.Ulo = C.Ulo;
+    v.xs = C.xs;
+    v.Mi = C.Mi;
+    v.qdd = C.qdd;
+    v.dT = C.dT;
+    v.cv = C.cv;
+    v.scal = C.scal;
+    v.h = C.h;
+    v.N = N;
+    v.dof = C.dof;
+    v.k0 = C.k0;
+    v.k1 = C.k1;
+    st_forward_dynamics_hp(v);
+    return;
+  }
   const int ke = C.k1 < N ? C.k1 : N;
   const float h = C.h;
   const int nk = ke - C.k0;  // 8 * nk + 1 <= 8 * KPC_MAX + 1 < NTHR: one round
@@ -475,7 +689,7 @@ __device__ __forceinline__ void knot_cost(const Ctx& C, int k) {
 #pragma unroll
     for (int i = 0; i < XM; ++i) {
       const float wi = i < QM ? wq : wqd;
-      const float d = x[i] - xref_at(C, k, i);
+      const float d = C.hp ? (x[i] - xref_at(C, k, i)) + C.Xlo[k * VS + i] : x[i] - xref_at(C, k, i);
       J += 0.5f * s * wi * d * d;
       qg[i] = s * wi * d;
     }
@@ -508,8 +722,19 @@ __device__ __forceinline__ void knot_cost(const Ctx& C, int k) {
     for (int i = 0; i < QM; ++i) {
       const float v = x[QM + i];
       J += 0.5f * s * wqd * v * v;
-      qg[QM + i] = s * wqd * v;
+      qg[QM + i] = s * wqd * (C.hp ? v + C.Xlo[k * VS + QM + i] : v);
       Qi[49 + i] = 1.f / __fadd_rn(__fmul_rn(s, wqd), rho);
+    }
+    if (C.hp) {  // p(q + q_lo) = p(q) + J_p q_lo to first order: the gradient gains J_p^T J_p q_lo
+      const float* xl = C.Xlo + k * VS;
+      float dp[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int i = 0; i < QM; ++i) dp[r] += Jp[r * QM + i] * xl[i];
+#pragma unroll
+      for (int i = 0; i < QM; ++i)
+        qg[i] += s * wee * (Jp[i] * dp[0] + Jp[QM + i] * dp[1] + Jp[2 * QM + i] * dp[2]);
     }
     // the packed Q_qq, inverted column by column in the next phase
 #pragma unroll
@@ -520,7 +745,7 @@ __device__ __forceinline__ void knot_cost(const Ctx& C, int k) {
 #pragma unroll
     for (int i = 0; i < QM; ++i) {
       J += 0.5f * wr * u[i] * u[i];
-      C.rg[k * US + i] = wr * u[i];
+      C.rg[k * US + i] = wr * (C.hp ? u[i] + C.Ulo[k * US + i] : u[i]);
       C.Ri[k * US + i] = 1.f / wr;
     }
   }
@@ -703,18 +928,22 @@ __device__ inline void st_schur(const Ctx& C) {
   const bool act = (lane < 28) && (k < C.k1);
   const bool actL = (lane < 28) && (k <= C.k1) && (k <= N) && (k > 0);
   const int kk = k - 1;  // the dynamics knot feeding block row k
+  // Every entry is accumulated in double-float and rounded once: B R^-1 B^T
+  // reaches ~1e4 (R^-1 = 1e3, h |M^-1| ~ 4) while theta's entries along M's
+  // well-conditioned directions are O(1), so FP32 partial sums would leave
+  // ~eps_32 1e4 of cancellation error in them.
   if (act && k == 0) {
     const float* Qi = C.Qi;
     for (int t = 0; t < 2; ++t) {
       const int i = j + QM * t;
-      float acc = 0.f;
+      DF acc = df_zero();
       for (int c = 0; c < XM; ++c) {
         const float qv = Qinv_elem(Qi, i, c);
         bD(C, 0, i, c) = qv;
-        acc += qv * C.Dx[c];
+        acc = df_fma(acc, qv, C.Dx[c]);
         bL(C, 0, i, c) = 0.f;
       }
-      vec(C, V_RHS, 0)[i] = -C.cv[i] - acc;
+      vec(C, V_RHS, 0)[i] = df_val(df_add(DF{-acc.hi, -acc.lo}, -C.cv[i]));
     }
   }
   if (actL) {
@@ -730,9 +959,10 @@ __device__ inline void st_schur(const Ctx& C) {
       for (int c = 0; c < XM; ++c) {
         float a;
         if (c < QM) {
-          a = 0.f;
+          DF s = df_zero();
 #pragma unroll
-          for (int l = 0; l < QM; ++l) a += Arow[l] * Qi[l * QM + c];
+          for (int l = 0; l < QM; ++l) s = df_fma(s, Arow[l], Qi[l * QM + c]);
+          a = df_val(s);
         } else {
           a = Arow[c] * Qi[49 + c - QM];
         }
@@ -753,30 +983,45 @@ __device__ inline void st_schur(const Ctx& C) {
 #pragma unroll
       for (int l = 0; l < XM; ++l) Arow[l] = A_elem(Fq, Fv, h, i, l);
       const float si = t == 0 ? h * h : h;
-      float BRrow[QM];
+      // row i of B R^-1 = si M^-1[j, :] R^-1 as exact (hi, lo) pairs
+      float BRrow[QM], BRlo[QM];
 #pragma unroll
-      for (int m = 0; m < QM; ++m) BRrow[m] = si * Mi[j * QM + m] * Ri[m];
+      for (int m = 0; m < QM; ++m) {
+        const float p1 = __fmul_rn(si, Mi[j * QM + m]);
+        const float e1 = __fmaf_rn(si, Mi[j * QM + m], -p1);
+        BRrow[m] = __fmul_rn(p1, Ri[m]);
+        BRlo[m] = __fmaf_rn(p1, Ri[m], -BRrow[m]) + e1 * Ri[m];
+      }
       for (int c = 0; c < XM; ++c) {
         // theta = -A L^T + B R^-1 B^T + Q_{k}^-1   (A Q^-1 A^T = -A L^T)
-        float a = 0.f;
+        DF a = df_zero();
 #pragma unroll
-        for (int l = 0; l < XM; ++l) a -= Arow[l] * bL(C, k, c, l);
+        for (int l = 0; l < XM; ++l) a = df_fma(a, -Arow[l], bL(C, k, c, l));
         const int cm = c < QM ? c : c - QM;
         const float sc = c < QM ? h * h : h;
-        float bb = 0.f;
+        DF bb = df_zero();
 #pragma unroll
-        for (int m = 0; m < QM; ++m) bb += BRrow[m] * Mi[cm * QM + m];
-        bD(C, k, i, c) = a + sc * bb + Qinv_elem(Qi1, i, c);
+        for (int m = 0; m < QM; ++m) {
+          bb = df_fma(bb, BRrow[m], Mi[cm * QM + m]);
+          bb = df_add(bb, BRlo[m] * Mi[cm * QM + m]);
+        }
+        // sc * bb, exactly to double-float accuracy
+        const float ph = __fmul_rn(sc, bb.hi);
+        const DF sbb = DF{ph, __fmaf_rn(sc, bb.hi, -ph) + sc * bb.lo};
+        bD(C, k, i, c) = df_val(df_add(df_addd(a, sbb), Qinv_elem(Qi1, i, c)));
       }
       // zeta with d: L_k d_{k-1} - B R^-1 d_u,{k-1} + Q_k^-1 d_k
-      float z = 0.f;
+      DF z = df_zero();
 #pragma unroll
-      for (int l = 0; l < XM; ++l) z += bL(C, k, i, l) * C.Dx[kk * VS + l];
+      for (int l = 0; l < XM; ++l) z = df_fma(z, bL(C, k, i, l), C.Dx[kk * VS + l]);
 #pragma unroll
-      for (int m = 0; m < QM; ++m) z -= BRrow[m] * C.Du[kk * US + m];
+      for (int m = 0; m < QM; ++m) {
+        z = df_fma(z, -BRrow[m], C.Du[kk * US + m]);
+        z = df_add(z, -BRlo[m] * C.Du[kk * US + m]);
+      }
 #pragma unroll
-      for (int l = 0; l < XM; ++l) z += Qinv_elem(Qi1, i, l) * C.Dx[k * VS + l];
-      vec(C, V_RHS, k)[i] = -C.cv[k * VS + i] - z;
+      for (int l = 0; l < XM; ++l) z = df_fma(z, Qinv_elem(Qi1, i, l), C.Dx[k * VS + l]);
+      vec(C, V_RHS, k)[i] = df_val(df_add(DF{-z.hi, -z.lo}, -C.cv[k * VS + i]));
     }
   }
 }
@@ -1671,6 +1916,128 @@ __device__ __forceinline__ float trial_cost(const Ctx& C, int k, const float* x,
 }
 
 
+// High-precision trial merits: the trial point (X + Xlo) + alpha dX in FP64;
+// qdd from the FP32 factor refined once against an FP64 RNEA residual
+// u - ID(q, qd, qdd_0); defects and costs in FP64.  Each per-knot value is
+// stored as an (hi, lo) float pair (hi in `hi`, lo in `lo`, [na][K] each).
+struct LsView {
+  const DevModel* M;
+  const float *X, *Xlo, *U, *Ulo, *dX, *dU, *xs, *x_ref, *ee_ref;
+  float *hi, *lo;
+  float w[6];
+  float fx, fy, fz;
+  float h, mu, beta;
+  int N, dof, cost_kind, k0, k1, na;
+  bool base;
+};
+
+static __device__ __noinline__ void st_line_search_hp(LsView v) {
+  const int N = v.N, K = v.k1 - v.k0;
+  const DevModel& M = *v.M;
+  const int nx = 2 * v.dof;
+  for (int it = threadIdx.x; it < v.na * K; it += NTHR) {
+    const int a = it / K, k = v.k0 + it % K;
+    double alpha = 1.0;
+    for (int i = 0; i < a; ++i) alpha /= (double)v.beta;
+    if (v.base) alpha = 0.0;
+    auto xat = [&](int idx) {
+      return ((double)v.X[idx] + (double)v.Xlo[idx]) + alpha * (double)v.dX[idx];
+    };
+    auto uat = [&](int idx) {
+      return ((double)v.U[idx] + (double)v.Ulo[idx]) + alpha * (double)v.dU[idx];
+    };
+    const double s = (k == N) ? (double)v.w[3] : 1.0;
+    double x[XM];
+#pragma unroll
+    for (int i = 0; i < XM; ++i) x[i] = xat(k * VS + i);
+    double val = 0.0;
+    // stage cost
+    if (v.cost_kind == 0) {
+#pragma unroll
+      for (int i = 0; i < XM; ++i) {
+        const int ui = i < QM ? i : i - QM + v.dof;  // user layout of x_ref
+        const bool used = (i < QM ? i : i - QM) < v.dof;
+        const double wi = i < QM ? (double)v.w[0] : (double)v.w[1];
+        const double d = used ? x[i] - (double)v.x_ref[k * nx + ui] : 0.0;
+        val += 0.5 * s * wi * d * d;
+      }
+    } else {
+      double p[3];
+      fk_ee<double>(M, x, p, nullptr);
+      const float* pr = v.ee_ref + 3 * k;
+      const double d0 = p[0] - (double)pr[0], d1 = p[1] - (double)pr[1], d2 = p[2] - (double)pr[2];
+      val += 0.5 * s * (double)v.w[4] * (d0 * d0 + d1 * d1 + d2 * d2);
+#pragma unroll
+      for (int i = 0; i < QM; ++i) val += 0.5 * s * (double)v.w[1] * x[QM + i] * x[QM + i];
+    }
+    if (k < N) {
+      double u[QM];
+#pragma unroll
+      for (int i = 0; i < QM; ++i) {
+        u[i] = uat(k * US + i);
+        val += 0.5 * (double)v.w[2] * u[i] * u[i];
+      }
+      // FP32 forward dynamics at the rounded point, then one refinement step
+      // against the FP64 inverse dynamics at the exact trial point
+      float qf[QM], qdf[QM], sqf[QM], cqf[QM], Ml[28], z[QM], b[QM], qdd[QM];
+#pragma unroll
+      for (int i = 0; i < QM; ++i) {
+        qf[i] = (float)x[i];
+        qdf[i] = (float)x[QM + i];
+        sincosf(qf[i], &sqf[i], &cqf[i]);
+        z[i] = 0.f;
+      }
+      mass_matrix_crba(M, sqf, cqf, Ml);
+      const V3 fw = v3(v.fx, v.fy, v.fz);
+      rnea_value(M, sqf, cqf, qdf, z, M.g, fw, b, nullptr);
+#pragma unroll
+      for (int i = 0; i < QM; ++i) qdd[i] = (float)u[i] - b[i];
+      chol7(Ml);
+      chol7_solve(Ml, qdd);
+      double sq[QM], cq[QM], qd[QM], a0[QM], tau[QM];
+#pragma unroll
+      for (int i = 0; i < QM; ++i) {
+        sincos(x[i], &sq[i], &cq[i]);
+        qd[i] = x[QM + i];
+        a0[i] = (double)qdd[i];
+      }
+      // two refinement steps: each shrinks the error of qdd by ~kappa(M) eps_32
+      // (the FP32 CRBA factor is the preconditioner), from ~1e-5 to ~1e-12
+      // relative, below the merit decreases the line search must resolve
+#pragma unroll 1
+      for (int pass = 0; pass < 2; ++pass) {
+        rnea_value<double>(M, sq, cq, qd, a0, (double)M.g, v3t<double>(v.fx, v.fy, v.fz), tau, nullptr);
+        float r[QM];
+#pragma unroll
+        for (int i = 0; i < QM; ++i) r[i] = i < v.dof ? (float)(u[i] - tau[i]) : 0.f;
+        chol7_solve(Ml, r);
+#pragma unroll
+        for (int i = 0; i < QM; ++i) a0[i] += (double)r[i];
+      }
+      const double h = (double)v.h;
+      double c1 = 0.0;
+#pragma unroll
+      for (int i = 0; i < QM; ++i) {
+        if (i >= v.dof) continue;
+        const double acc = a0[i];
+        const double cqd = (x[QM + i] - xat((k + 1) * VS + QM + i)) + h * acc;
+        const double cq_ = (x[i] - xat((k + 1) * VS + i)) + h * x[QM + i] + h * h * acc;
+        c1 += fabs(cq_) + fabs(cqd);
+      }
+      val += (double)v.mu * c1;
+    }
+    if (k == 0) {
+      double c0 = 0.0;
+#pragma unroll
+      for (int i = 0; i < XM; ++i) c0 += fabs((double)v.xs[i] - x[i]);
+      val += (double)v.mu * c0;
+    }
+    const float vh = (float)val;
+    v.hi[a * K + (k - v.k0)] = vh;
+    v.lo[a * K + (k - v.k0)] = (float)(val - (double)vh);
+  }
+}
+
 // Merit (Eq. 3) of Z + alpha_i dZ for alpha_i = beta^-i (Eq. 7), i < n_alpha:
 // one thread per (alpha, own knot); per-alpha sums over the CTA's knots in a
 // fixed order, then over the cluster's CTAs in rank order.
@@ -1679,7 +2046,40 @@ __device__ inline void st_line_search(const Ctx& C, float mu, float beta, int n_
   const int N = C.N, K = C.k1 - C.k0;
   const int na = base ? 1 : n_alpha;
   float* contrib = vec(C, V_Y, C.k0);  // [na][K] (free during the line search)
-  for (int it = threadIdx.x; it < na * K; it += NTHR) {
+  float* contrib_lo = vec(C, V_Z, C.k0);  // low parts in the high-precision mode
+  if (C.hp) {
+    LsView v;
+    v.M = C.M;
+    v.X = C.X;
+    v.Xlo = C.Xlo;
+    v.U = C.U;
+    v.Ulo = C.Ulo;
+    v.dX = C.dX;
+    v.dU = C.dU;
+    v.xs = C.xs;
+    v.x_ref = C.x_ref;
+    v.ee_ref = C.ee_ref;
+    v.hi = contrib;
+    v.lo = contrib_lo;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) v.w[i] = C.w[i];
+    const V3 fw = ee_force(C);
+    v.fx = fw.x;
+    v.fy = fw.y;
+    v.fz = fw.z;
+    v.h = C.h;
+    v.mu = mu;
+    v.beta = beta;
+    v.N = N;
+    v.dof = C.dof;
+    v.cost_kind = C.cost_kind;
+    v.k0 = C.k0;
+    v.k1 = C.k1;
+    v.na = na;
+    v.base = base;
+    st_line_search_hp(v);
+  }
+  for (int it = threadIdx.x; it < (C.hp ? 0 : na * K); it += NTHR) {
     const int a = it / K, k = C.k0 + it % K;
     float alpha = 1.f;
     for (int i = 0; i < a; ++i) alpha /= beta;
@@ -1721,7 +2121,10 @@ __device__ inline void st_line_search(const Ctx& C, float mu, float beta, int n_
   float* slots = C.red + rbuf * RED_SLOTS * RED_W;  // [rank][alpha] pairs
   for (int a = warp; a < na; a += NWARP) {
     DF s = df_zero();
-    for (int kk = lane; kk < K; kk += 32) s = df_add(s, contrib[a * K + kk]);
+    for (int kk = lane; kk < K; kk += 32) {
+      s = df_add(s, contrib[a * K + kk]);
+      if (C.hp) s = df_add(s, contrib_lo[a * K + kk]);
+    }
     s = warp_df_sum(s);
     if (lane == 0) {
       const int o = (C.rank * MAX_ALPHA + a) * 2;
@@ -1775,8 +2178,23 @@ __device__ inline int st_accept(const Ctx& C, float beta, int n_alpha) {
     float alpha = 1.f;
     for (int i = 0; i < choice; ++i) alpha /= beta;
     const int ke = C.k1 < N ? C.k1 : N;
-    for (int i = threadIdx.x; i < (C.k1 - C.k0) * VS; i += NTHR) C.X[C.k0 * VS + i] += alpha * C.dX[C.k0 * VS + i];
-    for (int i = threadIdx.x; i < (ke - C.k0) * US; i += NTHR) C.U[C.k0 * US + i] += alpha * C.dU[C.k0 * US + i];
+    if (C.hp) {  // the double-float iterate: (hi, lo) <- hi + lo + alpha d, rounded to a pair
+      for (int i = threadIdx.x; i < (C.k1 - C.k0) * VS; i += NTHR) {
+        const int o = C.k0 * VS + i;
+        const double v = ((double)C.X[o] + (double)C.Xlo[o]) + (double)alpha * (double)C.dX[o];
+        C.X[o] = (float)v;
+        C.Xlo[o] = (float)(v - (double)C.X[o]);
+      }
+      for (int i = threadIdx.x; i < (ke - C.k0) * US; i += NTHR) {
+        const int o = C.k0 * US + i;
+        const double v = ((double)C.U[o] + (double)C.Ulo[o]) + (double)alpha * (double)C.dU[o];
+        C.U[o] = (float)v;
+        C.Ulo[o] = (float)(v - (double)C.U[o]);
+      }
+    } else {
+      for (int i = threadIdx.x; i < (C.k1 - C.k0) * VS; i += NTHR) C.X[C.k0 * VS + i] += alpha * C.dX[C.k0 * VS + i];
+      for (int i = threadIdx.x; i < (ke - C.k0) * US; i += NTHR) C.U[C.k0 * US + i] += alpha * C.dU[C.k0 * US + i];
+    }
   }
   csync(C);  // every thread (and CTA) has read the old base merit
   if (choice >= 0 && threadIdx.x == 0) {

@@ -24,7 +24,7 @@ constexpr int kMaxModels = 8;
 constexpr int kMaxDevices = 64;
 // Floats of one solve's workspace at N = 64 (Schur blocks in shared memory);
 // checked against ws_layout() at set-up.
-constexpr size_t kWsStride = 40960;
+constexpr size_t kWsStride = 43008;
 
 static __device__ __align__(256) float g_scratch[kMaxSolves * kWsStride];
 static __device__ __align__(256) ProbDesc g_probs[kMaxSolves];
@@ -69,45 +69,25 @@ gato_status setup_device(DevicePtrs** out) {
   return GATO_OK;
 }
 
-bool model_ok(const gato_model_desc& d, DevModel& m) {
-  if (d.dof < 1 || d.dof > QM || !(d.gravity >= 0.f) || !std::isfinite(d.gravity)) return false;
-  std::memset(&m, 0, sizeof(m));
-  m.dof = d.dof;
-  m.g = d.gravity;
-  for (int i = 0; i < QM; ++i) {
-    if (i >= d.dof) {
-      m.axis[i] = 2;  // massless padding joint at the end effector
-      continue;
-    }
-    if (d.axis[i] < 0 || d.axis[i] > 2 || !(d.link_len[i] >= 0.f) || !std::isfinite(d.link_len[i]) ||
-        !(d.mass[i] > 0.f) || !std::isfinite(d.mass[i]))
-      return false;
-    m.axis[i] = d.axis[i];
-    m.L[i] = d.link_len[i];
-    m.m[i] = d.mass[i];
-    for (int a = 0; a < 3; ++a) {
-      const float c = d.com[3 * i + a], I = d.inertia[3 * i + a];
-      if (!std::isfinite(c) || !(I >= 0.f) || !std::isfinite(I)) return false;
-      m.com[3 * i + a] = c;
-      m.Ic[3 * i + a] = I;
-    }
-  }
-  return true;
-}
+// The call's descriptors, passed to a one-block kernel by value (kernel
+// parameters travel with the launch itself), which stores them into the
+// file-scope arrays ahead of the solve on the same stream: no host-to-device
+// copy from pageable memory.
+struct NoallocDescs {
+  DevModel models[kMaxModels];
+  ProbDesc probs[kMaxSolves];
+  int order[kMaxSolves];
+  int n_models, n;
+};
+static_assert(sizeof(NoallocDescs) <= 4096, "descriptors must fit the classic kernel-parameter limit");
 
-bool problem_ok(const gato_problem& p, int n_models) {
-  if (p.mem != GATO_MEM_DEVICE) return false;
-  if (p.model < 0 || p.model >= n_models || p.N < 1 || p.N > kMaxHorizon) return false;
-  if (!(p.dt > 0.f) || !std::isfinite(p.dt) || !p.x_s || !p.X || !p.U) return false;
-  for (int i = 0; i < 6; ++i)
-    if (!std::isfinite(p.w[i]) || p.w[i] < 0.f) return false;
-  for (int i = 0; i < 3; ++i)
-    if (!std::isfinite(p.f_ext[i])) return false;
-  const float wq = p.w[0], wqd = p.w[1], wr = p.w[2], ts = p.w[3], rho = p.w[5];
-  if (!(wr > 0.f) || !(ts > 0.f)) return false;
-  if (p.cost_kind == GATO_COST_JOINT) return p.x_ref && wq + rho > 0.f && wqd + rho > 0.f;
-  if (p.cost_kind == GATO_COST_EE) return p.ee_ref && rho > 0.f && wqd + rho > 0.f;
-  return false;
+__global__ void noalloc_store_descs(const NoallocDescs d) {
+  const int t = threadIdx.x;
+  if (t < d.n_models) g_models[t] = d.models[t];
+  if (t < d.n) {
+    g_probs[t] = d.probs[t];
+    g_order[t] = d.order[t];
+  }
 }
 
 }  // namespace
@@ -121,26 +101,21 @@ extern "C" gato_status gato_solve_noalloc(const gato_model_desc* models, int32_t
   if (n < 1 || n > kMaxSolves || n_models < 1 || n_models > kMaxModels || max_sqp_iters < 1)
     return GATO_E_INVALID;
   const gato_solver_params& sp = *params;
-  if (!(sp.mu >= 0.f) || !std::isfinite(sp.mu) || !(sp.beta > 1.f) || !std::isfinite(sp.beta) ||
-      sp.n_alpha < 1 || sp.n_alpha > MAX_ALPHA || !(sp.pcg_eps > 0.f) || sp.pcg_max_iter < 1 ||
-      (sp.precond != GATO_PRECOND_STAIR && sp.precond != GATO_PRECOND_JACOBI) ||
-      (sp.linsolve != GATO_LINSOLVE_PCG && sp.linsolve != GATO_LINSOLVE_DIRECT) ||
-      (sp.rho_adapt != 0 && sp.rho_adapt != 1) ||
-      !std::isfinite(sp.kkt_tol))
-    return GATO_E_INVALID;
-  DevModel dm[kMaxModels];
+  if (check_params(sp)) return GATO_E_INVALID;
+  NoallocDescs D;
+  std::memset(&D, 0, sizeof(D));
+  D.n_models = n_models;
+  D.n = n;
   int dofs[kMaxModels];
   for (int i = 0; i < n_models; ++i) {
-    if (!model_ok(models[i], dm[i])) return GATO_E_INVALID;
+    if (check_model(models[i], D.models[i])) return GATO_E_INVALID;
     dofs[i] = models[i].dof;
   }
-  ProbDesc pd[kMaxSolves];
-  int order[kMaxSolves];
   int Ns[kMaxSolves];
   for (int i = 0; i < n; ++i) {
     const gato_problem& p = problems[i];
-    if (!problem_ok(p, n_models)) return GATO_E_INVALID;
-    ProbDesc& d = pd[i];
+    if (p.mem != GATO_MEM_DEVICE || check_problem(p, n_models, kMaxHorizon)) return GATO_E_INVALID;
+    ProbDesc& d = D.probs[i];
     std::memset(&d, 0, sizeof(d));
     d.model = p.model;
     d.N = p.N;
@@ -158,18 +133,13 @@ extern "C" gato_status gato_solve_noalloc(const gato_model_desc* models, int32_t
     Ns[i] = p.N;
   }
   // grouped by cluster size, longest horizon first within a group
-  order_solves(Ns, n, order, LaunchPlan());
+  order_solves(Ns, n, D.order, LaunchPlan());
   DevicePtrs* P = nullptr;
   gato_status s = setup_device(&P);
   if (s != GATO_OK) return s;
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
-  // pageable sources: each copy has consumed its host buffer when it returns
-  if (cudaMemcpyAsync(P->models, dm, n_models * sizeof(DevModel), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
-      cudaMemcpyAsync(P->probs, pd, n * sizeof(ProbDesc), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
-      cudaMemcpyAsync(P->order, order, n * sizeof(int), cudaMemcpyHostToDevice, stream) != cudaSuccess) {
-    cudaGetLastError();
-    return GATO_E_CUDA;
-  }
+  noalloc_store_descs<<<1, 32, 0, stream>>>(D);
+  if (cudaGetLastError() != cudaSuccess) return GATO_E_CUDA;
   FusedLaunch a;
   a.probs = P->probs;
   a.models = P->models;
@@ -192,9 +162,10 @@ extern "C" gato_status gato_solve_noalloc(const gato_model_desc* models, int32_t
   a.prm.max_iter = max_sqp_iters;
   a.prm.linsolve = sp.linsolve;
   a.prm.rho_adapt = sp.rho_adapt;
+  a.prm.escalate = sp.precision == GATO_PRECISION_ESCALATE;
   a.timing = nullptr;
   a.variant = 0;
-  if (launch_fused_grouped(a, order, P->order, Ns, n, stream, LaunchPlan()) != cudaSuccess) {
+  if (launch_fused_grouped(a, D.order, P->order, Ns, n, stream, LaunchPlan()) != cudaSuccess) {
     cudaGetLastError();
     return GATO_E_CUDA;
   }

@@ -24,6 +24,7 @@ SOLVE_CONVERGED, SOLVE_MAXITER, SOLVE_LSFAIL, SOLVE_PCG_MAXIT, SOLVE_NONFINITE =
 COST_JOINT, COST_EE = 0, 1
 PRECOND_STAIR, PRECOND_JACOBI = 0, 1
 LINSOLVE_PCG, LINSOLVE_DIRECT = 0, 1
+PRECISION_FP32, PRECISION_ESCALATE = 0, 1
 MEM_HOST, MEM_DEVICE = 0, 1
 
 EXPORTED = (
@@ -35,6 +36,7 @@ EXPORTED = (
     "gato_server_open", "gato_server_submit", "gato_server_poll", "gato_server_read",
     "gato_server_close", "gato_server_get_stats", "gato_server_last_error", "gato_server_destroy",
     "gato_server_drive", "gato_query_launch", "gato_plant_rk4", "gato_plant_ee",
+    "gato_debug_iteration_log",
 )
 LAYOUT_NAMES = ("X", "U", "dX", "dU", "Fq", "Fv", "Minv", "qdd", "dTau", "Qinv", "Rinv", "q", "r",
                 "c", "Jk", "Linv", "links", "D", "L", "P", "vec", "scal", "Dx", "Du", "nu")
@@ -49,7 +51,8 @@ class ModelDesc(C.Structure):
 class SolverParams(C.Structure):
     _fields_ = [("mu", C.c_float), ("beta", C.c_float), ("n_alpha", C.c_int32),
                 ("pcg_eps", C.c_float), ("pcg_max_iter", C.c_int32), ("precond", C.c_int32),
-                ("kkt_tol", C.c_float), ("linsolve", C.c_int32), ("rho_adapt", C.c_int32)]
+                ("kkt_tol", C.c_float), ("linsolve", C.c_int32), ("rho_adapt", C.c_int32),
+                ("precision", C.c_int32)]
 
 
 class BatchDesc(C.Structure):
@@ -144,6 +147,8 @@ def load() -> C.CDLL:
     L.gato_solve_noalloc.restype = C.c_int
     L.gato_debug_stage_cycles.argtypes = [bp, C.c_int32, C.c_void_p, C.c_int32]
     L.gato_debug_stage_cycles.restype = C.c_int
+    L.gato_debug_iteration_log.argtypes = [bp, C.c_int32, C.c_int32, C.c_void_p, C.c_int32]
+    L.gato_debug_iteration_log.restype = C.c_int
     L.gato_set_launch_config.argtypes = [bp, C.POINTER(LaunchConfig)]
     L.gato_set_launch_config.restype = C.c_int
     L.gato_query_launch.argtypes = [C.c_int32, C.c_int32, C.POINTER(LaunchConfig), C.POINTER(LaunchInfo)]
@@ -292,6 +297,21 @@ def gato_debug_stage_cycles(handle, enable, n=0):
                                        out.ctypes.data if (not enable and n) else None, n)
     _check(handle, s, "gato_debug_stage_cycles")
     return None if enable else out[:n]
+
+
+def gato_debug_iteration_log(handle, enable, max_iters, n=0):
+    """enable=1: start logging max_iters iterations per solve; enable=0: return
+    a dict of (n, max_iters) arrays (alpha index, PCG iterations, KKT residual,
+    high-precision flag) and stop."""
+    out = np.zeros((max(n, 1), max_iters, 4), np.int32)
+    s = load().gato_debug_iteration_log(C.c_void_p(handle), enable, max_iters,
+                                        out.ctypes.data if (not enable and n) else None, n)
+    _check(handle, s, "gato_debug_iteration_log")
+    if enable:
+        return None
+    out = out[:n]
+    return {"alpha_idx": out[:, :, 0].copy(), "pcg_iters": out[:, :, 1].copy(),
+            "kkt": out[:, :, 2].copy().view(np.float32), "hp": out[:, :, 3].copy()}
 
 
 def gato_solve_noalloc(models, n_models, params, problems, n, iters, results_dev_ptr, stream=0):

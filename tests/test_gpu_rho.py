@@ -53,14 +53,17 @@ def test_rho_adapt_fused_and_plain_agree(G):
 
 @pytest.mark.parametrize("seed,rho0", [(1, 0.1), (3, 1e-3)])
 def test_rho_adapt_replays_the_rule(G, oracle, seed, rho0):
+    # FP32 throughout (no precision escalation): a call that escalated would
+    # stay in the high-precision mode for its later iterations, which the
+    # single-iteration replay, starting every call in FP32, would not
     p = with_rho(I.ee_problem(seed, I.arm7(), 16, 0.05), rho0)
     iters = 8
-    full = gpu_solve(G, [p], iters, rho_adapt=1)[0]
+    full = gpu_solve(G, [p], iters, rho_adapt=1, precision=0)[0]
     X, U, lam = (a.astype(np.float32) for a in oracle.cold_start(p))
     rho = np.float32(rho0)
     outcomes = []
     for _ in range(iters):
-        g = gpu_solve(G, [with_rho(p, rho)], 1, X=[X], U=[U], lam=[lam])[0]
+        g = gpu_solve(G, [with_rho(p, rho)], 1, X=[X], U=[U], lam=[lam], precision=0)[0]
         accepted = not (g["flags"] & 4)
         outcomes.append(accepted)
         X, U, lam = (g[k].astype(np.float32) for k in ("X", "U", "lam"))
