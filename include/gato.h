@@ -102,16 +102,18 @@ typedef struct {
                               [1e-8, 1e1]; it starts from w[5] at every call.
                               0 (default): rho fixed */
   int32_t precision;       /* GATO_PRECISION_ESCALATE (default): the bulk runs in FP32;
-                              a solve whose FP32 line search finds no merit decrease
-                              (near a solution, where FP32 rounding of the dynamics
-                              and of the iterate exceeds the decrease) repeats that
-                              SQP iteration in a high-precision mode and stays in it
-                              for the rest of the call: FP64 mass matrix and bias,
-                              each dynamics solve refined once in FP64, the iterate
-                              kept as double-float pairs, trial merits in FP64.  The
-                              repeated iteration counts once.
-                              GATO_PRECISION_FP32: never escalate (the step is then
-                              rejected with GATO_SOLVE_LSFAIL) */
+                              when a KKT tolerance is set (kkt_tol > 0), a solve whose
+                              FP32 line search finds no merit decrease (near a
+                              solution, where FP32 rounding of the dynamics and of the
+                              iterate exceeds the decrease), or whose FP32 KKT test
+                              passes, repeats that SQP iteration in a high-precision
+                              mode and stays in it for the rest of the call: FP64 mass
+                              matrix and bias, each dynamics solve refined in FP64, the
+                              iterate kept as double-float pairs, trial merits in FP64.
+                              The repeated iteration counts once.  Without a tolerance
+                              (fixed iteration counts, real-time ticks) nothing
+                              escalates.  GATO_PRECISION_FP32: never escalate (the step
+                              is then rejected with GATO_SOLVE_LSFAIL) */
 } gato_solver_params;
 
 typedef struct {

@@ -104,6 +104,8 @@ def lib():
         L.ora_solve.restype = C.c_int32
         L.ora_blocktri_solve.argtypes = [C.c_int32, C.c_int32, dp, dp, dp, dp]
         L.ora_blocktri_solve.restype = C.c_int32
+        L.ora_count_flops.argtypes = [mp, C.c_int32]
+        L.ora_count_flops.restype = C.c_int64
         _lib = L
     return _lib
 
@@ -348,3 +350,15 @@ def solve(prob, max_iter=10, X=None, U=None, lam=None, replay=None, **kw):
                 kkt=res.kkt, merit=res.merit, alpha_idx=la[:k].copy(), pcg_iters=lp[:k].copy(),
                 merit_before=m0[:k].copy(), merit_after=m1[:k].copy(), kkt_log=kk[:k].copy(),
                 merit_gap=gap[:k].copy())
+
+
+FLOP_PRIMITIVES = ("rnea", "rnea_tangent_and_value", "cholesky_solve", "fk", "fk_and_tangent",
+                   "block_product_14", "blocktri_row_14", "forward_dynamics")
+
+
+def count_flops(model):
+    """Operation counts (FMA = 2) of the method's primitive computations for
+    `model`, from the oracle's formulas run on a FLOP-counting scalar: a dict
+    keyed by FLOP_PRIMITIVES (see ora_count_flops in gato_oracle.cpp)."""
+    m = make_model(model)
+    return {name: int(lib().ora_count_flops(C.byref(m), i)) for i, name in enumerate(FLOP_PRIMITIVES)}

@@ -107,26 +107,63 @@ namespace {
 
 /* ----------------------------------------------------------------- scalars */
 
-struct Dual {
-  double v, d;
-  Dual() : v(0), d(0) {}
-  Dual(double x) : v(x), d(0) {}
-  Dual(double x, double dx) : v(x), d(dx) {}
+/* FLOP-counting scalar: a double whose arithmetic adds to a per-thread
+   counter, 1 per +, -, *, / and 1 per sin, cos or sqrt (a multiply-add counts
+   2).  Running the templated code below on it counts the operations of the
+   formulas as written (ora_count_flops). */
+thread_local long long g_flops = 0;
+struct Cnt {
+  double v;
+  Cnt() : v(0) {}
+  Cnt(double x) : v(x) {}
 };
-inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
-inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
-inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
-inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
-inline Dual operator/(Dual a, Dual b) {
-  return Dual(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v));
+inline Cnt operator+(Cnt a, Cnt b) { ++g_flops; return Cnt(a.v + b.v); }
+inline Cnt operator-(Cnt a, Cnt b) { ++g_flops; return Cnt(a.v - b.v); }
+inline Cnt operator-(Cnt a) { return Cnt(-a.v); }
+inline Cnt operator*(Cnt a, Cnt b) { ++g_flops; return Cnt(a.v * b.v); }
+inline Cnt operator/(Cnt a, Cnt b) { ++g_flops; return Cnt(a.v / b.v); }
+inline Cnt& operator+=(Cnt& a, Cnt b) { a = a + b; return a; }
+inline Cnt& operator-=(Cnt& a, Cnt b) { a = a - b; return a; }
+inline Cnt sin(Cnt a) { ++g_flops; return Cnt(std::sin(a.v)); }
+inline Cnt cos(Cnt a) { ++g_flops; return Cnt(std::cos(a.v)); }
+inline Cnt sqrt(Cnt a) { ++g_flops; return Cnt(std::sqrt(a.v)); }
+
+/* Forward-mode dual numbers over a scalar S (double for the oracle's
+   derivatives, Cnt for counting them). */
+template <class S> struct DualT {
+  S v, d;
+  DualT() : v(0.0), d(0.0) {}
+  DualT(double x) : v(x), d(0.0) {}
+  DualT(S x, S dx) : v(x), d(dx) {}
+};
+template <class S> inline DualT<S> operator+(DualT<S> a, DualT<S> b) { return DualT<S>(a.v + b.v, a.d + b.d); }
+template <class S> inline DualT<S> operator-(DualT<S> a, DualT<S> b) { return DualT<S>(a.v - b.v, a.d - b.d); }
+template <class S> inline DualT<S> operator-(DualT<S> a) { return DualT<S>(-a.v, -a.d); }
+template <class S> inline DualT<S> operator*(DualT<S> a, DualT<S> b) {
+  return DualT<S>(a.v * b.v, a.d * b.v + a.v * b.d);
 }
-inline Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
-inline Dual& operator-=(Dual& a, Dual b) { a = a - b; return a; }
-inline Dual sin(Dual a) { return Dual(std::sin(a.v), std::cos(a.v) * a.d); }
-inline Dual cos(Dual a) { return Dual(std::cos(a.v), -std::sin(a.v) * a.d); }
-inline Dual sqrt(Dual a) { double s = std::sqrt(a.v); return Dual(s, a.d / (2.0 * s)); }
+template <class S> inline DualT<S> operator/(DualT<S> a, DualT<S> b) {
+  return DualT<S>(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v));
+}
+template <class S> inline DualT<S>& operator+=(DualT<S>& a, DualT<S> b) { a = a + b; return a; }
+template <class S> inline DualT<S>& operator-=(DualT<S>& a, DualT<S> b) { a = a - b; return a; }
+template <class S> inline DualT<S> sin(DualT<S> a) {
+  using std::sin; using std::cos;
+  return DualT<S>(sin(a.v), cos(a.v) * a.d);
+}
+template <class S> inline DualT<S> cos(DualT<S> a) {
+  using std::sin; using std::cos;
+  return DualT<S>(cos(a.v), -sin(a.v) * a.d);
+}
+template <class S> inline DualT<S> sqrt(DualT<S> a) {
+  using std::sqrt;
+  S r = sqrt(a.v);
+  return DualT<S>(r, a.d / (S(2.0) * r));
+}
+typedef DualT<double> Dual;
 inline double val(double a) { return a; }
-inline double val(Dual a) { return a.v; }
+inline double val(Cnt a) { return a.v; }
+template <class S> inline double val(DualT<S> a) { return val(a.v); }
 
 /* --------------------------------------------------- spatial algebra (6D) */
 /* Motion vectors are [angular; linear], forces [moment; force]. */
@@ -446,11 +483,12 @@ void fk_jacobian(const ora_model& m, const double* q, double* p, double* J) {
 
 typedef std::vector<double> Vec;
 
-void matmul(int n, int k, int mm, const double* A, const double* B, double* C) {
+template <class T>
+void matmul(int n, int k, int mm, const T* A, const T* B, T* C) {
   /* C (n x mm) = A (n x k) B (k x mm) */
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < mm; ++j) {
-      double s = 0.0;
+      T s = T(0.0);
       for (int l = 0; l < k; ++l) s += A[i * k + l] * B[l * mm + j];
       C[i * mm + j] = s;
     }
@@ -657,12 +695,13 @@ Schur form_schur(const Lin& L, int precond) {
   return S;
 }
 
-void blocktri_mv(int N, int nx, const double* D, const double* Lw, const double* x, double* y) {
+template <class T>
+void blocktri_mv(int N, int nx, const T* D, const T* Lw, const T* x, T* y) {
   /* y = T x for a symmetric block-tridiagonal T with diagonal D and sub-diagonal Lw. */
   size_t bb = (size_t)nx * nx;
   for (int k = 0; k <= N; ++k)
     for (int i = 0; i < nx; ++i) {
-      double s = 0.0;
+      T s = T(0.0);
       for (int j = 0; j < nx; ++j) s += D[k * bb + i * nx + j] * x[(size_t)k * nx + j];
       if (k > 0)
         for (int j = 0; j < nx; ++j) s += Lw[(k - 1) * bb + i * nx + j] * x[(size_t)(k - 1) * nx + j];
@@ -969,6 +1008,92 @@ int32_t ora_solve(const ora_model* m, const ora_problem* p, const ora_params* pr
   }
   if (res) *res = R;
   return 0;
+}
+
+/* Operation counts of the method's primitive computations, from the
+   templated code above run on the counting scalar Cnt (FMA = 2), for the
+   model m at a generic state (nonzero q, qd, qdd; gravity on):
+     0  inverse dynamics, one RNEA pass (Sec. II-A's dynamics f; the same code
+        gives one column of M with a unit acceleration)
+     1  an RNEA pass carrying one forward-mode directional derivative
+        (value + tangent; the tangent alone is 1 minus 0)
+     2  Cholesky factor and one solve of a dof x dof SPD system
+     3  end-effector position (forward kinematics)
+     4  end-effector position carrying one directional derivative
+     5  product of two 14 x 14 blocks (also the cost of a Gauss-Jordan
+        inverse of a 14 x 14 block: n^3 multiply-adds)
+     6  one block row (14 rows) of a block-tridiagonal matrix-vector product
+     7  forward dynamics as the oracle writes it: M by dof RNEA columns, the
+        bias pass and a Cholesky solve
+   Returns -1 for an unknown `what`. */
+int64_t ora_count_flops(const ora_model* m, int32_t what) {
+  const int n = m->dof;
+  std::vector<Cnt> q(n), qd(n), qdd(n), tau(n);
+  for (int i = 0; i < n; ++i) {
+    q[i] = Cnt(0.3 + 0.1 * i);
+    qd[i] = Cnt(0.2 - 0.05 * i);
+    qdd[i] = Cnt(1.0 + 0.5 * i);
+  }
+  g_flops = 0;
+  switch (what) {
+    case 0:
+      rnea(*m, q.data(), qd.data(), qdd.data(), true, tau.data());
+      break;
+    case 1: {
+      typedef DualT<Cnt> DC;
+      std::vector<DC> a(n), b(n), c(n), t(n);
+      for (int i = 0; i < n; ++i) {
+        a[i] = DC(q[i], Cnt(i == 0 ? 1.0 : 0.0));
+        b[i] = DC(qd[i], Cnt(0.0));
+        c[i] = DC(qdd[i], Cnt(0.0));
+      }
+      g_flops = 0;
+      rnea(*m, a.data(), b.data(), c.data(), true, t.data());
+      break;
+    }
+    case 2: {
+      std::vector<Cnt> A((size_t)n * n);
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) A[(size_t)i * n + j] = Cnt(i == j ? 4.0 : 0.5);
+      g_flops = 0;
+      cholesky_solve(n, A, qdd.data());
+      break;
+    }
+    case 3: {
+      Cnt p[3];
+      fk_ee(*m, q.data(), p);
+      break;
+    }
+    case 4: {
+      typedef DualT<Cnt> DC;
+      std::vector<DC> a(n);
+      for (int i = 0; i < n; ++i) a[i] = DC(q[i], Cnt(i == 0 ? 1.0 : 0.0));
+      DC p[3];
+      g_flops = 0;
+      fk_ee(*m, a.data(), p);
+      break;
+    }
+    case 5: {
+      std::vector<Cnt> A(196, Cnt(0.5)), B(196, Cnt(0.25)), C(196);
+      g_flops = 0;
+      matmul(14, 14, 14, A.data(), B.data(), C.data());
+      break;
+    }
+    case 6: {
+      const int N = 3;  /* four block rows; the count is per block row */
+      std::vector<Cnt> D((N + 1) * 196, Cnt(0.5)), L(N * 196, Cnt(0.25)), x((N + 1) * 14, Cnt(1.0)),
+          y((N + 1) * 14);
+      g_flops = 0;
+      blocktri_mv(N, 14, D.data(), L.data(), x.data(), y.data());
+      return (int64_t)(g_flops / (N + 1));
+    }
+    case 7:
+      forward_dynamics(*m, q.data(), qd.data(), qdd.data(), tau.data());
+      break;
+    default:
+      return -1;
+  }
+  return (int64_t)g_flops;
 }
 
 /* Direct solve of the block-tridiagonal SPD system (block Cholesky), for checks. */

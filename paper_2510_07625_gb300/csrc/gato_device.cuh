@@ -59,8 +59,9 @@ struct Params {
   int max_iter;
   int linsolve;  // 0 PCG, 1 direct block elimination
   int rho_adapt; // 1: rho / 3 after an accepted step, * 2 after a rejected one
-  int escalate;  // 1: a solve whose FP32 line search finds no decrease repeats the
-                 // iteration in the high-precision mode and stays in it
+  int escalate;  // 1: with kkt_tol > 0, a solve whose FP32 line search finds no
+                 // decrease, or whose FP32 KKT test passes, repeats the iteration
+                 // in the high-precision mode and stays in it
 };
 
 struct Result {

@@ -232,7 +232,7 @@ cudaError_t launch_plain(const ProbDesc* probs, const DevModel* models, Result* 
       if ((e = go(st)) != cudaSuccess) return e;
       if (stop_stage == st) return cudaSuccess;
     }
-    if (prm.escalate) {
+    if (prm.escalate && prm.kkt_tol > 0.f) {
       // the pass that repeats the iteration in the high-precision mode when its
       // FP32 line search found no decrease (each launch returns at once otherwise)
       a.redo = 1;

@@ -156,7 +156,7 @@ __device__ void sqp_solve(Ctx& C, const ProbDesc& P, const Params& prm, int iter
     tstamp(C, T_LS, tl);
     const int choice = st_accept(C, prm.beta, prm.n_alpha);
     csync(C);
-    if (choice < 0 && prm.escalate && !C.hp) {
+    if (choice < 0 && prm.escalate && prm.kkt_tol > 0.f && !C.hp) {
       // the FP32 line search found no decrease: repeat this iteration in the
       // high-precision mode (every thread takes the same branch)
       C.hp = 1;
@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(NTHR, 1) sqp_plain_stage(int stage, PlainArgs 
     case PS_LS: st_line_search(C, prm.mu, prm.beta, prm.n_alpha, rbuf); break;
     case PS_ACCEPT: {
       const int choice = st_accept(C, prm.beta, prm.n_alpha);
-      if (choice < 0 && prm.escalate && !C.hp) {
+      if (choice < 0 && prm.escalate && prm.kkt_tol > 0.f && !C.hp) {
         // repeat this iteration in the high-precision mode (the next pass)
         if (lead) {
           C.scal[S_HP] = 1.f;

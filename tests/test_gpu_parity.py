@@ -112,9 +112,9 @@ def test_fused_equals_plain_bitwise_through_escalation(G):
     """Both forms escalate to the high-precision mode at the same iteration
     (their FP32 line searches are the same code) and agree bit for bit after."""
     p = I.joint_problem(3, I.arm7(), N=12)
-    a = gpu_solve(G, [p], 30, log=True)[0]
+    a = gpu_solve(G, [p], 30, log=True, kkt_tol=1e-9)[0]
     assert a["hp"].any(), "the solve did not reach its FP32 floor within 30 iterations"
-    b = gpu_solve(G, [p], 30, plain=True)[0]
+    b = gpu_solve(G, [p], 30, plain=True, kkt_tol=1e-9)[0]
     np.testing.assert_array_equal(a["X"], b["X"])
     np.testing.assert_array_equal(a["U"], b["U"])
     assert (a["flags"], a["sqp_iters"], a["pcg_iters"]) == (b["flags"], b["sqp_iters"], b["pcg_iters"])
@@ -315,13 +315,13 @@ def test_fixed_count_headline(G, pool):
 
 def _converged_parity(G, pool, probs, iters, **kw):
     """Both sides solved to convergence: the GPU until its KKT residual is
-    below the bar (its converged flag at 9e-6, confirmed in the
+    below half the bar (its converged flag at 5e-6, confirmed in the
     high-precision mode), the oracle to 1e-9.  X, U and the multiplier within
     1e-4; the KKT residual of the GPU's final iterate, evaluated by the oracle
     (kkt_at), within 1e-5 of the oracle's own (and so below 1e-5)."""
     import oracle
 
-    gs = gpu_solve(G, probs, iters, kkt_tol=9e-6, **kw)
+    gs = gpu_solve(G, probs, iters, kkt_tol=5e-6, **kw)
     ora = pool.map(oracle_jobs.solve, [(p, dict(max_iter=iters + 60, kkt_tol=1e-9, **kw)) for p in probs])
     worst = 0.0
     for p, g, o in zip(probs, gs, ora):
