@@ -609,7 +609,7 @@ def error_workloads(I):
 
 def error_runs(gato, I):
     """Every error workload on the GPU: the fixed-count solve with its
-    per-iteration line-search log, and the converged solve (KKT 5e-6, at most
+    per-iteration line-search log, and the converged solve (KKT 1e-5, at most
     100 iterations).  Host problems, cold start."""
     out = []
     for name, probs, iters, kw in error_workloads(I):
@@ -618,7 +618,7 @@ def error_runs(gato, I):
             if p.model not in models:
                 models.append(p.model)
         runs = {}
-        for key, it, extra in (("fixed", iters, kw), ("converged", 100, {"kkt_tol": 5e-6})):
+        for key, it, extra in (("fixed", iters, kw), ("converged", 100, {"kkt_tol": 1e-5})):
             B = gato.Batch(models, len(probs), max(p.N for p in probs), **extra)
             hp = gato.HostProblems(B, probs)
             gato.gato_debug_iteration_log(B.handle, 1, it)

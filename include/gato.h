@@ -61,7 +61,7 @@ enum { GATO_PRECOND_STAIR = 0, GATO_PRECOND_JACOBI = 1 };
 enum { GATO_LINSOLVE_PCG = 0, GATO_LINSOLVE_DIRECT = 1 };
 enum { GATO_MEM_HOST = 0, GATO_MEM_DEVICE = 1 };
 /* Arithmetic of a solve (gato_solver_params.precision). */
-enum { GATO_PRECISION_FP32 = 0, GATO_PRECISION_ESCALATE = 1 };
+enum { GATO_PRECISION_FP32 = 0, GATO_PRECISION_ESCALATE = 1, GATO_PRECISION_HIGH = 2 };
 
 /* Serial revolute chain (Sec. II-A "discrete-time dynamical system"; the
  * paper's robots are modelled the same way by its dynamics library).  Joint i
@@ -113,7 +113,9 @@ typedef struct {
                               The repeated iteration counts once.  Without a tolerance
                               (fixed iteration counts, real-time ticks) nothing
                               escalates.  GATO_PRECISION_FP32: never escalate (the step
-                              is then rejected with GATO_SOLVE_LSFAIL) */
+                              is then rejected with GATO_SOLVE_LSFAIL).
+                              GATO_PRECISION_HIGH: every iteration in the
+                              high-precision mode from the start */
 } gato_solver_params;
 
 typedef struct {
@@ -415,11 +417,13 @@ gato_status gato_debug_stage_cycles(gato_batch* b, int32_t enable, int64_t* cycl
  * enable = 1 allocates a log of max_iters records per solve (device memory);
  * every following gato_solve / gato_step call of the batch rewrites it from
  * iteration 0.  enable = 0 copies n x max_iters records to `log` (if non-NULL;
- * max_iters must equal the enabled value) and frees it.  A record is 4 int32:
+ * max_iters must equal the enabled value) and frees it.  A record is 8 int32:
  * the line search's choice (alpha index i of alpha = beta^-i, -1 = step
  * rejected, -2 = iteration not reached), the PCG iterations of that SQP
- * iteration, the KKT residual at its linearisation (the bits of a float), and
- * 1 if the iteration ran in the high-precision mode.  Synchronous.
+ * iteration, the KKT residual at its linearisation (the bits of a float),
+ * 1 if the iteration ran in the high-precision mode, the merit (Eq. 3) of the
+ * iterate and the merit of the full step's trial point (alpha = 1), each as
+ * the bits of a (hi, lo) float pair whose sum is the value.  Synchronous.
  * GATO_E_INVALID for bad arguments, GATO_E_NOMEM if the log cannot be
  * allocated. */
 gato_status gato_debug_iteration_log(gato_batch* b, int32_t enable, int32_t max_iters, int32_t* log,

@@ -72,8 +72,9 @@ const char* check_params(const gato_solver_params& p) {
   if (p.precond != GATO_PRECOND_STAIR && p.precond != GATO_PRECOND_JACOBI) return "unknown preconditioner";
   if (p.linsolve != GATO_LINSOLVE_PCG && p.linsolve != GATO_LINSOLVE_DIRECT) return "unknown linear solver";
   if (p.rho_adapt != 0 && p.rho_adapt != 1) return "rho_adapt must be 0 or 1";
-  if (p.precision != GATO_PRECISION_FP32 && p.precision != GATO_PRECISION_ESCALATE)
-    return "precision must be GATO_PRECISION_FP32 or GATO_PRECISION_ESCALATE";
+  if (p.precision != GATO_PRECISION_FP32 && p.precision != GATO_PRECISION_ESCALATE &&
+      p.precision != GATO_PRECISION_HIGH)
+    return "precision must be GATO_PRECISION_FP32, _ESCALATE or _HIGH";
   if (!std::isfinite(p.kkt_tol)) return "kkt_tol must be finite";
   return nullptr;
 }
@@ -237,6 +238,7 @@ Params to_params(const gato_solver_params& p, int iters) {
   o.linsolve = p.linsolve;
   o.rho_adapt = p.rho_adapt;
   o.escalate = p.precision == GATO_PRECISION_ESCALATE;
+  o.high = p.precision == GATO_PRECISION_HIGH;
   return o;
 }
 

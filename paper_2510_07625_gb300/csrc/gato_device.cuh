@@ -62,6 +62,7 @@ struct Params {
   int escalate;  // 1: with kkt_tol > 0, a solve whose FP32 line search finds no
                  // decrease, or whose FP32 KKT test passes, repeats the iteration
                  // in the high-precision mode and stays in it
+  int high;      // 1: every iteration in the high-precision mode from the start
 };
 
 struct Result {

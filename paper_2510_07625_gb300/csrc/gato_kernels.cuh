@@ -68,6 +68,7 @@ __device__ void sqp_solve(Ctx& C, const ProbDesc& P, const Params& prm, int iter
   int rbuf = 0;
   long long tl = C.tm ? clock64() : 0;
   const bool logging = itlog && C.rank == 0 && threadIdx.x == 0;
+  C.hp = prm.high ? 1 : 0;
   if (logging)
     for (int i = 0; i < itlog_iters * ITLOG_W; ++i) itlog[i] = (i % ITLOG_W == 0) ? -2 : 0;
   load_iterate(C, P);
@@ -154,6 +155,8 @@ __device__ void sqp_solve(Ctx& C, const ProbDesc& P, const Params& prm, int iter
     tstamp(C, T_RECOVER, tl);
     st_line_search(C, prm.mu, prm.beta, prm.n_alpha, rbuf);
     tstamp(C, T_LS, tl);
+    const float m_base[2] = {C.scal[S_MDF], C.scal[S_MDF + 1]};
+    const float m_full[2] = {C.scal[S_MDF + 2], C.scal[S_MDF + 3]};
     const int choice = st_accept(C, prm.beta, prm.n_alpha);
     csync(C);
     if (choice < 0 && prm.escalate && prm.kkt_tol > 0.f && !C.hp) {
@@ -169,6 +172,10 @@ __device__ void sqp_solve(Ctx& C, const ProbDesc& P, const Params& prm, int iter
       r[1] = pcg_total - pcg_at_start;
       r[2] = __float_as_int(kkt);
       r[3] = C.hp;
+      r[4] = __float_as_int(m_base[0]);
+      r[5] = __float_as_int(m_base[1]);
+      r[6] = __float_as_int(m_full[0]);
+      r[7] = __float_as_int(m_full[1]);
     }
     if (prm.rho_adapt) C.w[5] = rho_next(C.w[5], choice);  // every thread, the same choice
     tstamp(C, T_ACCEPT, tl);
@@ -309,6 +316,7 @@ __global__ void __launch_bounds__(NTHR, 1) sqp_plain_stage(int stage, PlainArgs 
       const int t = threadIdx.x;
       C.scal[t] = t == S_RHO ? P.w[5]
                 : (t == S_FEXT ? P.fext[0] : (t == S_FEXT + 1 ? P.fext[1] : (t == S_FEXT + 2 ? P.fext[2] : 0.f)));
+      if (t == S_HP) C.scal[t] = a.prm.high ? 1.f : 0.f;
     }
     load_iterate(C, P);
     return;

@@ -128,8 +128,9 @@ __device__ __forceinline__ float rho_next(float rho, int choice) {
 // One record of the per-iteration log (int32 each): the line search's choice
 // (alpha index, -1 rejected; -2 for an iteration not reached), the PCG
 // iterations of the iteration, the KKT residual at its linearisation (float
-// bits), 1 if it ran in the high-precision mode.
-constexpr int ITLOG_W = 4;
+// bits), 1 if it ran in the high-precision mode, then the merit of the
+// iterate and the merit of the full step's trial point as (hi, lo) float bits.
+constexpr int ITLOG_W = 8;
 
 // Per-knot strides of the global workspace arrays.
 constexpr int FQS = 49, QIS = 56, DTS = 14 * 8, LIS = 196;
@@ -1917,7 +1918,7 @@ __device__ __forceinline__ float trial_cost(const Ctx& C, int k, const float* x,
 
 
 // High-precision trial merits: the trial point (X + Xlo) + alpha dX in FP64;
-// qdd from the FP32 factor refined once against an FP64 RNEA residual
+// qdd from the FP32 factor refined twice against an FP64 RNEA residual
 // u - ID(q, qd, qdd_0); defects and costs in FP64.  Each per-knot value is
 // stored as an (hi, lo) float pair (hi in `hi`, lo in `lo`, [na][K] each).
 struct LsView {
@@ -1977,7 +1978,7 @@ static __device__ __noinline__ void st_line_search_hp(LsView v) {
         u[i] = uat(k * US + i);
         val += 0.5 * (double)v.w[2] * u[i] * u[i];
       }
-      // FP32 forward dynamics at the rounded point, then one refinement step
+      // FP32 forward dynamics at the rounded point, then refinement
       // against the FP64 inverse dynamics at the exact trial point
       float qf[QM], qdf[QM], sqf[QM], cqf[QM], Ml[28], z[QM], b[QM], qdd[QM];
 #pragma unroll

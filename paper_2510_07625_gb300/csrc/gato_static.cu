@@ -163,6 +163,7 @@ extern "C" gato_status gato_solve_noalloc(const gato_model_desc* models, int32_t
   a.prm.linsolve = sp.linsolve;
   a.prm.rho_adapt = sp.rho_adapt;
   a.prm.escalate = sp.precision == GATO_PRECISION_ESCALATE;
+  a.prm.high = sp.precision == GATO_PRECISION_HIGH;
   a.timing = nullptr;
   a.variant = 0;
   if (launch_fused_grouped(a, D.order, P->order, Ns, n, stream, LaunchPlan()) != cudaSuccess) {

@@ -24,7 +24,7 @@ SOLVE_CONVERGED, SOLVE_MAXITER, SOLVE_LSFAIL, SOLVE_PCG_MAXIT, SOLVE_NONFINITE =
 COST_JOINT, COST_EE = 0, 1
 PRECOND_STAIR, PRECOND_JACOBI = 0, 1
 LINSOLVE_PCG, LINSOLVE_DIRECT = 0, 1
-PRECISION_FP32, PRECISION_ESCALATE = 0, 1
+PRECISION_FP32, PRECISION_ESCALATE, PRECISION_HIGH = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 
 EXPORTED = (
@@ -302,16 +302,18 @@ def gato_debug_stage_cycles(handle, enable, n=0):
 def gato_debug_iteration_log(handle, enable, max_iters, n=0):
     """enable=1: start logging max_iters iterations per solve; enable=0: return
     a dict of (n, max_iters) arrays (alpha index, PCG iterations, KKT residual,
-    high-precision flag) and stop."""
-    out = np.zeros((max(n, 1), max_iters, 4), np.int32)
+    high-precision flag, merit of the iterate, merit of the full step) and stop."""
+    out = np.zeros((max(n, 1), max_iters, 8), np.int32)
     s = load().gato_debug_iteration_log(C.c_void_p(handle), enable, max_iters,
                                         out.ctypes.data if (not enable and n) else None, n)
     _check(handle, s, "gato_debug_iteration_log")
     if enable:
         return None
     out = out[:n]
+    f = out.view(np.float32).astype(np.float64)
     return {"alpha_idx": out[:, :, 0].copy(), "pcg_iters": out[:, :, 1].copy(),
-            "kkt": out[:, :, 2].copy().view(np.float32), "hp": out[:, :, 3].copy()}
+            "kkt": out[:, :, 2].copy().view(np.float32), "hp": out[:, :, 3].copy(),
+            "merit": f[:, :, 4] + f[:, :, 5], "merit_full_step": f[:, :, 6] + f[:, :, 7]}
 
 
 def gato_solve_noalloc(models, n_models, params, problems, n, iters, results_dev_ptr, stream=0):
