@@ -98,3 +98,27 @@ def test_rho_adapt_with_the_direct_solve(G):
     np.testing.assert_array_equal(a["X"], b["X"])
     fixed = gpu_solve(G, [p], 5, rho_adapt=0, linsolve=1)[0]
     assert np.abs(a["X"] - fixed["X"]).max() > 0  # the adaptation changed the path
+
+
+def test_rho_adapt_against_oracle(G, oracle):
+    """An adapted GPU solve against the oracle's adapted solve (Sec. IV-C's
+    rule, oracle.solve(rho_adapt=1)).  The first SQP iterations take the
+    oracle's line-search decisions (accept/reject drives rho, so the rho
+    sequences agree too) unless a decision is a near-tie; run to convergence,
+    both reach the same KKT point: X, U within 1e-4, the KKT residuals within
+    1e-5 (rho changes the path, not the solution)."""
+    from tests.test_gpu_parity import kkt_at, rel
+
+    p = with_rho(I.joint_problem(2, I.arm7(), 32, 0.01), 1e-2)
+    g = gpu_solve(G, [p], 6, rho_adapt=1, log=True)[0]
+    o = oracle.solve(p, max_iter=6, rho_adapt=1)
+    for t in range(6):
+        ga, oa = int(g["alpha_idx"][t]), int(o["alpha_idx"][t])
+        if ga != oa:
+            assert o["merit_gap"][t] <= 1e-5, (t, ga, oa, o["merit_gap"][t])
+            break
+    gc = gpu_solve(G, [p], 80, rho_adapt=1, kkt_tol=1e-5)[0]
+    oc = oracle.solve(p, max_iter=160, rho_adapt=1, kkt_tol=1e-9)
+    assert gc["flags"] & 1 and oc["kkt"] <= 1e-7, (gc["flags"], gc["kkt"], oc["kkt"])
+    assert rel(gc["X"], oc["X"]) <= 1e-4 and rel(gc["U"], oc["U"]) <= 1e-4
+    assert abs(kkt_at(oracle, p, gc["X"], gc["U"], gc["lam"]) - kkt_at(oracle, p, oc["X"], oc["U"], oc["lam"])) <= 1e-5
