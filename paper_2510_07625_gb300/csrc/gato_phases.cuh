@@ -1521,13 +1521,31 @@ __device__ inline int st_pcg_t(const Ctx& C, float eps, int maxit, int precond, 
 
 // The loop with halo knots (C.hrep: fused latency form in a cluster) and
 // without are separate instantiations, so the one-CTA loop carries none of
-// the halo logic.
+// the halo logic.  Each is an out-of-line call with the context passed by
+// value: its registers are allocated on their own, so the live state of the
+// other stages (the high-precision paths above all) cannot push the loop's
+// register-resident block rows into local memory.
+struct PcgOut {
+  int it, hit, rbuf;
+};
+
+template <bool REG, bool HREP>
+static __device__ __noinline__ PcgOut st_pcg_call(const Ctx C, float eps, int maxit, int precond, int rbuf) {
+  bool hit = false;
+  const int it = st_pcg_t<REG, HREP>(C, eps, maxit, precond, &hit, rbuf);
+  return PcgOut{it, hit ? 1 : 0, rbuf};
+}
+
 template <bool REG>
 __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bool* hit_max, int& rbuf) {
-  if constexpr (REG) {
-    if (C.hrep) return st_pcg_t<true, true>(C, eps, maxit, precond, hit_max, rbuf);
-  }
-  return st_pcg_t<REG, false>(C, eps, maxit, precond, hit_max, rbuf);
+  PcgOut o;
+  if (REG && C.hrep)
+    o = st_pcg_call<REG, true>(C, eps, maxit, precond, rbuf);
+  else
+    o = st_pcg_call<REG, false>(C, eps, maxit, precond, rbuf);
+  *hit_max = o.hit != 0;
+  rbuf = o.rbuf;
+  return o.it;
 }
 
 // ------------------------------------------------- stage 4: step recovery
