@@ -33,6 +33,7 @@ struct FusedLaunch {
   int* itlog = nullptr;    // device [n_total][itlog_iters][ITLOG_W] iteration records, or null
   int itlog_iters = 0;
   int variant;             // 0 = automatic, 1 = register rows (1 CTA/SM), 2 = 2 CTAs/SM
+  int resume = 0;          // high-precision kernel: resume the FP32 launch's hand-over records
 };
 
 // How solves map onto the GPU: the space the autotuner searches.
@@ -59,7 +60,15 @@ int cluster_size(int N, int knots_per_cta, int cluster = 0);
 cudaError_t configure_fused(size_t smem);
 
 // One persistent fused launch: n clusters of csize CTAs, one solve each.
+// FP32 kernel, followed on the same stream by the high-precision kernel that
+// resumes the escalated solves when the parameters allow escalation; the
+// high-precision kernel alone in the high-precision mode.
 cudaError_t launch_fused(const FusedLaunch& a, cudaStream_t s);
+
+// The high-precision instantiations (gato_kernels_hp.cu): one launch, and the
+// shared-memory attribute of both forms.
+cudaError_t launch_fused_hp(const FusedLaunch& a, size_t smem, cudaStream_t s, bool reg);
+cudaError_t configure_fused_hp(size_t smem);
 
 // Launches the solves in `order_host` (sorted by cluster size, then horizon,
 // both descending; order_dev is its device copy) as one launch per cluster

@@ -5,9 +5,9 @@
 //   recover -> line search) with the PCG working set on chip (block rows in
 //   registers, vectors in shared memory) and exits on its own convergence.
 //   Clusters are launched longest horizon first.
-// sqp_plain_stage: the plain form used as the comparison baseline.  The same
-//   stage functions, but each stage of each SQP iteration of one solve is a
-//   separate launch and every array lives in global memory.
+// The plain form (sqp_plain_stage, gato_kernels.cu) is the comparison
+// baseline: the same stage functions, but each stage of each SQP iteration of
+// one solve is a separate launch and every array lives in global memory.
 #pragma once
 
 #include "gato_internal.h"
@@ -61,27 +61,70 @@ __device__ __forceinline__ void bind_partition(Ctx& C, int rank, int csize) {
   C.k1 = min(C.k0 + kpc, K);
 }
 
-// The whole SQP loop of one solve (Sec. II-A Steps 1-3, repeated).
-template <bool REG>
-__device__ void sqp_solve(Ctx& C, const ProbDesc& P, const Params& prm, int iters, Result* out,
-                          int* itlog = nullptr, int itlog_iters = 0) {
+// Hand-over record of an escalating solve (ints in the solve's workspace at
+// WsLayout::hand): the FP32 kernel stops where a solve escalates and the
+// high-precision kernel, launched after it, resumes that iteration from the
+// workspace.  The two instantiations keep the high-precision stages out of
+// the FP32 kernel entirely, so they add no register pressure to its PCG.
+enum : int {
+  H_PENDING = 0,  // 1: the solve escalated and waits for the high-precision kernel
+  H_IT,           // the SQP iteration to repeat
+  H_SQP,          // SQP iterations completed
+  H_PCG,          // PCG iterations so far
+  H_FLAGS,        // result flags so far
+  H_PCG_AT,       // PCG iterations when iteration H_IT began (for its log record)
+  H_RHO,          // the solve's (possibly adapted) rho, float bits
+  H_COUNT
+};
+
+// The whole SQP loop of one solve (Sec. II-A Steps 1-3, repeated).  HP
+// false: FP32 throughout; where the precision mode asks to escalate, the
+// solve's state goes to `hand` and the loop stops without a result.  HP true:
+// the high-precision mode throughout, either from the start or, with
+// `resume`, from the hand-over record of an escalated solve (a solve without
+// one returns at once).
+template <bool REG, bool HP>
+__device__ void sqp_solve(Ctx& C, const ProbDesc& P, const Params& prm, int iters, Result* out, int* hand,
+                          bool resume, int* itlog = nullptr, int itlog_iters = 0) {
   int rbuf = 0;
   long long tl = C.tm ? clock64() : 0;
   const bool logging = itlog && C.rank == 0 && threadIdx.x == 0;
-  C.hp = prm.high ? 1 : 0;
-  if (logging)
-    for (int i = 0; i < itlog_iters * ITLOG_W; ++i) itlog[i] = (i % ITLOG_W == 0) ? -2 : 0;
-  load_iterate(C, P);
-  csync(C);
-  tstamp(C, T_LOAD, tl);
+  C.hp = HP ? 1 : 0;
   int flags = 0, sqp = 0, pcg_total = 0;
   float kkt = 0.f, merit = 0.f;
   bool base_stale = true;  // the iterate's own merit is due (first iteration, or after escalating)
   int pcg_at_start = 0;    // pcg_total when the iteration began (for the log)
-  for (int it = 0;; ++it) {
-    if (it == iters && !(prm.kkt_tol > 0.f)) break;
-    pcg_at_start = pcg_total;
-  retry:
+  int it = 0;
+  if (HP && resume) {
+    // every thread of the cluster reads the same record: the exit is uniform
+    const volatile int* h = hand;
+    if (h[H_PENDING] == 0) return;
+    it = h[H_IT];
+    sqp = h[H_SQP];
+    pcg_total = h[H_PCG];
+    flags = h[H_FLAGS];
+    pcg_at_start = h[H_PCG_AT];
+    C.w[5] = __int_as_float(h[H_RHO]);
+    // the iterate, multipliers and low parts (zero in FP32) stay in the
+    // workspace; only x_s is shared-memory state
+    if (threadIdx.x < 2 * C.dof) C.xs[pad_state(threadIdx.x, C.dof)] = P.x_s[threadIdx.x];
+    csync(C);
+  } else {
+    if (logging)
+      for (int i = 0; i < itlog_iters * ITLOG_W; ++i) itlog[i] = (i % ITLOG_W == 0) ? -2 : 0;
+    if (!HP && C.rank == 0 && threadIdx.x == 0) hand[H_PENDING] = 0;
+    load_iterate(C, P);
+    csync(C);
+  }
+  tstamp(C, T_LOAD, tl);
+  bool escalated = false;     // FP32 kernel: the solve's state went to the hand-over record
+  bool resuming = HP && resume;  // the first pass repeats the hand-over iteration
+  for (;; ++it) {
+    if (!resuming) {
+      if (it == iters && !(prm.kkt_tol > 0.f)) break;
+      pcg_at_start = pcg_total;
+    }
+    resuming = false;
     st_mass_bias(C);
     __syncthreads();
     tstamp(C, T_MASS, tl);
@@ -111,12 +154,11 @@ __device__ void sqp_solve(Ctx& C, const ProbDesc& P, const Params& prm, int iter
       break;
     }
     if (prm.kkt_tol > 0.f && kkt <= prm.kkt_tol) {
-      if (prm.escalate && !C.hp) {
+      if (!HP && prm.escalate) {
         // confirm convergence with the high-precision residual: the FP32
         // dual residual carries the kappa(M)-amplified error of A_k
-        C.hp = 1;
-        base_stale = true;
-        goto retry;
+        escalated = true;
+        break;
       }
       flags |= F_CONVERGED;
       break;
@@ -143,7 +185,7 @@ __device__ void sqp_solve(Ctx& C, const ProbDesc& P, const Params& prm, int iter
       }
       tstamp(C, T_BINV, tl);
       bool hit = false;
-      pcg_total += st_pcg<REG>(C, prm.pcg_eps, prm.pcg_max, prm.precond, &hit, rbuf);
+      pcg_total += st_pcg<REG, HP>(C, prm.pcg_eps, prm.pcg_max, prm.precond, &hit, rbuf);
       if (hit) flags |= F_PCGMAX;
     }
     if (C.tm && C.rank == 0 && threadIdx.x == 0) tl = clock64();
@@ -159,12 +201,11 @@ __device__ void sqp_solve(Ctx& C, const ProbDesc& P, const Params& prm, int iter
     const float m_full[2] = {C.scal[S_MDF + 2], C.scal[S_MDF + 3]};
     const int choice = st_accept(C, prm.beta, prm.n_alpha);
     csync(C);
-    if (choice < 0 && prm.escalate && prm.kkt_tol > 0.f && !C.hp) {
+    if (!HP && choice < 0 && prm.escalate && prm.kkt_tol > 0.f) {
       // the FP32 line search found no decrease: repeat this iteration in the
       // high-precision mode (every thread takes the same branch)
-      C.hp = 1;
-      base_stale = true;
-      goto retry;
+      escalated = true;
+      break;
     }
     if (logging && it < itlog_iters) {
       int* r = itlog + it * ITLOG_W;
@@ -186,6 +227,18 @@ __device__ void sqp_solve(Ctx& C, const ProbDesc& P, const Params& prm, int iter
     ++sqp;
   }
   csync(C);
+  if (!HP && escalated) {
+    if (C.rank == 0 && threadIdx.x == 0) {
+      hand[H_IT] = it;
+      hand[H_SQP] = sqp;
+      hand[H_PCG] = pcg_total;
+      hand[H_FLAGS] = flags;
+      hand[H_PCG_AT] = pcg_at_start;
+      hand[H_RHO] = __float_as_int(C.w[5]);
+      hand[H_PENDING] = 1;
+    }
+    return;
+  }
   store_iterate(C, P);
   if (C.rank == 0 && threadIdx.x == 0) {
     out->flags = flags;
@@ -198,7 +251,10 @@ __device__ void sqp_solve(Ctx& C, const ProbDesc& P, const Params& prm, int iter
 
 // REG = true: 1 CTA per SM, all PCG block rows in registers (latency);
 // REG = false: 2 CTAs per SM, off-diagonal rows read from shared memory (throughput).
-template <bool REG>
+// HP = false: the FP32 solve (escalating solves stop at a hand-over record);
+// HP = true: the high-precision mode, from the start or (a.resume) resuming
+// the hand-over records of the FP32 launch before it on the same stream.
+template <bool REG, bool HP>
 __global__ void __launch_bounds__(NTHR, REG ? 1 : 2) sqp_fused(FusedLaunch a) {
   extern __shared__ float4 smem4[];
   float* sm = reinterpret_cast<float*>(smem4);
@@ -260,179 +316,50 @@ __global__ void __launch_bounds__(NTHR, REG ? 1 : 2) sqp_fused(FusedLaunch a) {
   }
   for (int i = threadIdx.x; i < 196; i += NTHR) zblock[i] = 0.f;
   __syncthreads();
-  sqp_solve<REG>(C, P, a.prm, a.iters, a.results + b,
-                 a.itlog ? a.itlog + (size_t)b * a.itlog_iters * ITLOG_W : nullptr, a.itlog_iters);
+  sqp_solve<REG, HP>(C, P, a.prm, a.iters, a.results + b, reinterpret_cast<int*>(ws + a.layout.hand),
+                     a.resume != 0, a.itlog ? a.itlog + (size_t)b * a.itlog_iters * ITLOG_W : nullptr,
+                     a.itlog_iters);
   if (a.timing) {
     __syncthreads();
     if (rank == 0 && threadIdx.x < T_COUNT) a.timing[(size_t)b * T_COUNT + threadIdx.x] += tm_sh[threadIdx.x];
   }
 }
 
-// ----------------------------------------------------------------- plain form
+// Shared-memory attribute of one fused instantiation, set once per device for
+// launches of up to `smem` bytes.
+template <bool REG, bool HP>
+cudaError_t configure_kernel(size_t smem) {
+  static size_t done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (smem > done[dev]) {
+    e = cudaFuncSetAttribute(sqp_fused<REG, HP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    done[dev] = smem;
+  }
+  return cudaSuccess;
+}
 
-struct PlainArgs {
-  const ProbDesc* probs;
-  const DevModel* models;
-  Result* results;
-  float* ws;
-  WsLayout layout;
-  int b, nmax, iters, it, csize;
-  int redo;  // 1: the pass that repeats an iteration in the high-precision mode
-  Params prm;
-};
-
-__global__ void __launch_bounds__(NTHR, 1) sqp_plain_stage(int stage, PlainArgs a) {
-  __shared__ __align__(16) float red[2 * RED_SLOTS * RED_W];
-  __shared__ float zeros196[196];
-  for (int i = threadIdx.x; i < 196; i += NTHR) zeros196[i] = 0.f;
-  __syncthreads();
-  const int csize = a.csize;
-  const int rank = csize > 1 ? (int)cg::this_cluster().block_rank() : 0;
-  const ProbDesc P = a.probs[a.b];
-  const size_t K = (size_t)a.nmax + 1;
-  Ctx C;
-  bind_problem(C, P, a.models + P.model);
-  bind_workspace(C, a.ws, a.layout);
-  bind_partition(C, rank, csize);
-  C.Dm = a.ws + a.layout.Dm;
-  C.Lm = a.ws + a.layout.Lm;
-  C.Pm = a.ws + a.layout.Pm;
-  C.bk0 = 0;
-  C.Lz = zeros196;
-  C.vb = a.ws + a.layout.vec;
-  C.vstride = (int)((K + 2) * VW);
-  C.vk0 = -1;
-  C.vbl = C.vbr = nullptr;
-  C.vk0l = C.vk0r = 0;
-  C.scal = C.vb + NVEC * C.vstride;
-  C.xs = C.scal + SCAL_FLOATS;
-  C.red = red;
-  C.tm = nullptr;
-  const Params& prm = a.prm;
-  int* rflags = reinterpret_cast<int*>(C.scal + S_RFLAGS);
-  int rbuf = 0;
-  if (stage == PS_LOAD) {
-    if (rank == 0 && threadIdx.x < SCAL_FLOATS) {
-      const int t = threadIdx.x;
-      C.scal[t] = t == S_RHO ? P.w[5]
-                : (t == S_FEXT ? P.fext[0] : (t == S_FEXT + 1 ? P.fext[1] : (t == S_FEXT + 2 ? P.fext[2] : 0.f)));
-      if (t == S_HP) C.scal[t] = a.prm.high ? 1.f : 0.f;
-    }
-    load_iterate(C, P);
-    return;
-  }
-  if (a.prm.rho_adapt) C.w[5] = C.scal[S_RHO];  // the adapted rho of this SQP iteration
-  C.hp = C.scal[S_HP] != 0.f;
-  if (stage == PS_STORE) {
-    store_iterate(C, P);
-    if (rank == 0 && threadIdx.x == 0) {
-      Result* out = a.results + a.b;
-      out->flags = *rflags;
-      out->sqp_iters = (int)C.scal[S_NSQP];
-      out->pcg_iters = (int)C.scal[S_NPCG];
-      out->kkt = C.scal[S_KKT];
-      out->merit = C.scal[S_MERITF];
-    }
-    return;
-  }
-  if (C.scal[S_DONE] != 0.f) return;
-  if (a.redo && C.scal[S_REDO] == 0.f) return;  // no escalation in this iteration
-  // an escalation decided at the KKT stage skips the rest of the first pass
-  if (!a.redo && stage > PS_KKT && C.scal[S_REDO] != 0.f) return;
-  const bool lead = rank == 0 && threadIdx.x == 0;
-  switch (stage) {
-    case PS_MASS: st_mass_bias(C); break;
-    case PS_FD: st_forward_dynamics(C); break;
-    case PS_VALUE: st_value_and_cost(C); break;
-    case PS_TANGENT: st_tangents(C); break;
-    case PS_JAC: st_dyn_jacobians(C); break;
-    case PS_KKT: {
-      st_kkt_merit(C, prm.mu, rbuf);
-      if (a.it == 0 || a.redo) st_line_search(C, prm.mu, prm.beta, prm.n_alpha, rbuf, true);  // the iterate's merit
-      const bool bad = *reinterpret_cast<volatile int*>(C.scal + S_FLAGS) != 0;
-      if (lead) {
-        C.scal[S_MERITF] = C.scal[S_MERIT0];
-        int f = *rflags;
-        bool done = false;
-        if (bad) {
-          f |= F_NONFINITE;
-          done = true;
-        } else if (prm.kkt_tol > 0.f && C.scal[S_KKT] <= prm.kkt_tol && prm.escalate && !C.hp) {
-          // confirm convergence with the high-precision residual (the pass
-          // that repeats this iteration in that mode)
-          C.scal[S_HP] = 1.f;
-          C.scal[S_REDO] = 1.f;
-        } else if (prm.kkt_tol > 0.f && C.scal[S_KKT] <= prm.kkt_tol) {
-          f |= F_CONVERGED;
-          done = true;
-        } else if (a.it == a.iters) {
-          f |= F_MAXITER;
-          done = true;
-        }
-        *rflags = f;
-        if (done) C.scal[S_DONE] = 1.f;
-      }
-      break;
-    }
-    case PS_SCHUR: st_schur(C); break;
-    case PS_BINV:
-      st_block_inverse(C);
-      csync(C);
-      if (lead && *reinterpret_cast<volatile int*>(C.scal + S_FLAGS)) {
-        *rflags |= F_NONFINITE;
-        C.scal[S_DONE] = 1.f;
-      }
-      break;
-    case PS_PCG: {
-      if (prm.linsolve == 1) {
-        st_direct(C);
-        csync(C);
-        if (lead && *reinterpret_cast<volatile int*>(C.scal + S_FLAGS)) {
-          *rflags |= F_NONFINITE;
-          C.scal[S_DONE] = 1.f;
-        }
-        break;
-      }
-      bool hit = false;
-      const int n = st_pcg<true>(C, prm.pcg_eps, prm.pcg_max, prm.precond, &hit, rbuf);
-      if (lead) {
-        C.scal[S_NPCG] += (float)n;
-        if (hit) *rflags |= F_PCGMAX;
-      }
-      break;
-    }
-    case PS_RECOVER:
-      st_recover(C);
-      csync(C);
-      if (lead && *reinterpret_cast<volatile int*>(C.scal + S_FLAGS)) {
-        *rflags |= F_NONFINITE;
-        C.scal[S_DONE] = 1.f;
-      }
-      break;
-    case PS_LS: st_line_search(C, prm.mu, prm.beta, prm.n_alpha, rbuf); break;
-    case PS_ACCEPT: {
-      const int choice = st_accept(C, prm.beta, prm.n_alpha);
-      if (choice < 0 && prm.escalate && prm.kkt_tol > 0.f && !C.hp) {
-        // repeat this iteration in the high-precision mode (the next pass)
-        if (lead) {
-          C.scal[S_HP] = 1.f;
-          C.scal[S_REDO] = 1.f;
-        }
-        break;
-      }
-      if (lead) C.scal[S_REDO] = 0.f;
-      if (lead && prm.rho_adapt) C.scal[S_RHO] = rho_next(C.w[5], choice);
-      if (lead) {
-        if (choice >= 0)
-          C.scal[S_MERITF] = C.scal[S_MERITS + choice];
-        else
-          *rflags |= F_LSFAIL;
-        C.scal[S_NSQP] += 1.f;
-      }
-      break;
-    }
-    default: break;
-  }
+// One launch of a fused instantiation: a.n clusters of a.csize CTAs.
+template <bool REG, bool HP>
+cudaError_t launch_kernel(const FusedLaunch& a, size_t smem, cudaStream_t s) {
+  cudaError_t e = configure_kernel<REG, HP>(smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(a.n * a.csize));
+  cfg.blockDim = dim3(NTHR);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)a.csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, sqp_fused<REG, HP>, a);
 }
 
 }  // namespace gato

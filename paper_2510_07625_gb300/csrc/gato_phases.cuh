@@ -137,7 +137,7 @@ constexpr int FQS = 49, QIS = 56, DTS = 14 * 8, LIS = 196;
 
 struct WsLayout {
   size_t X, U, dX, dU, Fq, Fv, Mi, qdd, dT, Qi, Ri, qg, rg, cv, Jk, Li, LV, Dm, Lm, Pm, vec, Dx, Du,
-      nu, Xlo, Ulo, total;
+      nu, Xlo, Ulo, hand, total;
 };
 
 __host__ __device__ inline size_t align32(size_t n) { return (n + 31) & ~size_t(31); }
@@ -170,6 +170,7 @@ __host__ __device__ inline WsLayout ws_layout(int Nmax, bool global_blocks, bool
   L.nu = o; o += align32(K * VS);
   L.Xlo = o; o += align32(K * VS);
   L.Ulo = o; o += align32(Nmax * US);
+  L.hand = o; o += 32;  // hand-over record of an escalating solve (ints)
   if (global_blocks) {
     L.Dm = o; o += align32(K * BS);
     L.Lm = o; o += align32(K * BS);
@@ -1519,12 +1520,12 @@ __device__ inline int st_pcg_t(const Ctx& C, float eps, int maxit, int precond, 
 #undef SLOT
 }
 
-// The loop with halo knots (C.hrep: fused latency form in a cluster) and
-// without are separate instantiations, so the one-CTA loop carries none of
-// the halo logic.  Each is an out-of-line call with the context passed by
-// value: its registers are allocated on their own, so the live state of the
-// other stages (the high-precision paths above all) cannot push the loop's
-// register-resident block rows into local memory.
+// Out-of-line form of the loop, with the context passed by value: its
+// registers are allocated on their own, so a caller whose other stages hold
+// many live values (the high-precision kernel) cannot push the loop's
+// register-resident block rows into local memory.  (In a caller without that
+// pressure the inlined loop is faster: the call boundary costs it ~8 % per
+// iteration.)
 struct PcgOut {
   int it, hit, rbuf;
 };
@@ -1536,16 +1537,23 @@ static __device__ __noinline__ PcgOut st_pcg_call(const Ctx C, float eps, int ma
   return PcgOut{it, hit ? 1 : 0, rbuf};
 }
 
-template <bool REG>
+// The loop with halo knots (C.hrep: fused latency form in a cluster) and
+// without are separate instantiations, so the one-CTA loop carries none of
+// the halo logic.  OOL: the out-of-line form above.
+template <bool REG, bool OOL = false>
 __device__ inline int st_pcg(const Ctx& C, float eps, int maxit, int precond, bool* hit_max, int& rbuf) {
-  PcgOut o;
-  if (REG && C.hrep)
-    o = st_pcg_call<REG, true>(C, eps, maxit, precond, rbuf);
-  else
-    o = st_pcg_call<REG, false>(C, eps, maxit, precond, rbuf);
-  *hit_max = o.hit != 0;
-  rbuf = o.rbuf;
-  return o.it;
+  if constexpr (OOL) {
+    const PcgOut o = (REG && C.hrep) ? st_pcg_call<REG, true>(C, eps, maxit, precond, rbuf)
+                                     : st_pcg_call<REG, false>(C, eps, maxit, precond, rbuf);
+    *hit_max = o.hit != 0;
+    rbuf = o.rbuf;
+    return o.it;
+  } else {
+    if constexpr (REG) {
+      if (C.hrep) return st_pcg_t<true, true>(C, eps, maxit, precond, hit_max, rbuf);
+    }
+    return st_pcg_t<REG, false>(C, eps, maxit, precond, hit_max, rbuf);
+  }
 }
 
 // ------------------------------------------------- stage 4: step recovery
