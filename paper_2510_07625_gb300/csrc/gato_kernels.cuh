@@ -106,7 +106,10 @@ __device__ void sqp_solve(Ctx& C, const ProbDesc& P, const Params& prm, int iter
     pcg_at_start = h[H_PCG_AT];
     C.w[5] = __int_as_float(h[H_RHO]);
     // the iterate, multipliers and low parts (zero in FP32) stay in the
-    // workspace; only x_s is shared-memory state
+    // workspace; only x_s is shared-memory state (padded, as load_iterate
+    // leaves it: the padding rows of the knot-0 defect read it)
+    if (threadIdx.x < VS) C.xs[threadIdx.x] = 0.f;
+    __syncthreads();
     if (threadIdx.x < 2 * C.dof) C.xs[pad_state(threadIdx.x, C.dof)] = P.x_s[threadIdx.x];
     csync(C);
   } else {

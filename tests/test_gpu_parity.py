@@ -121,6 +121,25 @@ def test_fused_equals_plain_bitwise_through_escalation(G):
     assert (a["flags"], a["sqp_iters"], a["pcg_iters"]) == (b["flags"], b["sqp_iters"], b["pcg_iters"])
 
 
+def test_batch_invariance_bitwise_through_escalation(G):
+    """An escalating batch of 6- and 7-DoF solves of mixed horizons (KKT
+    1e-5, 20 iterations): the solves that escalate continue in the
+    high-precision kernel from their hand-over records, and every solve's
+    result is the one it gets alone.  In a mixed batch a resumed CTA meets
+    shared memory left by other solves' CTAs, so state the resume fails to
+    rebuild shows up here."""
+    probs = I.config_uneven(16)
+    together = gpu_solve(G, probs, 20, log=True, kkt_tol=1e-5)
+    assert sum(bool(r["hp"].any()) for r in together) >= 2, "too few solves escalated"
+    assert len({p.model.dof for p in probs}) == 2
+    for i, p in enumerate(probs):
+        alone = gpu_solve(G, [p], 20, kkt_tol=1e-5)[0]
+        for k in ("X", "U", "lam"):
+            np.testing.assert_array_equal(alone[k], together[i][k], err_msg=f"solve {i} {k}")
+        assert (alone["flags"], alone["sqp_iters"], alone["pcg_iters"]) == \
+            (together[i]["flags"], together[i]["sqp_iters"], together[i]["pcg_iters"]), i
+
+
 def test_batch_invariance_bitwise(G):
     probs = I.config_fixed_batch(B=8, N=20)
     together = gpu_solve(G, probs, 3)
