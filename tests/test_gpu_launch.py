@@ -167,3 +167,18 @@ def test_halo_recompute_equals_pushed_halos_bitwise(G, N, cl, precond):
         for k in ("X", "U", "lam"):
             np.testing.assert_array_equal(x[k], y[k])
         assert (x["flags"], x["sqp_iters"], x["pcg_iters"]) == (y["flags"], y["sqp_iters"], y["pcg_iters"])
+
+
+@pytest.mark.parametrize("N", [64, 100])
+def test_halo_recompute_equals_plain_exchange_bitwise(G, N):
+    # The plain form, like the throughput form, exchanges boundary y and u
+    # rows between the CTAs of a cluster; the fused latency form, with the
+    # same split of the knots (cluster_for(N) CTAs), recomputes them.  Two
+    # and four CTAs.
+    probs = [I.ee_problem(7, I.arm7(), N), I.joint_problem(9, I.arm6(), N, 0.01)]
+    for p in probs:
+        a = gpu_solve(G, [p], 3, launch=(1, 0, 0))[0]
+        b = gpu_solve(G, [p], 3, plain=True)[0]
+        for k in ("X", "U", "lam"):
+            np.testing.assert_array_equal(a[k], b[k])
+        assert (a["flags"], a["sqp_iters"], a["pcg_iters"]) == (b["flags"], b["sqp_iters"], b["pcg_iters"])
