@@ -1592,6 +1592,10 @@ __device__ __forceinline__ void st_direct_body(const Ctx& C) {
   const int t = threadIdx.x;
   const int i = t % XM, j = t / XM;  // element (i, j) of a column-major block, t < BB
   const bool el = t < BB;
+  // the vector part of a step runs on warp 7, which holds no block element
+  // (warp 6 holds elements 192-195)
+  constexpr int YT = 7 * 32;
+  static_assert(BB <= YT && YT + XM <= NTHR, "vector part on its own warp");
   float* const W = C.red;
   float* const G0 = W + BB;
   float* const G1 = G0 + BB;
@@ -1621,20 +1625,16 @@ __device__ __forceinline__ void st_direct_body(const Ctx& C) {
         const float id = 1.f / det;
         const float P00 = d * id, P01 = -b * id, P10 = -c * id, P11 = a * id;
         const bool ip = (i == p || i == q), jp = (j == p || j == q);
-        float out;
-        if (ip && jp) {
-          out = (i == p) ? (j == p ? P00 : P01) : (j == p ? P10 : P11);
-        } else if (ip) {
-          const float apj = A[j * XM + p], aqj = A[j * XM + q];
-          out = (i == p) ? P00 * apj + P01 * aqj : P10 * apj + P11 * aqj;
-        } else if (jp) {
-          const float aip = A[p * XM + i], aiq = A[q * XM + i];
-          out = (j == p) ? -(aip * P00 + aiq * P10) : -(aip * P01 + aiq * P11);
-        } else {
-          const float aip = A[p * XM + i], aiq = A[q * XM + i], apj = A[j * XM + p], aqj = A[j * XM + q];
-          const float v0 = P00 * apj + P01 * aqj, v1 = P10 * apj + P11 * aqj;
-          out = A[t] - (aip * v0 + aiq * v1);
-        }
+        // every class's value (pivot block, pivot rows, pivot columns, the
+        // rest) by its own expressions, then one select: the elements of a
+        // warp fall in all four classes, so branches would run one by one
+        const float apj = A[j * XM + p], aqj = A[j * XM + q], aip = A[p * XM + i], aiq = A[q * XM + i];
+        const float v0 = P00 * apj + P01 * aqj, v1 = P10 * apj + P11 * aqj;  // Pi A[P, j]
+        const float piv = (i == p) ? (j == p ? P00 : P01) : (j == p ? P10 : P11);
+        const float row = (i == p) ? v0 : v1;
+        const float col = (j == p) ? -(aip * P00 + aiq * P10) : -(aip * P01 + aiq * P11);
+        const float rest = A[t] - (aip * v0 + aiq * v1);
+        const float out = ip ? (jp ? piv : row) : (jp ? col : rest);
         (p == XM - 2 ? Pk : B)[t] = out;
         if (t == 0 && !(a > 0.f && det > 0.f && det < INFINITY)) flag_nonfinite(C);
       }
@@ -1661,8 +1661,8 @@ __device__ __forceinline__ void st_direct_body(const Ctx& C) {
 #pragma unroll
       for (int l = 0; l < XM; ++l) a -= W[l * XM + i] * Lk[l * XM + j];
       G0[t] = a;
-    } else if (t < BB + XM) {
-      const int r = t - BB;
+    } else if (t >= YT && t < YT + XM) {
+      const int r = t - YT;
       float a = rs[r];
 #pragma unroll
       for (int l = 0; l < XM; ++l) a -= W[l * XM + r] * yp[l];
@@ -1688,8 +1688,8 @@ __device__ __forceinline__ void st_direct_body(const Ctx& C) {
 #pragma unroll
       for (int l = 0; l < XM; ++l) a -= W[l * XM + i] * Ln[j * XM + l];
       G0[t] = a;
-    } else if (t < BB + XM) {
-      const int r = t - BB;
+    } else if (t >= YT && t < YT + XM) {
+      const int r = t - YT;
       float a = rk[r];
 #pragma unroll
       for (int l = 0; l < XM; ++l) a -= W[l * XM + r] * yn[l];
@@ -1700,7 +1700,7 @@ __device__ __forceinline__ void st_direct_body(const Ctx& C) {
   // the block as it is: D_k, rhs_k (the first knot from either end)
   auto as_is = [&](int k) {
     if (el) G0[t] = bD(C, k, i, j);
-    else if (t < BB + XM) vec(C, V_Y, k)[t - BB] = vec(C, V_RHS, k)[t - BB];
+    else if (t >= YT && t < YT + XM) vec(C, V_Y, k)[t - YT] = vec(C, V_RHS, k)[t - YT];
     __syncthreads();
   };
 
@@ -1778,7 +1778,9 @@ __device__ __forceinline__ void st_direct_body(const Ctx& C) {
     const bool mid = own && C.rank == rm && s == 0;
     const bool down = mid || (own && C.rank < rm && s == sdown);
     const bool up = mid || (own && C.rank > rm && s == sup);
-    if (down) {  // k from m-1 (rank rm) or k1-1 down to k0
+    // the substitution runs on lanes 0-13 of warp 0 (warp barriers); the
+    // other warps wait at the stage's cluster barrier
+    if (down && t < 32) {  // k from m-1 (rank rm) or k1-1 down to k0
       for (int k = (C.rank == rm ? m - 1 : C.k1 - 1); k >= C.k0; --k) {
         if (t < XM) {
           float b = vec(C, V_Y, k)[t];
@@ -1788,7 +1790,7 @@ __device__ __forceinline__ void st_direct_body(const Ctx& C) {
           for (int l = 0; l < XM; ++l) b -= Ln[t * XM + l] * xn[l];
           W[t] = b;
         }
-        __syncthreads();
+        __syncwarp();
         if (t < XM) {
           const float* Pk = &bP(C, k, 0, 0);
           float x = 0.f;
@@ -1796,13 +1798,13 @@ __device__ __forceinline__ void st_direct_body(const Ctx& C) {
           for (int l = 0; l < XM; ++l) x += Pk[l * XM + t] * W[l];
           vec(C, V_DNU, k)[t] = x;
         }
-        __syncthreads();
+        __syncwarp();
       }
       // the first dnu to the previous CTA (unless dnu_m went there already)
       if (t < XM && C.rank > 0 && !(C.rank == rm && m == C.k0))
         cg::this_cluster().map_shared_rank(dR, C.rank - 1)[t] = vec(C, V_DNU, C.k0)[t];
     }
-    if (up) {  // k from m+1 (rank rm) or k0 up to k1-1
+    if (up && t < 32) {  // k from m+1 (rank rm) or k0 up to k1-1
       for (int k = (C.rank == rm ? m + 1 : C.k0); k < C.k1; ++k) {
         if (t < XM) {
           float b = vec(C, V_Y, k)[t];
@@ -1812,7 +1814,7 @@ __device__ __forceinline__ void st_direct_body(const Ctx& C) {
           for (int l = 0; l < XM; ++l) b -= Lk[l * XM + t] * xp[l];
           W[t] = b;
         }
-        __syncthreads();
+        __syncwarp();
         if (t < XM) {
           const float* Pk = &bP(C, k, 0, 0);
           float x = 0.f;
@@ -1820,7 +1822,7 @@ __device__ __forceinline__ void st_direct_body(const Ctx& C) {
           for (int l = 0; l < XM; ++l) x += Pk[l * XM + t] * W[l];
           vec(C, V_DNU, k)[t] = x;
         }
-        __syncthreads();
+        __syncwarp();
       }
       // the last dnu to the next CTA (unless dnu_m went there already)
       if (t < XM && C.rank + 1 < C.csize && C.k1 <= N && !(C.rank == rm && m == C.k1 - 1))
