@@ -6,7 +6,8 @@ the same order) and every solve's arithmetic are the same as gato_solve's
 automatic choice; only where the workspace lives differs.  So on the same
 inputs its output must equal gato_solve's bit for bit, for the default
 solver (PCG), the direct linear solve and rho adaptation alike, on two calls in
-a row (the second reuses the scratch the first left behind).  This file is
+a row (the second reuses the scratch the first left behind), and through an
+escalation to the high-precision mode.  This file is
 collected last so that a failure here comes after every other test has run.
 """
 import ctypes
@@ -74,6 +75,22 @@ def test_noalloc_matches_gato_solve_two_calls(G, prm):
     _run_pair(G, first, 4, **prm)
     second = [I.ee_problem(s, I.arm7(), 64, 0.01) for s in range(3)] + [I.joint_problem(7, I.arm7(), 48)]
     _run_pair(G, second, 3, **prm)
+
+
+def test_noalloc_matches_gato_solve_through_escalation(G):
+    """With a KKT tolerance the solves escalate to the high-precision mode:
+    the FP32 kernel leaves a hand-over record in the solve's workspace and the
+    high-precision kernel resumes it.  Through the static scratch the records
+    and the resumed solves must equal gato_solve's bit for bit."""
+    from tests.test_gpu_parity import gpu_solve
+
+    # a tolerance below the FP32 floor: the solves escalate and go on
+    # iterating in the mode (so the log shows it)
+    probs = [I.joint_problem(3, I.arm7(), N=12), I.joint_problem(1, I.arm7(), 32, 0.01),
+             I.joint_problem(5, I.arm6(), 20)]
+    logged = gpu_solve(G, probs, 30, log=True, kkt_tol=1e-9)
+    assert sum(bool(r["hp"].any()) for r in logged) >= 1, "no solve escalated"
+    _run_pair(G, probs, 30, kkt_tol=1e-9)
 
 
 def test_noalloc_rejects_sizes_beyond_its_limits(G):
