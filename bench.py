@@ -292,7 +292,7 @@ def run_gpu(args):
             "wall_s_timed": round(t_wall, 4),
             "roofline": {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 2),
                          "unit": "TFLOP/s", "frac": round(achieved / peak, 5), "traffic": TRAFFIC_BYTES,
-                         "kernel": "sqp_fused<%s>" % ("false" if launch["variant"] == 2 else "true"),
+                         "kernel": "sqp_fused<%s, false>" % ("false" if launch["variant"] == 2 else "true"),
                          "flops_per_launch": flops,
                          "peak_note": f"FP32 non-tensor: {sms} SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz "
                                       f"(sampled clock; SM count from the device)"},
