@@ -432,7 +432,8 @@ gato_status gato_debug_iteration_log(gato_batch* b, int32_t enable, int32_t max_
 /* Fills offsets[0..24] (floats) of the workspace arrays in the order
  * X U dX dU Fq Fv Minv qdd dTau Qinv Rinv q r c Jk Linv links D L P vec scal
  * dres_x dres_u nu,
- * and returns the workspace size in floats (or -1). */
+ * and returns the workspace size in floats (or -1).  Linv is empty (its offset
+ * equals that of links): the block inverse keeps its rows in registers. */
 int64_t gato_debug_layout(const gato_batch* b, int64_t* offsets);
 
 const char* gato_status_string(gato_status s);
