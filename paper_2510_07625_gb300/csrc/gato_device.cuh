@@ -191,6 +191,65 @@ __device__ __forceinline__ float warp_max(float v) {
   return v;
 }
 
+// ------------------------------------------------ double-float scalar (dfl)
+// A value carried as a normalised pair hi + lo of floats (|lo| <= ulp(hi)),
+// with the arithmetic of Dekker and Knuth: TwoSum for sums, an FMA-based
+// TwoProduct for products, each result renormalised by a fast two-sum.
+// About 44-48 bits of significand from FP32 operations; on this part the
+// FP32 pipe is some 64 times the FP64 rate, so the templated dynamics run
+// much faster on dfl than on double at the accuracy the high-precision mode
+// needs.  Products with a float are exact before the renormalisation.
+struct dfl {
+  float hi, lo;
+  __device__ __forceinline__ dfl() : hi(0.f), lo(0.f) {}
+  __device__ __forceinline__ dfl(float h) : hi(h), lo(0.f) {}
+  __device__ __forceinline__ dfl(int h) : hi((float)h), lo(0.f) {}
+  __device__ __forceinline__ dfl(float h, float l) : hi(h), lo(l) {}
+};
+// (s, e) with |e| small next to |s| as a normalised pair
+__device__ __forceinline__ dfl dfl_fast(float s, float e) {
+  const float h = __fadd_rn(s, e);
+  return dfl(h, __fsub_rn(e, __fsub_rn(h, s)));
+}
+__device__ __forceinline__ dfl dfl_of(double d) {
+  const float h = (float)d;
+  return dfl(h, (float)(d - (double)h));
+}
+__device__ __forceinline__ double dfl_double(dfl a) { return (double)a.hi + (double)a.lo; }
+// a + b of two floats, exactly
+__device__ __forceinline__ dfl dfl_sum(float a, float b) {
+  float s, e;
+  two_sum(a, b, s, e);
+  return dfl(s, e);
+}
+__device__ __forceinline__ dfl operator+(dfl a, dfl b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  return dfl_fast(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ dfl operator-(dfl a) { return dfl(-a.hi, -a.lo); }
+__device__ __forceinline__ dfl operator-(dfl a, dfl b) { return a + (-b); }
+__device__ __forceinline__ dfl operator*(dfl a, dfl b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return dfl_fast(p, e);
+}
+__device__ __forceinline__ dfl& operator+=(dfl& a, dfl b) { return a = a + b; }
+__device__ __forceinline__ dfl& operator-=(dfl& a, dfl b) { return a = a - b; }
+__device__ __forceinline__ bool operator!=(dfl a, dfl b) { return a.hi != b.hi || a.lo != b.lo; }
+__device__ __forceinline__ dfl dfl_abs(dfl a) { return a.hi < 0.f ? -a : a; }
+// (the double overload keeps unqualified calls on doubles resolving here)
+__device__ __forceinline__ void sincos(double x, double* s, double* c) { ::sincos(x, s, c); }
+// sin and cos to double-float accuracy: one FP64 sincos, split
+__device__ __forceinline__ void sincos(dfl x, dfl* s, dfl* c) {
+  double sd, cd;
+  ::sincos(dfl_double(x), &sd, &cd);
+  *s = dfl_of(sd);
+  *c = dfl_of(cd);
+}
+
 // ------------------------------------------------------------------ dynamics
 
 struct LinkRec {  // value-pass quantities of one link (link coordinates)
@@ -489,19 +548,16 @@ __device__ __forceinline__ bool forward_dynamics(const DevModel& M, const float*
 
 // End-effector position and (float only, J non-null) its 3x7 Jacobian
 // (row-major) in base coordinates.
+// fk_ee_sc takes sin and cos of q (sq, cq); fk_ee forms them.
 template <typename T>
-__device__ __forceinline__ void fk_ee(const DevModel& M, const T* q, T* p, float* J) {
+__device__ __forceinline__ void fk_ee_sc(const DevModel& M, const T* sq, const T* cq, T* p, float* J) {
   T R[9] = {T(1), T(0), T(0), T(0), T(1), T(0), T(0), T(0), T(1)};  // row-major, columns are the frame axes
   Vec3<T> pos = vzero<T>();
   Vec3<T> pj[QM], ej[QM];
 #pragma unroll
   for (int i = 0; i < QM; ++i) {
     if (i > 0) pos = pos + T(M.L[i - 1]) * v3t<T>(R[2], R[5], R[8]);
-    T s, c;
-    if constexpr (std::is_same<T, float>::value)
-      sincosf(q[i], &s, &c);
-    else
-      sincos(q[i], &s, &c);
+    const T s = sq[i], c = cq[i];
     const int a = M.axis[i];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
@@ -535,6 +591,19 @@ __device__ __forceinline__ void fk_ee(const DevModel& M, const T* q, T* p, float
       }
     }
   }
+}
+
+template <typename T>
+__device__ __forceinline__ void fk_ee(const DevModel& M, const T* q, T* p, float* J) {
+  T sq[QM], cq[QM];
+#pragma unroll
+  for (int i = 0; i < QM; ++i) {
+    if constexpr (std::is_same<T, float>::value)
+      sincosf(q[i], &sq[i], &cq[i]);
+    else
+      sincos(q[i], &sq[i], &cq[i]);
+  }
+  fk_ee_sc<T>(M, sq, cq, p, J);
 }
 
 }  // namespace gato

@@ -58,8 +58,8 @@ struct Ctx {
   // low parts of the iterate (X + Xlo, U + Ulo as double-float pairs); zero
   // until the solve escalates to the high-precision mode
   float *Xlo, *Ulo;
-  // 1 once the solve has escalated: FP64 mass matrix and bias, refined
-  // dynamics solves, double-float iterate, FP64 trial merits
+  // 1 once the solve has escalated: double-float mass matrix and bias,
+  // refined dynamics solves, double-float iterate and trial merits
   int hp = 0;
   LinkRec* LV;
   float* xs;            // padded x_s [VS]
@@ -412,15 +412,16 @@ __device__ inline void store_iterate(const Ctx& C, const ProbDesc& P) {
 // solution that noise, and the FP32 rounding of the iterate itself, are larger
 // than the merit decrease of a step, so the FP32 line search stalls with a
 // KKT residual of 1e-6..1e-4.  The high-precision mode removes both: M and the
-// bias in FP64, each dynamics solve refined once against them, the iterate as
-// double-float (hi, lo) pairs, the trial merits in FP64.
+// bias in double-float (dfl), each dynamics solve refined once against them,
+// the iterate as double-float (hi, lo) pairs, the trial merits in double-float.
+// Double-float runs on the FP32 pipe; only sin and cos of q use FP64.
 //
 // The stages below run as out-of-line calls with their fields passed by
-// value, so that their FP64 registers do not enter the allocation of the
-// kernel that calls them.
+// value, so that their registers do not enter the allocation of the kernel
+// that calls them.
 
-// Mass-matrix columns and bias in FP64 at q = X + Xlo, one (knot, column) per
-// thread.  Each value is stored as an (hi, lo) float pair: hi in Mi (the bias
+// Mass-matrix columns and bias in double-float (dfl; sin and cos of q by
+// FP64) at q = X + Xlo, one (knot, column) per thread.  Each value is stored as an (hi, lo) float pair: hi in Mi (the bias
 // in qdd), lo in the tangent array dT (column c at dT + c * 8, the bias at
 // dT + 56), which is free until the tangent stage.
 struct MassView {
@@ -433,27 +434,34 @@ struct MassView {
 
 static __device__ __noinline__ void st_mass_bias_hp(MassView v) {
   const DevModel& M = *v.M;
-  for (int it = threadIdx.x; it < (v.ke - v.k0) * 8; it += NTHR) {
-    const int k = v.k0 + (it >> 3), col = it & 7;
-    double sq[QM], cq[QM], qd[QM], acc[QM], tau[QM];
-    const float* x = v.X + k * VS;
-    const float* xl = v.Xlo + k * VS;
+  // one (knot, column) per thread, one round (8 KPC_MAX <= NTHR); the knot's
+  // eight threads share a warp, each forms sin and cos of one joint and the
+  // others take them by shuffles (idle threads join the shuffles)
+  const int it = threadIdx.x;
+  const bool act = it < (v.ke - v.k0) * 8;
+  const int k = v.k0 + (act ? it >> 3 : 0), col = it & 7;
+  const int base = (it & 31) & ~7;
+  const float* x = v.X + k * VS;
+  const float* xl = v.Xlo + k * VS;
+  dfl sj(0), cj(1);
+  if (act && col < QM) sincos(dfl(x[col], xl[col]), &sj, &cj);
+  dfl sq[QM], cq[QM], qd[QM], acc[QM], tau[QM];
 #pragma unroll
-    for (int i = 0; i < QM; ++i) {
-      sincos((double)x[i] + (double)xl[i], &sq[i], &cq[i]);
-      qd[i] = (col == 7) ? (double)x[QM + i] + (double)xl[QM + i] : 0.0;
-      acc[i] = (i == col) ? 1.0 : 0.0;
-    }
-    const Vec3<double> fw = col == 7 ? v3t<double>(v.fx, v.fy, v.fz) : vzero<double>();
-    rnea_value<double>(M, sq, cq, qd, acc, col == 7 ? (double)M.g : 0.0, fw, tau, nullptr);
-    float* lo = v.dT + k * DTS + col * 8;
+  for (int i = 0; i < QM; ++i) {
+    sq[i] = dfl(__shfl_sync(0xffffffffu, sj.hi, base + i), __shfl_sync(0xffffffffu, sj.lo, base + i));
+    cq[i] = dfl(__shfl_sync(0xffffffffu, cj.hi, base + i), __shfl_sync(0xffffffffu, cj.lo, base + i));
+    qd[i] = (col == 7) ? dfl(x[QM + i], xl[QM + i]) : dfl(0);
+    acc[i] = (i == col) ? dfl(1) : dfl(0);
+  }
+  if (!act) return;
+  const Vec3<dfl> fw = col == 7 ? v3t<dfl>(dfl(v.fx), dfl(v.fy), dfl(v.fz)) : vzero<dfl>();
+  rnea_value<dfl>(M, sq, cq, qd, acc, col == 7 ? dfl(M.g) : dfl(0), fw, tau, nullptr);
+  float* lo = v.dT + k * DTS + col * 8;
 #pragma unroll
-    for (int r = 0; r < QM; ++r) {
-      const float hi = (float)tau[r];
-      lo[r] = (float)(tau[r] - (double)hi);
-      if (col < 7) v.Mi[k * FQS + r * QM + col] = hi;
-      else v.qdd[k * US + r] = hi;
-    }
+  for (int r = 0; r < QM; ++r) {
+    lo[r] = tau[r].lo;
+    if (col < 7) v.Mi[k * FQS + r * QM + col] = tau[r].hi;
+    else v.qdd[k * US + r] = tau[r].hi;
   }
 }
 
@@ -501,11 +509,11 @@ __device__ inline void st_mass_bias(const Ctx& C) {
 
 // High-precision forward dynamics: M^-1 and qdd = M^-1 (u - bias) with one
 // step of iterative refinement each (the residual of the FP32 solution against
-// the FP64 (hi, lo) matrix, formed in FP64 and solved with the same FP32
+// the (hi, lo) matrix, formed in double-float and solved with the same FP32
 // factor: the refined error is ~kappa(M) eps_32 times the first one), and the
-// defects of the double-float iterate formed in FP64 from differences of the
-// iterates, e = (qd_k - qd_{k+1}) + h qdd, so that their rounding scales with
-// e itself rather than with the state.
+// defects of the double-float iterate formed in double-float from differences
+// of the iterates, e = (qd_k - qd_{k+1}) + h qdd, so that their rounding
+// scales with e itself rather than with the state.
 struct FdView {
   const float *X, *Xlo, *U, *Ulo, *xs;
   float *Mi, *qdd, *dT, *cv, *scal;
@@ -516,7 +524,6 @@ struct FdView {
 static __device__ __noinline__ void st_forward_dynamics_hp(FdView v) {
   const int N = v.N;
   const int ke = v.k1 < N ? v.k1 : N;
-  const double h = v.h;
   const int nk = ke - v.k0;
   const int it = threadIdx.x;
   const int k = v.k0 + (it >> 3), col = it & 7;
@@ -532,36 +539,36 @@ static __device__ __noinline__ void st_forward_dynamics_hp(FdView v) {
     for (int i = 0; i < QM; ++i)
       if (i >= v.dof) Ml[i * (i + 1) / 2 + i] = 1.f;
   }
-  // the FP64 right-hand side and the residual of the first solve against the
-  // (hi, lo) matrix, both read before any column of M^-1 overwrites M
-  double res[QM];
+  // the double-float right-hand side and the residual of the first solve
+  // against the (hi, lo) matrix, both read before any column of M^-1
+  // overwrites M
+  dfl res[QM];
   float x[QM];
   bool ok = true;
   if (act) {
     const float* lo = v.dT + k * DTS;
-    double rhs[QM];
+    dfl rhs[QM];
 #pragma unroll
     for (int i = 0; i < QM; ++i)
-      rhs[i] = col == 7 ? ((double)v.U[k * US + i] + (double)v.Ulo[k * US + i]) -
-                              ((double)v.qdd[k * US + i] + (double)lo[56 + i])
-                        : (i == col ? 1.0 : 0.0);
+      rhs[i] = col == 7 ? dfl(v.U[k * US + i], v.Ulo[k * US + i]) - dfl(v.qdd[k * US + i], lo[56 + i])
+                        : dfl(i == col ? 1 : 0);
     ok = chol7(Ml);
 #pragma unroll
-    for (int i = 0; i < QM; ++i) x[i] = (float)rhs[i];
+    for (int i = 0; i < QM; ++i) x[i] = rhs[i].hi;
     chol7_solve(Ml, x);
 #pragma unroll
     for (int i = 0; i < QM; ++i) {
-      double r = rhs[i];
+      dfl r = rhs[i];
 #pragma unroll
       for (int j2 = 0; j2 < QM; ++j2) {
-        double m;
+        dfl m;
         if (i >= v.dof || j2 >= v.dof) {
-          m = (i == j2) ? 1.0 : 0.0;
+          m = dfl(i == j2 ? 1 : 0);
         } else {
-          m = 0.5 * (((double)v.Mi[k * FQS + i * QM + j2] + (double)lo[j2 * 8 + i]) +
-                     ((double)v.Mi[k * FQS + j2 * QM + i] + (double)lo[i * 8 + j2]));
+          m = dfl(0.5f) * (dfl(v.Mi[k * FQS + i * QM + j2], lo[j2 * 8 + i]) +
+                           dfl(v.Mi[k * FQS + j2 * QM + i], lo[i * 8 + j2]));
         }
-        r -= m * (double)x[j2];
+        r -= m * dfl(x[j2]);
       }
       res[i] = r;
     }
@@ -570,7 +577,7 @@ static __device__ __noinline__ void st_forward_dynamics_hp(FdView v) {
   if (act) {
     float d[QM];
 #pragma unroll
-    for (int i = 0; i < QM; ++i) d[i] = (float)res[i];
+    for (int i = 0; i < QM; ++i) d[i] = res[i].hi;
     chol7_solve(Ml, d);
     if (col == 7) {
       if (!ok) atomicOr(reinterpret_cast<int*>(v.scal + S_FLAGS), F_NONFINITE);
@@ -578,25 +585,26 @@ static __device__ __noinline__ void st_forward_dynamics_hp(FdView v) {
       const float* xkl = v.Xlo + k * VS;
       const float* xn = v.X + (k + 1) * VS;
       const float* xnl = v.Xlo + (k + 1) * VS;
+      const dfl h(v.h), h2 = h * h;
 #pragma unroll
       for (int i = 0; i < QM; ++i) {
-        const double a = (double)x[i] + (double)d[i];
-        v.qdd[k * US + i] = (float)a;
+        const dfl a = dfl_sum(x[i], d[i]);
+        v.qdd[k * US + i] = a.hi;
         // qd+ = qd + h qdd, q+ = q + h qd+ = q + h qd + h^2 qdd
-        const double dqd = ((double)xk[QM + i] - (double)xn[QM + i]) + ((double)xkl[QM + i] - (double)xnl[QM + i]);
-        const double dq = ((double)xk[i] - (double)xn[i]) + ((double)xkl[i] - (double)xnl[i]);
-        const double qdk = (double)xk[QM + i] + (double)xkl[QM + i];
-        v.cv[(k + 1) * VS + QM + i] = (float)(dqd + h * a);
-        v.cv[(k + 1) * VS + i] = (float)(dq + h * qdk + h * h * a);
+        const dfl dqd = (dfl(xk[QM + i]) - dfl(xn[QM + i])) + (dfl(xkl[QM + i]) - dfl(xnl[QM + i]));
+        const dfl dq = (dfl(xk[i]) - dfl(xn[i])) + (dfl(xkl[i]) - dfl(xnl[i]));
+        const dfl qdk(xk[QM + i], xkl[QM + i]);
+        v.cv[(k + 1) * VS + QM + i] = (dqd + h * a).hi;
+        v.cv[(k + 1) * VS + i] = (dq + h * qdk + h2 * a).hi;
       }
     } else {
 #pragma unroll
-      for (int i = 0; i < QM; ++i) v.Mi[k * FQS + i * QM + col] = (float)((double)x[i] + (double)d[i]);
+      for (int i = 0; i < QM; ++i) v.Mi[k * FQS + i * QM + col] = dfl_sum(x[i], d[i]).hi;
     }
   }
   if (it == 8 * nk && v.k0 == 0) {  // c_0 = x_s - x_0, by the CTA owning knot 0
 #pragma unroll
-    for (int i = 0; i < XM; ++i) v.cv[i] = (float)(((double)v.xs[i] - (double)v.X[i]) - (double)v.Xlo[i]);
+    for (int i = 0; i < XM; ++i) v.cv[i] = ((dfl(v.xs[i]) - dfl(v.X[i])) - dfl(v.Xlo[i])).hi;
   }
 }
 
@@ -1945,10 +1953,11 @@ __device__ __forceinline__ float trial_cost(const Ctx& C, int k, const float* x,
 }
 
 
-// High-precision trial merits: the trial point (X + Xlo) + alpha dX in FP64;
-// qdd from the FP32 factor refined twice against an FP64 RNEA residual
-// u - ID(q, qd, qdd_0); defects and costs in FP64.  Each per-knot value is
-// stored as an (hi, lo) float pair (hi in `hi`, lo in `lo`, [na][K] each).
+// High-precision trial merits: the trial point (X + Xlo) + alpha dX in
+// double-float (dfl); qdd from the FP32 factor refined twice against a
+// double-float RNEA residual u - ID(q, qd, qdd_0); defects and costs in
+// double-float (sin and cos of q by FP64).  Each per-knot value is stored as
+// an (hi, lo) float pair (hi in `hi`, lo in `lo`, [na][K] each).
 struct LsView {
   const DevModel* M;
   const float *X, *Xlo, *U, *Ulo, *dX, *dU, *xs, *x_ref, *ee_ref;
@@ -1964,55 +1973,59 @@ static __device__ __noinline__ void st_line_search_hp(LsView v) {
   const int N = v.N, K = v.k1 - v.k0;
   const DevModel& M = *v.M;
   const int nx = 2 * v.dof;
+  const dfl half(0.5f);
   for (int it = threadIdx.x; it < v.na * K; it += NTHR) {
     const int a = it / K, k = v.k0 + it % K;
-    double alpha = 1.0;
-    for (int i = 0; i < a; ++i) alpha /= (double)v.beta;
-    if (v.base) alpha = 0.0;
-    auto xat = [&](int idx) {
-      return ((double)v.X[idx] + (double)v.Xlo[idx]) + alpha * (double)v.dX[idx];
-    };
-    auto uat = [&](int idx) {
-      return ((double)v.U[idx] + (double)v.Ulo[idx]) + alpha * (double)v.dU[idx];
-    };
-    const double s = (k == N) ? (double)v.w[3] : 1.0;
-    double x[XM];
+    // the step length as the accept stage forms it (a float)
+    float alpha = 1.f;
+    for (int i = 0; i < a; ++i) alpha /= v.beta;
+    if (v.base) alpha = 0.f;
+    auto xat = [&](int idx) { return dfl(v.X[idx], v.Xlo[idx]) + dfl(alpha) * dfl(v.dX[idx]); };
+    auto uat = [&](int idx) { return dfl(v.U[idx], v.Ulo[idx]) + dfl(alpha) * dfl(v.dU[idx]); };
+    const dfl s = (k == N) ? dfl(v.w[3]) : dfl(1);
+    dfl x[XM];
 #pragma unroll
     for (int i = 0; i < XM; ++i) x[i] = xat(k * VS + i);
-    double val = 0.0;
+    // sin and cos of the trial q, shared by the kinematics and the dynamics
+    dfl sq[QM], cq[QM];
+    if (v.cost_kind != 0 || k < N) {
+#pragma unroll
+      for (int i = 0; i < QM; ++i) sincos(x[i], &sq[i], &cq[i]);
+    }
+    dfl val(0);
     // stage cost
     if (v.cost_kind == 0) {
 #pragma unroll
       for (int i = 0; i < XM; ++i) {
         const int ui = i < QM ? i : i - QM + v.dof;  // user layout of x_ref
         const bool used = (i < QM ? i : i - QM) < v.dof;
-        const double wi = i < QM ? (double)v.w[0] : (double)v.w[1];
-        const double d = used ? x[i] - (double)v.x_ref[k * nx + ui] : 0.0;
-        val += 0.5 * s * wi * d * d;
+        const dfl wi(i < QM ? v.w[0] : v.w[1]);
+        const dfl d = used ? x[i] - dfl(v.x_ref[k * nx + ui]) : dfl(0);
+        val += half * s * wi * d * d;
       }
     } else {
-      double p[3];
-      fk_ee<double>(M, x, p, nullptr);
+      dfl p[3];
+      fk_ee_sc<dfl>(M, sq, cq, p, nullptr);
       const float* pr = v.ee_ref + 3 * k;
-      const double d0 = p[0] - (double)pr[0], d1 = p[1] - (double)pr[1], d2 = p[2] - (double)pr[2];
-      val += 0.5 * s * (double)v.w[4] * (d0 * d0 + d1 * d1 + d2 * d2);
+      const dfl d0 = p[0] - dfl(pr[0]), d1 = p[1] - dfl(pr[1]), d2 = p[2] - dfl(pr[2]);
+      val += half * s * dfl(v.w[4]) * (d0 * d0 + d1 * d1 + d2 * d2);
 #pragma unroll
-      for (int i = 0; i < QM; ++i) val += 0.5 * s * (double)v.w[1] * x[QM + i] * x[QM + i];
+      for (int i = 0; i < QM; ++i) val += half * s * dfl(v.w[1]) * x[QM + i] * x[QM + i];
     }
     if (k < N) {
-      double u[QM];
+      dfl u[QM];
 #pragma unroll
       for (int i = 0; i < QM; ++i) {
         u[i] = uat(k * US + i);
-        val += 0.5 * (double)v.w[2] * u[i] * u[i];
+        val += half * dfl(v.w[2]) * u[i] * u[i];
       }
       // FP32 forward dynamics at the rounded point, then refinement
-      // against the FP64 inverse dynamics at the exact trial point
+      // against the double-float inverse dynamics at the exact trial point
       float qf[QM], qdf[QM], sqf[QM], cqf[QM], Ml[28], z[QM], b[QM], qdd[QM];
 #pragma unroll
       for (int i = 0; i < QM; ++i) {
-        qf[i] = (float)x[i];
-        qdf[i] = (float)x[QM + i];
+        qf[i] = x[i].hi;
+        qdf[i] = x[QM + i].hi;
         sincosf(qf[i], &sqf[i], &cqf[i]);
         z[i] = 0.f;
       }
@@ -2020,50 +2033,48 @@ static __device__ __noinline__ void st_line_search_hp(LsView v) {
       const V3 fw = v3(v.fx, v.fy, v.fz);
       rnea_value(M, sqf, cqf, qdf, z, M.g, fw, b, nullptr);
 #pragma unroll
-      for (int i = 0; i < QM; ++i) qdd[i] = (float)u[i] - b[i];
+      for (int i = 0; i < QM; ++i) qdd[i] = u[i].hi - b[i];
       chol7(Ml);
       chol7_solve(Ml, qdd);
-      double sq[QM], cq[QM], qd[QM], a0[QM], tau[QM];
+      dfl qd[QM], a0[QM], tau[QM];
 #pragma unroll
       for (int i = 0; i < QM; ++i) {
-        sincos(x[i], &sq[i], &cq[i]);
         qd[i] = x[QM + i];
-        a0[i] = (double)qdd[i];
+        a0[i] = dfl(qdd[i]);
       }
       // two refinement steps: each shrinks the error of qdd by ~kappa(M) eps_32
       // (the FP32 CRBA factor is the preconditioner), from ~1e-5 to ~1e-12
       // relative, below the merit decreases the line search must resolve
 #pragma unroll 1
       for (int pass = 0; pass < 2; ++pass) {
-        rnea_value<double>(M, sq, cq, qd, a0, (double)M.g, v3t<double>(v.fx, v.fy, v.fz), tau, nullptr);
+        rnea_value<dfl>(M, sq, cq, qd, a0, dfl(M.g), v3t<dfl>(dfl(v.fx), dfl(v.fy), dfl(v.fz)), tau, nullptr);
         float r[QM];
 #pragma unroll
-        for (int i = 0; i < QM; ++i) r[i] = i < v.dof ? (float)(u[i] - tau[i]) : 0.f;
+        for (int i = 0; i < QM; ++i) r[i] = i < v.dof ? (u[i] - tau[i]).hi : 0.f;
         chol7_solve(Ml, r);
 #pragma unroll
-        for (int i = 0; i < QM; ++i) a0[i] += (double)r[i];
+        for (int i = 0; i < QM; ++i) a0[i] += dfl(r[i]);
       }
-      const double h = (double)v.h;
-      double c1 = 0.0;
+      const dfl h(v.h), h2 = h * h;
+      dfl c1(0);
 #pragma unroll
       for (int i = 0; i < QM; ++i) {
         if (i >= v.dof) continue;
-        const double acc = a0[i];
-        const double cqd = (x[QM + i] - xat((k + 1) * VS + QM + i)) + h * acc;
-        const double cq_ = (x[i] - xat((k + 1) * VS + i)) + h * x[QM + i] + h * h * acc;
-        c1 += fabs(cq_) + fabs(cqd);
+        const dfl acc = a0[i];
+        const dfl cqd = (x[QM + i] - xat((k + 1) * VS + QM + i)) + h * acc;
+        const dfl cq_ = (x[i] - xat((k + 1) * VS + i)) + h * x[QM + i] + h2 * acc;
+        c1 += dfl_abs(cq_) + dfl_abs(cqd);
       }
-      val += (double)v.mu * c1;
+      val += dfl(v.mu) * c1;
     }
     if (k == 0) {
-      double c0 = 0.0;
+      dfl c0(0);
 #pragma unroll
-      for (int i = 0; i < XM; ++i) c0 += fabs((double)v.xs[i] - x[i]);
-      val += (double)v.mu * c0;
+      for (int i = 0; i < XM; ++i) c0 += dfl_abs(dfl(v.xs[i]) - x[i]);
+      val += dfl(v.mu) * c0;
     }
-    const float vh = (float)val;
-    v.hi[a * K + (k - v.k0)] = vh;
-    v.lo[a * K + (k - v.k0)] = (float)(val - (double)vh);
+    v.hi[a * K + (k - v.k0)] = val.hi;
+    v.lo[a * K + (k - v.k0)] = val.lo;
   }
 }
 
@@ -2210,15 +2221,15 @@ __device__ inline int st_accept(const Ctx& C, float beta, int n_alpha) {
     if (C.hp) {  // the double-float iterate: (hi, lo) <- hi + lo + alpha d, rounded to a pair
       for (int i = threadIdx.x; i < (C.k1 - C.k0) * VS; i += NTHR) {
         const int o = C.k0 * VS + i;
-        const double v = ((double)C.X[o] + (double)C.Xlo[o]) + (double)alpha * (double)C.dX[o];
-        C.X[o] = (float)v;
-        C.Xlo[o] = (float)(v - (double)C.X[o]);
+        const dfl v = dfl(C.X[o], C.Xlo[o]) + dfl(alpha) * dfl(C.dX[o]);  // the line search's trial point
+        C.X[o] = v.hi;
+        C.Xlo[o] = v.lo;
       }
       for (int i = threadIdx.x; i < (ke - C.k0) * US; i += NTHR) {
         const int o = C.k0 * US + i;
-        const double v = ((double)C.U[o] + (double)C.Ulo[o]) + (double)alpha * (double)C.dU[o];
-        C.U[o] = (float)v;
-        C.Ulo[o] = (float)(v - (double)C.U[o]);
+        const dfl v = dfl(C.U[o], C.Ulo[o]) + dfl(alpha) * dfl(C.dU[o]);
+        C.U[o] = v.hi;
+        C.Ulo[o] = v.lo;
       }
     } else {
       for (int i = threadIdx.x; i < (C.k1 - C.k0) * VS; i += NTHR) C.X[C.k0 * VS + i] += alpha * C.dX[C.k0 * VS + i];
