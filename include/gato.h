@@ -107,9 +107,11 @@ typedef struct {
                               solution, where FP32 rounding of the dynamics and of the
                               iterate exceeds the decrease), or whose FP32 KKT test
                               passes, repeats that SQP iteration in a high-precision
-                              mode and stays in it for the rest of the call: FP64 mass
-                              matrix and bias, each dynamics solve refined in FP64, the
-                              iterate kept as double-float pairs, trial merits in FP64.
+                              mode and stays in it for the rest of the call: mass
+                              matrix and bias in double-float (FP32 pairs; sin and cos
+                              of q in FP64), each dynamics solve refined against them,
+                              the iterate kept as double-float pairs, trial merits in
+                              double-float.
                               The repeated iteration counts once.  Without a tolerance
                               (fixed iteration counts, real-time ticks) nothing
                               escalates.  GATO_PRECISION_FP32: never escalate (the step
