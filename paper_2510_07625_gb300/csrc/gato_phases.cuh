@@ -987,6 +987,23 @@ __device__ inline void st_schur(const Ctx& C) {
     const float* Mi = C.Mi + kk * FQS;
     const float* Ri = C.Ri + kk * US;
     const float* Qi1 = C.Qi + k * QIS;
+    // B R^-1 B^T = si sc K with K = M^-1 R^-1 M^-1 and the row and column
+    // factors si, sc (h^2 on q rows, h on qd rows): row j of K once, each
+    // term (M^-1[j, m] R^-1[m]) M^-1[c, m] formed exactly as a (hi, lo) pair
+    DF Kr[QM];
+#pragma unroll
+    for (int cm = 0; cm < QM; ++cm) {
+      DF sk = df_zero();
+#pragma unroll
+      for (int m = 0; m < QM; ++m) {
+        const float p = __fmul_rn(Mi[j * QM + m], Ri[m]);
+        const float pe = __fmaf_rn(Mi[j * QM + m], Ri[m], -p);
+        const float mi = Mi[cm * QM + m];
+        const float q = __fmul_rn(p, mi);
+        sk = df_addd(sk, DF{q, __fmaf_rn(p, mi, -q) + pe * mi});
+      }
+      Kr[cm] = sk;
+    }
     for (int t = 0; t < 2; ++t) {
       const int i = j + QM * t;
       float Arow[XM];
@@ -1009,15 +1026,14 @@ __device__ inline void st_schur(const Ctx& C) {
         for (int l = 0; l < XM; ++l) a = df_fma(a, -Arow[l], bL(C, k, c, l));
         const int cm = c < QM ? c : c - QM;
         const float sc = c < QM ? h * h : h;
-        DF bb = df_zero();
+        DF kv = Kr[0];  // K[j][cm] (a select: cm is not a compile-time index)
 #pragma unroll
-        for (int m = 0; m < QM; ++m) {
-          bb = df_fma(bb, BRrow[m], Mi[cm * QM + m]);
-          bb = df_add(bb, BRlo[m] * Mi[cm * QM + m]);
-        }
-        // sc * bb, exactly to double-float accuracy
-        const float ph = __fmul_rn(sc, bb.hi);
-        const DF sbb = DF{ph, __fmaf_rn(sc, bb.hi, -ph) + sc * bb.lo};
+        for (int m = 1; m < QM; ++m) kv = (cm == m) ? Kr[m] : kv;
+        // (si sc) K[j][cm], both products exact to double-float accuracy
+        const float f = __fmul_rn(si, sc);
+        const float fe = __fmaf_rn(si, sc, -f);
+        const float ph = __fmul_rn(f, kv.hi);
+        const DF sbb = DF{ph, __fmaf_rn(f, kv.hi, -ph) + (f * kv.lo + fe * kv.hi)};
         bD(C, k, i, c) = df_val(df_add(df_addd(a, sbb), Qinv_elem(Qi1, i, c)));
       }
       // zeta with d: L_k d_{k-1} - B R^-1 d_u,{k-1} + Q_k^-1 d_k
