@@ -309,7 +309,7 @@ def run_gpu(args):
 # DRAM bytes (read + written) per launch of the dominant kernel on this
 # workload (latency form, 33 knots per CTA), from an ncu capture of the
 # current kernel; None while the kernel has changed since the last capture.
-TRAFFIC_BYTES = 25539072
+TRAFFIC_BYTES = 25120512
 
 
 def latency_runs(gato, I, torch, stream, flush, n_calls=1000, launch_cfg=False, **prm):
