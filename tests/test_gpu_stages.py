@@ -289,3 +289,64 @@ def test_pcg_recovery_and_line_search_stages(G, oracle, name, mk, precond):
         al = 0.5 ** a
         m_ora = oracle.merit(prob, X + al * dX, U + al * dU)
         assert abs(scal[16 + a] - m_ora) <= 2e-5 * m_ora, (a, scal[16 + a], m_ora)
+
+
+EPS32 = 2.0 ** -24
+
+
+def f32_problem(prob):
+    """The problem as the GPU holds it: model parameters, gravity, time step,
+    force and initial state rounded to float32 (the oracle then evaluates
+    the same model, so only the arithmetic differs)."""
+    import dataclasses
+
+    r = lambda t: tuple(float(np.float32(v)) for v in t)
+    m = prob.model
+    fm = dataclasses.replace(m, link_len=r(m.link_len), mass=r(m.mass), com=r(m.com), inertia=r(m.inertia),
+                             gravity=float(np.float32(m.gravity)))
+    return dataclasses.replace(prob, model=fm, dt=float(np.float32(prob.dt)), f_ext=r(prob.f_ext),
+                               x_s=np.asarray(prob.x_s, np.float32).astype(np.float64))
+
+
+@pytest.mark.parametrize("name,mk", PROBS, ids=[p[0] for p in PROBS])
+def test_high_precision_dynamics_stages(G, oracle, name, mk):
+    """The high-precision mode's dynamics (GATO_PRECISION_HIGH, plain form)
+    against the FP64 oracle on the float32-rounded model.  After the mass
+    stage M and the bias
+    ID(q, qd, 0) - J_p^T f_ext, kept as (hi, lo) float pairs, carry the
+    double-float accuracy of their arithmetic (1e-10 of their scale here; the
+    FP32 mode's error is ~1e-6).  After the forward dynamics the stored qdd
+    is refined once with the FP32 factor: error ~(kappa(M) eps_32)^2 from the
+    refinement plus its FP32 rounding, and the defects carry h times that
+    plus their own rounding."""
+    prob = mk()
+    X, U, lam = midpoint(oracle, prob)
+    N, K = prob.N, prob.N + 1
+    dof = prob.model.dof
+    Xf = X.astype(np.float32).astype(np.float64)
+    Uf = U.astype(np.float32).astype(np.float64)
+    buf, off, _ = stage(G, prob, 1, X, U, lam, precision=2)
+    prob = f32_problem(prob)
+    f = np.array(prob.f_ext, dtype=np.float64)
+    DTS = 112
+    for k in range(N):
+        q, qd = Xf[k, :dof], Xf[k, dof:]
+        M_ora = oracle.mass_matrix(prob.model, q)
+        b_ora = oracle.rnea(prob.model, q, qd, np.zeros(dof)) - oracle.ee_joint_torque(prob.model, q, f)
+        hi = buf[off["Minv"] + k * 49:off["Minv"] + k * 49 + 49].reshape(7, 7)
+        lo = buf[off["dTau"] + k * DTS:off["dTau"] + k * DTS + 56].reshape(7, 8)[:, :7].T  # lo[r][col] at col * 8 + r
+        M_gpu = (hi + lo)[:dof, :dof]
+        np.testing.assert_allclose(M_gpu, M_ora, atol=1e-10 * max(1.0, np.abs(M_ora).max()), rtol=0)
+        b_gpu = buf[off["qdd"] + k * US:off["qdd"] + k * US + dof] + \
+            buf[off["dTau"] + k * DTS + 56:off["dTau"] + k * DTS + 56 + dof]
+        np.testing.assert_allclose(b_gpu, b_ora, atol=1e-10 * max(1.0, np.abs(b_ora).max()), rtol=0)
+    buf, off, _ = stage(G, prob, 2, X, U, lam, precision=2)
+    qdd_gpu = knots(buf, off, "qdd", N, US, dof)
+    qdd_ora = np.array([oracle.forward_dynamics(prob.model, Xf[k, :dof], Xf[k, dof:], Uf[k], f) for k in range(N)])
+    kappa = max(np.linalg.cond(oracle.mass_matrix(prob.model, Xf[k, :dof])) for k in range(N))
+    tol_qdd = np.abs(qdd_ora).max() * (10 * (kappa * EPS32) ** 2 + 4 * EPS32)
+    np.testing.assert_allclose(qdd_gpu, qdd_ora, atol=tol_qdd, rtol=0)
+    lin = oracle.linearize(prob, Xf, Uf)
+    c = knots(buf, off, "c", K, VS, XM)[:, pad_idx(dof)]
+    tol_c = prob.dt * tol_qdd + 4 * EPS32 * max(1.0, np.abs(lin["c"]).max())
+    np.testing.assert_allclose(c, lin["c"], atol=tol_c, rtol=0)
