@@ -296,16 +296,18 @@ EPS32 = 2.0 ** -24
 
 def f32_problem(prob):
     """The problem as the GPU holds it: model parameters, gravity, time step,
-    force and initial state rounded to float32 (the oracle then evaluates
-    the same model, so only the arithmetic differs)."""
+    force, initial state, cost weights and references rounded to float32
+    (the oracle then evaluates the same problem, so only the arithmetic
+    differs)."""
     import dataclasses
 
     r = lambda t: tuple(float(np.float32(v)) for v in t)
+    a = lambda x: None if x is None else np.asarray(x, np.float32).astype(np.float64)
     m = prob.model
     fm = dataclasses.replace(m, link_len=r(m.link_len), mass=r(m.mass), com=r(m.com), inertia=r(m.inertia),
                              gravity=float(np.float32(m.gravity)))
     return dataclasses.replace(prob, model=fm, dt=float(np.float32(prob.dt)), f_ext=r(prob.f_ext),
-                               x_s=np.asarray(prob.x_s, np.float32).astype(np.float64))
+                               x_s=a(prob.x_s), w=r(prob.w), x_ref=a(prob.x_ref), ee_ref=a(prob.ee_ref))
 
 
 @pytest.mark.parametrize("name,mk", PROBS, ids=[p[0] for p in PROBS])
@@ -350,3 +352,30 @@ def test_high_precision_dynamics_stages(G, oracle, name, mk):
     c = knots(buf, off, "c", K, VS, XM)[:, pad_idx(dof)]
     tol_c = prob.dt * tol_qdd + 4 * EPS32 * max(1.0, np.abs(lin["c"]).max())
     np.testing.assert_allclose(c, lin["c"], atol=tol_c, rtol=0)
+
+
+@pytest.mark.parametrize("name,mk", PROBS, ids=[p[0] for p in PROBS])
+def test_high_precision_line_search_stage(G, oracle, name, mk):
+    """The high-precision mode's trial merits (double-float pairs) against the
+    oracle's merit on the float32-rounded problem at the same trial points:
+    with a zero low part the trial point X + alpha dX is exact on both sides,
+    and qdd, refined twice, errs by ~(kappa(M) eps_32)^3, so the merits agree
+    to 1e-9 relative (the FP32 mode's bound is 2e-5)."""
+    prob = mk()
+    X, U, lam = midpoint(oracle, prob)
+    N, K = prob.N, prob.N + 1
+    dof = prob.model.dof
+    pi = pad_idx(dof)
+    buf, off, _ = stage(G, prob, 11, X, U, lam, precision=2)
+    pf = f32_problem(prob)
+    Xf = X.astype(np.float32).astype(np.float64)
+    Uf = U.astype(np.float32).astype(np.float64)
+    dX = knots(buf, off, "dX", K, VS, XM)[:, pi]
+    dU = knots(buf, off, "dU", N, US, 7)[:, :dof]
+    scal = buf[off["scal"]:off["scal"] + 128]
+    for a in range(8):
+        al = 0.5 ** a
+        m_gpu = scal[66 + 2 * a] + scal[67 + 2 * a]
+        m_ora = oracle.merit(pf, Xf + al * dX, Uf + al * dU)
+        assert abs(m_gpu - m_ora) <= 1e-9 * m_ora, (a, m_gpu, m_ora)
+
