@@ -706,8 +706,8 @@ def cpu_baseline():
 
 
 def oracle_error_report(runs, rho_probs, rho_rows):
-    """The oracle leg's comparison of the GPU's results with the FP64 oracle
-    (the benchmark spec pattern 1: the error against the oracle per config).
+    """The oracle leg's comparison of the GPU's results with the FP64 oracle:
+    the error against the oracle for every workload.
 
     Per workload, fixed count: the oracle from the same cold start (its PCG at
     eps = 1e-6, and its direct solve: their distance is the spread of the
